@@ -1,0 +1,201 @@
+/*
+ * lrh.h — C ABI of the B300 message-passing dual solver for local relaxation
+ * hierarchies of quantum ground-state energies.
+ *
+ * The library runs, on one GPU, the data-parallel iteration of the paper's
+ * dual solvers over every region e of a cluster family C:
+ *
+ *   theta_e = h_e - sum_{f in D(e)} 1_{e\f} (x) nu_{e->f} + sum_{g in A(e)} nu_{g->e}
+ *                                                        (Sec. 4.2, local augmented Hamiltonian)
+ *   theta_e = V diag(lambda) V^dagger                    (Hermitian eigendecomposition, FP32)
+ *   subgradient (Alg. 1):  mu_e = ground projector / its trace,  value lambda_min(theta_e)
+ *   smoothed   (Alg. 2):  rho_e = V softmax(-beta lambda) V^dagger,
+ *                         value F_beta = lambda_min - log(sum e^{-beta(lambda-lambda_min)}) / beta
+ *                                                        (Sec. 4.1.2, soft local minimum eigenvalue)
+ *   g_{e->f} = rho_f - Tr_{e\f} rho_e                    (Sec. 4.1.1 / 4.1.2 / 4.2 gradient components)
+ *   Alg. 1 update:  nu += alpha_t g,  best-so-far q and nu tracked
+ *   Alg. 2 update:  zeta += g / (theta_k L_hat),  nu = (1-theta_k) nu + theta_k zeta,
+ *                   theta_{k+1} = (sqrt(theta_k^4 + 4 theta_k^2) - theta_k^2) / 2,
+ *                   messages evaluated at eta = (1-theta_k) nu + theta_k zeta
+ *   bound Q(nu) = sum_e lambda_min(theta_e(nu))           (Eq. dual_function_non-smooth; Q_C, Sec. 4.2)
+ *                 summed in FP64; the certified bound rebuilds theta_e in FP64 from the stored
+ *                 FP32 messages and takes lambda_min in FP64 (weak duality makes it a valid
+ *                 lower bound on E_0 for any Hermitian nu).
+ *
+ * Conventions
+ * -----------
+ * - Every site is a qubit (local dimension d = 2).  A region with k sites has D = 2^k.
+ * - Kronecker order inside a region (and inside a term): the region's sites sorted ascending,
+ *   first site = most significant bit of the basis index.
+ * - Pairs e->f are the covering relation of the region family under inclusion (f a proper
+ *   subset of e with no region strictly between them; Sec. 4.2 remark that only consecutive
+ *   levels need constraints).  Pair order: ascending parent index, then ascending child index.
+ * - Message layout (all message-like arrays: nu, zeta, nu_best, gradient): per instance, the
+ *   pairs in pair order, each a D_f x D_f complex matrix row-major, complex64 = (float re, float im).
+ *   Instances are contiguous blocks of lrh_info.msg_elems complex entries.
+ * - Term placement: each Hamiltonian term goes to the smallest region containing its sites
+ *   (lowest region index on ties).
+ *
+ * Ownership and errors
+ * --------------------
+ * - Every pointer in lrh_problem_desc is a HOST pointer; the library copies what it needs
+ *   during lrh_create and keeps no reference.
+ * - The library owns all device memory of a problem; lrh_destroy frees it.
+ * - Buffers passed to lrh_get_messages / lrh_set_messages belong to the caller; a device buffer
+ *   must be on the problem's device.
+ * - All calls return LRH_OK (0) or a negative LRH_E* code; no C++ exception crosses the ABI.
+ *   lrh_last_error() returns a thread-local message describing the last failure.
+ * - Work is enqueued on the stream given at creation (NULL = the legacy default stream);
+ *   lrh_step returns without waiting.  Calls that return numbers to the host synchronise
+ *   that stream.  A problem must not be used from two host threads at once.
+ */
+#ifndef LRH_H
+#define LRH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- return codes */
+#define LRH_OK            0
+#define LRH_EINVAL       (-1)  /* bad argument, size or option */
+#define LRH_ENOTHERM     (-2)  /* a term matrix is not Hermitian */
+#define LRH_EPOSET       (-3)  /* duplicate region, or a term fits in no region */
+#define LRH_ENOMEM       (-4)  /* host or device allocation failed */
+#define LRH_ECUDA        (-5)  /* a CUDA runtime call failed */
+#define LRH_ETIMEOUT     (-6)  /* reserved: a bounded device wait gave up */
+#define LRH_ENUMERIC     (-7)  /* a non-finite eigenvalue, value or message was produced */
+#define LRH_EUNSUPPORTED (-8)  /* region size beyond the kernels built into this library */
+
+/* ---------------------------------------------------------------- enums */
+#define LRH_SUBGRADIENT   0    /* Alg. 1: ground projectors, nu += alpha_t g            */
+#define LRH_NESTEROV      1    /* Alg. 2: Gibbs states at eta, accelerated update of Q_beta */
+
+#define LRH_STEP_CONST    0    /* alpha_t = alpha                        (Thm 4 choice)  */
+#define LRH_STEP_INV_SQRT 1    /* alpha_t = alpha / sqrt(t + 1)                           */
+
+#define LRH_MSG_NU        0    /* current multipliers nu                                  */
+#define LRH_MSG_ZETA      1    /* Nesterov auxiliary sequence zeta                        */
+#define LRH_MSG_NU_BEST   2    /* subgradient: nu at the best q seen so far               */
+#define LRH_MSG_GRAD      3    /* gradient g of the last lrh_evaluate (read only)         */
+
+#define LRH_BOUND_CERTIFIED 0  /* FP64 rebuild + FP64 lambda_min at nu (Alg. 2) or nu_best (Alg. 1) */
+#define LRH_BOUND_LAST      1  /* FP64 sum of the per-region FP32 values of the last region pass:
+                                  Q_beta(eta) for Alg. 2, Q(nu) for Alg. 1                   */
+#define LRH_BOUND_BEST      2  /* Alg. 1 q_best = max over past iterations of Q(nu^(t))      */
+
+/* ---------------------------------------------------------------- problem description */
+typedef struct {
+    int32_t n_sites;              /* sites 0 .. n_sites-1, all qubits                          */
+    int32_t n_regions;            /* regions of the cluster family                             */
+    const int64_t* region_ptr;    /* [n_regions + 1] CSR offsets into region_sites             */
+    const int32_t* region_sites;  /* sorted, unique site ids of each region (1..7 sites)       */
+    int32_t n_terms;              /* Hamiltonian terms                                          */
+    const int64_t* term_ptr;      /* [n_terms + 1] CSR offsets into term_sites                 */
+    const int32_t* term_sites;    /* sorted, unique sites of each term                          */
+    const int64_t* term_mat_off;  /* [n_terms] offset (complex entries) of each term's matrix  */
+    int64_t term_mat_total;       /* complex entries of all term matrices of ONE instance       */
+    const double* term_mats;      /* [n_instances][term_mat_total][2] (re, im), row-major
+                                     2^k x 2^k per term; instance i holds its own matrices     */
+    int32_t n_instances;          /* >= 1 Hamiltonians sharing one region family (batch)       */
+} lrh_problem_desc;
+
+typedef struct {
+    int32_t variant;      /* LRH_SUBGRADIENT or LRH_NESTEROV                                  */
+    int32_t step_rule;    /* LRH_STEP_CONST or LRH_STEP_INV_SQRT (subgradient only)           */
+    double  alpha;        /* subgradient step scale (> 0)                                     */
+    double  beta;         /* smoothing inverse temperature (> 0, Nesterov)                    */
+    double  lhat;         /* Lipschitz estimate L_hat; <= 0 selects beta * Lambda_G / 2       */
+    double  degen_tol;    /* ground space = eigenvalues within degen_tol * max(1,||theta||_F)
+                             of lambda_min (subgradient); <= 0 selects 1e-5                   */
+    int32_t max_sweeps;   /* Jacobi sweep cap of the FP32 eigensolver; <= 0 selects 15        */
+    int32_t use_graph;    /* nonzero: lrh_step replays a captured CUDA graph of iterations    */
+} lrh_options;
+
+typedef struct lrh_problem lrh_problem;
+
+typedef struct {
+    int32_t n_instances;
+    int32_t n_regions;            /* per instance                                              */
+    int32_t n_pairs;              /* per instance                                              */
+    int32_t max_region_sites;
+    int64_t msg_elems;            /* complex entries of one instance's message array           */
+    double  lambda_G;             /* Lambda_G of the L_hat rule (Delta_G + d at level 1,
+                                     max_{e->f} m_f + m_e D_e/D_f otherwise; Thms 5 and 7)     */
+    double  gamma_G;              /* Gamma_G = sum_e log D_e (smoothing-error lemma)           */
+    int64_t iteration;            /* iterations run since creation                             */
+    int32_t n_classes;            /* region size classes present                               */
+    int32_t class_sites[8];       /* k of each class                                           */
+    int32_t class_regions[8];     /* regions per instance of each class                        */
+    uint64_t sweeps[8];           /* cumulative FP32 Jacobi sweeps x regions, per class        */
+} lrh_info;
+
+/* ---------------------------------------------------------------- entry points */
+
+/* Build the region poset, place and embed the terms, allocate device state and zero the
+ * messages (Alg. 1 / Alg. 2 initialisation nu = zeta = 0, theta_0 = 1).  `stream` is a
+ * cudaStream_t (or NULL) on the current device.  On failure *out is NULL. */
+int lrh_create(const lrh_problem_desc* desc, const lrh_options* opts, void* stream,
+               lrh_problem** out);
+
+/* Free all host and device memory of the problem (NULL is accepted). */
+void lrh_destroy(lrh_problem* p);
+
+/* Sizes, constants and counters (host only, no synchronisation). */
+int lrh_get_info(const lrh_problem* p, lrh_info* info);
+
+/* Pair table in pair order: parent, child region ids and the complex offset of each
+ * message inside one instance's message array.  Each output may be NULL; arrays hold
+ * lrh_info.n_pairs entries. */
+int lrh_get_pairs(const lrh_problem* p, int32_t* parent, int32_t* child, int64_t* msg_off);
+
+/* Replace the options (beta / L_hat / alpha / rule / tolerances).  Stream-ordered. */
+int lrh_set_options(lrh_problem* p, const lrh_options* opts);
+
+/* Start a new smoothing stage: theta = 1 and zeta = nu (beta-continuation restart), and
+ * reset the step counter t used by LRH_STEP_INV_SQRT. Stream-ordered. */
+int lrh_restart(lrh_problem* p);
+
+/* Run n_iters iterations of the selected algorithm (asynchronous). */
+int lrh_step(lrh_problem* p, int32_t n_iters);
+
+/* One region pass at the current point without updating any message: stores the per-region
+ * values and the gradient g (readable with LRH_MSG_GRAD / lrh_get_region_values).
+ * Alg. 2 evaluates at eta = (1-theta) nu + theta zeta, Alg. 1 at nu. Asynchronous. */
+int lrh_evaluate(lrh_problem* p);
+
+/* Enqueue only the region pass of one size class (regions with k_sites sites, all instances)
+ * at the current point, without any message update: assembly, FP32 eigendecomposition,
+ * state, partial traces and per-region values of that class.  Used to time the dominant
+ * kernel of an iteration on the problem's stream.  Returns LRH_EINVAL if no region has
+ * k_sites sites. Asynchronous. */
+int lrh_launch_region_pass(lrh_problem* p, int32_t k_sites);
+
+/* Per-instance bound of the requested kind into out[n_instances] (host). Synchronises. */
+int lrh_bound(lrh_problem* p, int32_t kind, double* out);
+
+/* Per-region values [n_instances][n_regions] (host): kind LRH_BOUND_LAST gives the FP32
+ * pass values (F_beta or lambda_min), LRH_BOUND_CERTIFIED the FP64 lambda_min of the last
+ * certification. Synchronises. */
+int lrh_get_region_values(lrh_problem* p, int32_t kind, double* out);
+
+/* Copy a message-like array out of / into the library.  `bytes` must equal
+ * n_instances * msg_elems * 8.  dst/src is a device pointer when *_is_device is nonzero.
+ * lrh_set_messages rejects LRH_MSG_GRAD and symmetrises nothing: the caller provides
+ * Hermitian blocks. Stream-ordered (get synchronises when dst is on the host). */
+int lrh_get_messages(lrh_problem* p, int32_t which, void* dst, int64_t bytes, int32_t dst_is_device);
+int lrh_set_messages(lrh_problem* p, int32_t which, const void* src, int64_t bytes, int32_t src_is_device);
+
+/* Wait for the problem's stream and report any device-side numeric error (LRH_ENUMERIC). */
+int lrh_synchronize(lrh_problem* p);
+
+/* Static message for an error code, and the thread-local detail of the last failure. */
+const char* lrh_strerror(int code);
+const char* lrh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRH_H */

@@ -1,0 +1,116 @@
+"""ctypes declarations of the C ABI in include/lrh.h (argument marshalling only).
+
+Loading fails loudly when ``liblrh.so`` has not been built: there is no CPU
+fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblrh.so")
+
+LRH_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOTHERM", -3: "EPOSET", -4: "ENOMEM", -5: "ECUDA",
+          -6: "ETIMEOUT", -7: "ENUMERIC", -8: "EUNSUPPORTED"}
+SUBGRADIENT, NESTEROV = 0, 1
+STEP_CONST, STEP_INV_SQRT = 0, 1
+MSG_NU, MSG_ZETA, MSG_NU_BEST, MSG_GRAD = 0, 1, 2, 3
+BOUND_CERTIFIED, BOUND_LAST, BOUND_BEST = 0, 1, 2
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [
+        ("n_sites", C.c_int32),
+        ("n_regions", C.c_int32),
+        ("region_ptr", C.POINTER(C.c_int64)),
+        ("region_sites", C.POINTER(C.c_int32)),
+        ("n_terms", C.c_int32),
+        ("term_ptr", C.POINTER(C.c_int64)),
+        ("term_sites", C.POINTER(C.c_int32)),
+        ("term_mat_off", C.POINTER(C.c_int64)),
+        ("term_mat_total", C.c_int64),
+        ("term_mats", C.POINTER(C.c_double)),
+        ("n_instances", C.c_int32),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("variant", C.c_int32),
+        ("step_rule", C.c_int32),
+        ("alpha", C.c_double),
+        ("beta", C.c_double),
+        ("lhat", C.c_double),
+        ("degen_tol", C.c_double),
+        ("max_sweeps", C.c_int32),
+        ("use_graph", C.c_int32),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("n_instances", C.c_int32),
+        ("n_regions", C.c_int32),
+        ("n_pairs", C.c_int32),
+        ("max_region_sites", C.c_int32),
+        ("msg_elems", C.c_int64),
+        ("lambda_G", C.c_double),
+        ("gamma_G", C.c_double),
+        ("iteration", C.c_int64),
+        ("n_classes", C.c_int32),
+        ("class_sites", C.c_int32 * 8),
+        ("class_regions", C.c_int32 * 8),
+        ("sweeps", C.c_uint64 * 8),
+    ]
+
+
+class LrhError(RuntimeError):
+    def __init__(self, code: int, fn: str, detail: str):
+        super().__init__(f"{fn} failed: {ERRORS.get(code, code)} ({detail})")
+        self.code = code
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "lrh_create": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(Options), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "lrh_destroy": (None, [C.c_void_p]),
+    "lrh_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "lrh_get_pairs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lrh_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "lrh_restart": (C.c_int, [C.c_void_p]),
+    "lrh_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lrh_evaluate": (C.c_int, [C.c_void_p]),
+    "lrh_launch_region_pass": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lrh_bound": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "lrh_get_region_values": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "lrh_get_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
+    "lrh_set_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
+    "lrh_synchronize": (C.c_int, [C.c_void_p]),
+    "lrh_strerror": (C.c_char_p, [C.c_int]),
+    "lrh_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load liblrh.so (built in-tree by ``paper_2609_40336_b300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2609_40336_b300.build`")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(code: int, fn: str) -> None:
+    if code != LRH_OK:
+        detail = load().lrh_last_error().decode(errors="replace")
+        raise LrhError(code, fn, detail)

@@ -1,0 +1,614 @@
+// Host side of the C ABI declared in include/lrh.h: region poset (covering pairs of the
+// inclusion order, Sec. 4.2), term placement and embedding, device state, and the
+// iteration driver (per-iteration kernel sequence, optionally replayed as a CUDA graph).
+#include "../../include/lrh.h"
+#include "lrh_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <limits>
+#include <memory>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+using namespace lrh;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define LRH_CK(call)                                                                           \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(LRH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+struct VecHash {
+    size_t operator()(const std::vector<int32_t>& v) const {
+        uint64_t h = 1469598103934665603ull;
+        for (int32_t x : v) { h ^= (uint64_t)(uint32_t)x; h *= 1099511628211ull; }
+        return (size_t)h;
+    }
+};
+
+constexpr int kMaxSites = 7;     // region size limit of the data layout (D <= 128)
+constexpr int kMaxKernelSites = 5;  // sizes with a region-pass kernel in this build (D <= 32)
+constexpr int kGraphChunk = 8;   // iterations per captured graph (even: parity returns to 0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev); else prev = -1;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+struct lrh_problem {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    lrh_options opt{};
+    double lhat_eff = 1.0;
+    int32_t n_inst = 1, n_regions = 0, n_pairs = 0, max_k = 0;
+    int64_t msg_elems = 0, h_elems = 0, rho_elems = 0;
+    double lambda_G = 0, gamma_G = 0;
+    int64_t iteration = 0;
+    bool stepped_since_restart = false;
+    std::vector<int32_t> pair_parent, pair_child;
+    std::vector<int64_t> pair_off;
+    // size classes: k -> device list of region ids
+    std::vector<int> class_k;
+    std::vector<int32_t> class_count;
+    std::vector<int32_t*> class_list;
+    // device memory
+    DevProblem P{};
+    std::vector<void*> allocs;
+    double* h_pinned = nullptr;   // host staging for bound / values
+    int64_t h_pinned_len = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+
+    template <typename T>
+    int dalloc(T** ptr, int64_t count) {
+        *ptr = nullptr;
+        if (count <= 0) count = 1;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)count * sizeof(T));
+        if (e != cudaSuccess) return fail(LRH_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        allocs.push_back(p);
+        *ptr = static_cast<T*>(p);
+        return LRH_OK;
+    }
+    ~lrh_problem() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : allocs) cudaFree(p);
+        if (h_pinned) cudaFreeHost(h_pinned);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+int validate_options(const lrh_options* o) {
+    if (!o) return fail(LRH_EINVAL, "options is NULL");
+    if (o->variant != LRH_SUBGRADIENT && o->variant != LRH_NESTEROV) return fail(LRH_EINVAL, "unknown variant");
+    if (o->step_rule != LRH_STEP_CONST && o->step_rule != LRH_STEP_INV_SQRT) return fail(LRH_EINVAL, "unknown step rule");
+    if (o->variant == LRH_SUBGRADIENT && !(o->alpha > 0.0)) return fail(LRH_EINVAL, "alpha must be > 0");
+    if (o->variant == LRH_NESTEROV && !(o->beta > 0.0)) return fail(LRH_EINVAL, "beta must be > 0");
+    if (!std::isfinite(o->beta) || !std::isfinite(o->alpha) || !std::isfinite(o->lhat)) return fail(LRH_EINVAL, "non-finite option");
+    return LRH_OK;
+}
+
+int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
+    const lrh_options& o = p->opt;
+    p->lhat_eff = o.lhat > 0.0 ? o.lhat : (o.beta > 0.0 ? o.beta * p->lambda_G / 2.0 : 1.0);
+    const double degen = o.degen_tol > 0.0 ? o.degen_tol : 1e-5;
+    const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
+    LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), theta, t, set_theta_t ? 1 : 0, o.beta,
+                            1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, p->stream));
+    return LRH_OK;
+}
+
+int run_iteration(lrh_problem* p, int par) {
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        LRH_CK(launch_region_pass(p->P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+    if (p->opt.variant == LRH_SUBGRADIENT) LRH_CK(launch_reduce(p->P, p->P.val, 1, p->stream));
+    LRH_CK(launch_update(p->P, par, UPD_STEP, p->stream));
+    return LRH_OK;
+}
+
+int build_graph(lrh_problem* p) {
+    LRH_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LRH_OK;
+    for (int i = 0; i < kGraphChunk && rc == LRH_OK; ++i) rc = run_iteration(p, i & 1);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (rc != LRH_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return fail(LRH_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    p->graph = g;
+    LRH_CK(cudaGraphInstantiate(&p->graph_exec, g, 0));
+    return LRH_OK;
+}
+
+int read_err(lrh_problem* p) {
+    int32_t h = 0;
+    LRH_CK(cudaMemcpyAsync(&h, p->P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    if (h & DEV_ERR_NUMERIC) return fail(LRH_ENUMERIC, "a non-finite eigenvalue, value or message was produced");
+    return LRH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lrh_strerror(int code) {
+    switch (code) {
+        case LRH_OK: return "ok";
+        case LRH_EINVAL: return "invalid argument";
+        case LRH_ENOTHERM: return "term matrix is not Hermitian";
+        case LRH_EPOSET: return "invalid region family";
+        case LRH_ENOMEM: return "out of memory";
+        case LRH_ECUDA: return "CUDA error";
+        case LRH_ETIMEOUT: return "device wait timed out";
+        case LRH_ENUMERIC: return "non-finite value";
+        case LRH_EUNSUPPORTED: return "unsupported region size";
+        default: return "unknown error";
+    }
+}
+
+const char* lrh_last_error(void) { return g_last_error.c_str(); }
+
+int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream, lrh_problem** out) {
+    if (!out) return fail(LRH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(LRH_EINVAL, "desc is NULL");
+    int rc = validate_options(opts);
+    if (rc) return rc;
+    if (d->n_sites <= 0 || d->n_regions <= 0 || d->n_instances <= 0 || d->n_terms < 0)
+        return fail(LRH_EINVAL, "n_sites, n_regions, n_instances must be positive");
+    if (!d->region_ptr || !d->region_sites) return fail(LRH_EINVAL, "region arrays are NULL");
+    if (d->n_terms > 0 && (!d->term_ptr || !d->term_sites || !d->term_mat_off || !d->term_mats))
+        return fail(LRH_EINVAL, "term arrays are NULL");
+
+    // ---------------------------------------------------------------- regions
+    const int R = d->n_regions;
+    std::vector<std::vector<int32_t>> regs(R);
+    std::unordered_map<std::vector<int32_t>, int, VecHash> index;
+    index.reserve((size_t)R * 2);
+    int maxk = 0;
+    for (int e = 0; e < R; ++e) {
+        const int64_t b = d->region_ptr[e], en = d->region_ptr[e + 1];
+        const int64_t k = en - b;
+        if (k < 1 || k > kMaxSites) return fail(LRH_EINVAL, "region " + std::to_string(e) + " has " + std::to_string(k) + " sites (1..7 allowed)");
+        regs[e].assign(d->region_sites + b, d->region_sites + en);
+        for (int64_t i = 0; i < k; ++i) {
+            if (regs[e][i] < 0 || regs[e][i] >= d->n_sites) return fail(LRH_EINVAL, "region site out of range");
+            if (i && regs[e][i] <= regs[e][i - 1]) return fail(LRH_EINVAL, "region sites must be sorted and unique");
+        }
+        if (!index.emplace(regs[e], e).second) return fail(LRH_EPOSET, "duplicate region " + std::to_string(e));
+        maxk = std::max<int>(maxk, (int)k);
+    }
+    if (maxk > kMaxKernelSites)
+        return fail(LRH_EUNSUPPORTED, "regions of " + std::to_string(maxk) + " sites need the D > 32 kernels, not in this build");
+
+    // covering pairs (children of e: proper sub-regions with no region strictly between)
+    std::vector<std::vector<std::pair<int, int>>> kids(R);   // (child, index-bit mask)
+    for (int e = 0; e < R; ++e) {
+        const int k = (int)regs[e].size();
+        std::vector<std::pair<int, int>> subs;   // (region, position mask: bit p = position p)
+        std::vector<int32_t> tmp;
+        for (int m = 1; m < (1 << k) - 1; ++m) {
+            tmp.clear();
+            for (int p = 0; p < k; ++p) if (m >> p & 1) tmp.push_back(regs[e][p]);
+            auto it = index.find(tmp);
+            if (it != index.end()) subs.emplace_back(it->second, m);
+        }
+        for (auto& f : subs) {
+            bool covered = true;
+            for (auto& gq : subs)
+                if (gq.second != f.second && (f.second & gq.second) == f.second) { covered = false; break; }
+            if (!covered) continue;
+            int im = 0;
+            for (int p = 0; p < k; ++p) if (f.second >> p & 1) im |= 1 << (k - 1 - p);
+            kids[e].emplace_back(f.first, im);
+        }
+        std::sort(kids[e].begin(), kids[e].end());
+    }
+    lrh_problem* p = new (std::nothrow) lrh_problem();
+    if (!p) return fail(LRH_ENOMEM, "host allocation");
+    std::unique_ptr<lrh_problem> guard(p);
+    p->opt = *opts;
+    p->n_inst = d->n_instances;
+    p->n_regions = R;
+    p->max_k = maxk;
+    cudaGetDevice(&p->device);
+
+    std::vector<PairInfo> pairs;
+    std::vector<std::vector<int32_t>> parent_of(R);
+    std::vector<RegionInfo> rinfo(R);
+    std::vector<int32_t> child_pairs, parent_pairs;
+    int64_t moff = 0;
+    for (int e = 0; e < R; ++e) {
+        rinfo[e].child_begin = (int32_t)child_pairs.size();
+        for (auto& f : kids[e]) {
+            PairInfo pi;
+            pi.off = moff;
+            pi.parent = e;
+            pi.child = f.first;
+            pi.mask = f.second;
+            pi.kf = (int32_t)regs[f.first].size();
+            moff += (int64_t)1 << (2 * pi.kf);
+            parent_of[f.first].push_back((int32_t)pairs.size());
+            child_pairs.push_back((int32_t)pairs.size());
+            pairs.push_back(pi);
+        }
+        rinfo[e].child_end = (int32_t)child_pairs.size();
+    }
+    for (int e = 0; e < R; ++e) {
+        rinfo[e].parent_begin = (int32_t)parent_pairs.size();
+        for (int32_t q : parent_of[e]) parent_pairs.push_back(q);
+        rinfo[e].parent_end = (int32_t)parent_pairs.size();
+    }
+    p->n_pairs = (int32_t)pairs.size();
+    p->msg_elems = moff;
+    for (auto& pi : pairs) { p->pair_parent.push_back(pi.parent); p->pair_child.push_back(pi.child); p->pair_off.push_back(pi.off); }
+
+    // Lambda_G and Gamma_G
+    bool level1 = maxk <= 2;
+    for (auto& pi : pairs) if (!(regs[pi.parent].size() == 2 && pi.kf == 1)) level1 = false;
+    if (level1) {
+        size_t deg = 0;
+        for (int e = 0; e < R; ++e) deg = std::max(deg, parent_of[e].size());
+        p->lambda_G = (double)deg + 2.0;
+    } else {
+        double best = 0;
+        for (auto& pi : pairs) {
+            const double me = (double)(parent_of[pi.parent].size() + kids[pi.parent].size());
+            const double mf = (double)(parent_of[pi.child].size() + kids[pi.child].size());
+            const double ratio = std::ldexp(1.0, (int)regs[pi.parent].size() - pi.kf);
+            best = std::max(best, mf + me * ratio);
+        }
+        p->lambda_G = best;
+    }
+    p->gamma_G = 0;
+    for (int e = 0; e < R; ++e) p->gamma_G += (double)regs[e].size() * std::log(2.0);
+
+    // ---------------------------------------------------------------- terms
+    std::vector<std::vector<int32_t>> by_site(d->n_sites);
+    for (int e = 0; e < R; ++e) for (int32_t s : regs[e]) by_site[s].push_back(e);
+    std::vector<int> place(d->n_terms, -1);
+    std::vector<char> has_term(R, 0);
+    for (int t = 0; t < d->n_terms; ++t) {
+        const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
+        if (en - b < 1 || en - b > kMaxSites) return fail(LRH_EINVAL, "term " + std::to_string(t) + " has a bad site count");
+        std::vector<int32_t> ts(d->term_sites + b, d->term_sites + en);
+        for (size_t i = 0; i < ts.size(); ++i) {
+            if (ts[i] < 0 || ts[i] >= d->n_sites) return fail(LRH_EINVAL, "term site out of range");
+            if (i && ts[i] <= ts[i - 1]) return fail(LRH_EINVAL, "term sites must be sorted and unique");
+        }
+        int bestr = -1;
+        for (int32_t e : by_site[ts[0]]) {
+            if (!std::includes(regs[e].begin(), regs[e].end(), ts.begin(), ts.end())) continue;
+            if (bestr < 0 || regs[e].size() < regs[bestr].size() || (regs[e].size() == regs[bestr].size() && e < bestr)) bestr = e;
+        }
+        if (bestr < 0) return fail(LRH_EPOSET, "term " + std::to_string(t) + " fits in no region");
+        place[t] = bestr;
+        has_term[bestr] = 1;
+        const int64_t Dt = (int64_t)1 << ts.size();
+        const int64_t off = d->term_mat_off[t];
+        if (off < 0 || off + Dt * Dt > d->term_mat_total) return fail(LRH_EINVAL, "term matrix offset out of range");
+        for (int i = 0; i < d->n_instances; ++i) {
+            const double* m = d->term_mats + 2 * ((int64_t)i * d->term_mat_total + off);
+            double mx = 0;
+            for (int64_t a = 0; a < Dt * Dt; ++a) mx = std::max(mx, std::fabs(m[2 * a]) + std::fabs(m[2 * a + 1]));
+            for (int64_t a = 0; a < Dt; ++a)
+                for (int64_t c = 0; c < Dt; ++c) {
+                    const double dr = m[2 * (a * Dt + c)] - m[2 * (c * Dt + a)];
+                    const double di = m[2 * (a * Dt + c) + 1] + m[2 * (c * Dt + a) + 1];
+                    if (!std::isfinite(dr) || !std::isfinite(di)) return fail(LRH_EINVAL, "non-finite term entry");
+                    if (std::fabs(dr) + std::fabs(di) > 1e-10 * std::max(1.0, mx))
+                        return fail(LRH_ENOTHERM, "term " + std::to_string(t) + " is not Hermitian");
+                }
+        }
+    }
+    int64_t hoff = 0, roff = 0;
+    for (int e = 0; e < R; ++e) {
+        const int64_t D = (int64_t)1 << regs[e].size();
+        rinfo[e].h_off = has_term[e] ? hoff : -1;
+        if (has_term[e]) hoff += D * D;
+        rinfo[e].rho_off = parent_of[e].empty() ? -1 : roff;
+        if (!parent_of[e].empty()) roff += D * D;
+    }
+    p->h_elems = hoff;
+    p->rho_elems = roff;
+    std::vector<double> h64((size_t)(2 * p->n_inst * std::max<int64_t>(hoff, 1)), 0.0);
+    for (int t = 0; t < d->n_terms; ++t) {
+        const int e = place[t];
+        const int k = (int)regs[e].size();
+        const int64_t D = (int64_t)1 << k;
+        const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
+        int M = 0;
+        for (int64_t i = b; i < en; ++i) {
+            const int pos = (int)(std::find(regs[e].begin(), regs[e].end(), d->term_sites[i]) - regs[e].begin());
+            M |= 1 << (k - 1 - pos);
+        }
+        auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 7; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
+        const int64_t Dt = (int64_t)1 << (en - b);
+        for (int inst = 0; inst < p->n_inst; ++inst) {
+            const double* m = d->term_mats + 2 * ((int64_t)inst * d->term_mat_total + d->term_mat_off[t]);
+            double* h = h64.data() + 2 * ((int64_t)inst * hoff + rinfo[e].h_off);
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    if (((i ^ j) & ~M) != 0) continue;
+                    const int64_t src = pext(i, M) * Dt + pext(j, M);
+                    h[2 * (i * D + j)] += m[2 * src];
+                    h[2 * (i * D + j) + 1] += m[2 * src + 1];
+                }
+        }
+    }
+
+    // ---------------------------------------------------------------- device state
+    LRH_CK(prepare_kernels());
+    if (stream) {
+        p->stream = (cudaStream_t)stream;
+    } else {
+        LRH_CK(cudaStreamCreate(&p->stream));   // blocking stream: ordered with the legacy default stream
+        p->own_stream = true;
+    }
+    DevProblem& P = p->P;
+    P.n_inst = p->n_inst;
+    P.n_regions = R;
+    P.n_pairs = p->n_pairs;
+    P.h_elems = hoff;
+    P.rho_elems = roff;
+    P.msg_elems = moff;
+    const int64_t NI = p->n_inst;
+    RegionInfo* dreg; PairInfo* dpair; int32_t *dcp, *dpp;
+    if ((rc = p->dalloc(&dreg, R)) || (rc = p->dalloc(&dpair, p->n_pairs)) || (rc = p->dalloc(&dcp, p->n_pairs)) ||
+        (rc = p->dalloc(&dpp, p->n_pairs)))
+        return rc;
+    float2* h32; double2* dh64;
+    if ((rc = p->dalloc(&h32, NI * hoff)) || (rc = p->dalloc(&dh64, NI * hoff))) return rc;
+    if ((rc = p->dalloc(&P.nu, NI * moff)) || (rc = p->dalloc(&P.zeta, NI * moff)) || (rc = p->dalloc(&P.nu_best, NI * moff)) ||
+        (rc = p->dalloc(&P.tr, NI * moff)) || (rc = p->dalloc(&P.grad, NI * moff)) || (rc = p->dalloc(&P.rho, NI * roff)))
+        return rc;
+    if ((rc = p->dalloc(&P.val, NI * R)) || (rc = p->dalloc(&P.val64, NI * R)) || (rc = p->dalloc(&P.q_sum, NI)) ||
+        (rc = p->dalloc(&P.q_best, NI)) || (rc = p->dalloc(&P.best_flag, NI)) || (rc = p->dalloc(&P.st, 1)) ||
+        (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)))
+        return rc;
+    P.reg = dreg; P.pair = dpair; P.child_pairs = dcp; P.parent_pairs = dpp; P.h32 = h32; P.h64 = dh64;
+    LRH_CK(cudaMemcpy(dreg, rinfo.data(), sizeof(RegionInfo) * R, cudaMemcpyHostToDevice));
+    if (p->n_pairs) {
+        LRH_CK(cudaMemcpy(dpair, pairs.data(), sizeof(PairInfo) * pairs.size(), cudaMemcpyHostToDevice));
+        LRH_CK(cudaMemcpy(dcp, child_pairs.data(), sizeof(int32_t) * child_pairs.size(), cudaMemcpyHostToDevice));
+        LRH_CK(cudaMemcpy(dpp, parent_pairs.data(), sizeof(int32_t) * parent_pairs.size(), cudaMemcpyHostToDevice));
+    }
+    if (hoff) {
+        std::vector<float> h32h(h64.size());
+        for (size_t i = 0; i < h64.size(); ++i) h32h[i] = (float)h64[i];
+        LRH_CK(cudaMemcpy(h32, h32h.data(), sizeof(float) * h32h.size(), cudaMemcpyHostToDevice));
+        LRH_CK(cudaMemcpy(dh64, h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice));
+    }
+    LRH_CK(cudaMemset(P.nu, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
+    LRH_CK(cudaMemset(P.zeta, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
+    LRH_CK(cudaMemset(P.nu_best, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
+    LRH_CK(cudaMemset(P.grad, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
+    LRH_CK(cudaMemset(P.best_flag, 0, sizeof(int32_t) * NI));
+    LRH_CK(cudaMemset(P.err, 0, sizeof(int32_t)));
+    LRH_CK(cudaMemset(P.sweeps, 0, sizeof(unsigned long long) * 8));
+    LRH_CK(cudaMemset(P.val64, 0, sizeof(double) * NI * R));
+    LRH_CK(cudaMemset(P.val, 0, sizeof(double) * NI * R));
+    LRH_CK(cudaMemset(P.st, 0, sizeof(IterState)));
+    {
+        std::vector<double> ninf(NI, -std::numeric_limits<double>::infinity());
+        LRH_CK(cudaMemcpy(P.q_best, ninf.data(), sizeof(double) * NI, cudaMemcpyHostToDevice));
+    }
+    // size classes
+    for (int k = 1; k <= kMaxSites; ++k) {
+        std::vector<int32_t> lst;
+        for (int e = 0; e < R; ++e) if ((int)regs[e].size() == k) lst.push_back(e);
+        if (lst.empty()) continue;
+        int32_t* dl;
+        if ((rc = p->dalloc(&dl, (int64_t)lst.size()))) return rc;
+        LRH_CK(cudaMemcpy(dl, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice));
+        p->class_k.push_back(k);
+        p->class_count.push_back((int32_t)lst.size());
+        p->class_list.push_back(dl);
+    }
+    p->h_pinned_len = std::max<int64_t>(NI * R, 16);
+    LRH_CK(cudaMallocHost(&p->h_pinned, sizeof(double) * p->h_pinned_len));
+    if ((rc = push_state(p, true, 1.0, 0.0))) return rc;
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    *out = guard.release();
+    return LRH_OK;
+}
+
+void lrh_destroy(lrh_problem* p) {
+    if (!p) return;
+    DeviceGuard dg(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    delete p;
+}
+
+int lrh_get_info(const lrh_problem* p, lrh_info* info) {
+    if (!p || !info) return fail(LRH_EINVAL, "NULL argument");
+    DeviceGuard dg(p->device);
+    std::memset(info, 0, sizeof(*info));
+    info->n_instances = p->n_inst;
+    info->n_regions = p->n_regions;
+    info->n_pairs = p->n_pairs;
+    info->max_region_sites = p->max_k;
+    info->msg_elems = p->msg_elems;
+    info->lambda_G = p->lambda_G;
+    info->gamma_G = p->gamma_G;
+    info->iteration = p->iteration;
+    info->n_classes = (int32_t)p->class_k.size();
+    unsigned long long sw[8] = {0};
+    LRH_CK(cudaMemcpyAsync(sw, p->P.sweeps, sizeof(sw), cudaMemcpyDeviceToHost, p->stream));
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    for (size_t c = 0; c < p->class_k.size() && c < 8; ++c) {
+        info->class_sites[c] = p->class_k[c];
+        info->class_regions[c] = p->class_count[c];
+        info->sweeps[c] = sw[p->class_k[c]];
+    }
+    return LRH_OK;
+}
+
+int lrh_get_pairs(const lrh_problem* p, int32_t* parent, int32_t* child, int64_t* msg_off) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (parent) std::copy(p->pair_parent.begin(), p->pair_parent.end(), parent);
+    if (child) std::copy(p->pair_child.begin(), p->pair_child.end(), child);
+    if (msg_off) std::copy(p->pair_off.begin(), p->pair_off.end(), msg_off);
+    return LRH_OK;
+}
+
+int lrh_set_options(lrh_problem* p, const lrh_options* opts) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    int rc = validate_options(opts);
+    if (rc) return rc;
+    DeviceGuard dg(p->device);
+    p->opt = *opts;
+    return push_state(p, false, 0.0, 0.0);
+}
+
+int lrh_restart(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    int rc = push_state(p, true, 1.0, 0.0);
+    if (rc) return rc;
+    LRH_CK(cudaMemcpyAsync(p->P.zeta, p->P.nu, sizeof(float2) * p->n_inst * p->msg_elems, cudaMemcpyDeviceToDevice, p->stream));
+    return LRH_OK;
+}
+
+int lrh_step(lrh_problem* p, int32_t n_iters) {
+    if (!p || n_iters < 0) return fail(LRH_EINVAL, "bad arguments to lrh_step");
+    DeviceGuard dg(p->device);
+    int rc;
+    while (n_iters > 0) {
+        if (p->opt.use_graph && (p->iteration & 1) == 0 && n_iters >= kGraphChunk) {
+            if (!p->graph_exec && (rc = build_graph(p))) return rc;
+            LRH_CK(cudaGraphLaunch(p->graph_exec, p->stream));
+            p->iteration += kGraphChunk;
+            n_iters -= kGraphChunk;
+        } else {
+            if ((rc = run_iteration(p, (int)(p->iteration & 1)))) return rc;
+            p->iteration += 1;
+            n_iters -= 1;
+        }
+    }
+    return LRH_OK;
+}
+
+int lrh_evaluate(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    const int par = (int)(p->iteration & 1);
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        LRH_CK(launch_region_pass(p->P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+    LRH_CK(launch_update(p->P, par, UPD_GRAD_ONLY, p->stream));
+    return LRH_OK;
+}
+
+int lrh_launch_region_pass(lrh_problem* p, int32_t k_sites) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        if (p->class_k[c] == k_sites) {
+            LRH_CK(launch_region_pass(p->P, k_sites, p->class_list[c], p->class_count[c], (int)(p->iteration & 1), p->stream));
+            return LRH_OK;
+        }
+    return fail(LRH_EINVAL, "no region class with " + std::to_string(k_sites) + " sites");
+}
+
+int lrh_bound(lrh_problem* p, int32_t kind, double* out) {
+    if (!p || !out) return fail(LRH_EINVAL, "NULL argument");
+    DeviceGuard dg(p->device);
+    const int64_t NI = p->n_inst;
+    if (kind == LRH_BOUND_CERTIFIED) {
+        const float2* msg = p->opt.variant == LRH_SUBGRADIENT ? p->P.nu_best : p->P.nu;
+        for (size_t c = 0; c < p->class_k.size(); ++c)
+            LRH_CK(launch_certify(p->P, p->class_k[c], p->class_list[c], p->class_count[c], msg, p->stream));
+        LRH_CK(launch_reduce(p->P, p->P.val64, 0, p->stream));
+        LRH_CK(cudaMemcpyAsync(p->h_pinned, p->P.q_sum, sizeof(double) * NI, cudaMemcpyDeviceToHost, p->stream));
+    } else if (kind == LRH_BOUND_LAST) {
+        LRH_CK(launch_reduce(p->P, p->P.val, 0, p->stream));
+        LRH_CK(cudaMemcpyAsync(p->h_pinned, p->P.q_sum, sizeof(double) * NI, cudaMemcpyDeviceToHost, p->stream));
+    } else if (kind == LRH_BOUND_BEST) {
+        LRH_CK(cudaMemcpyAsync(p->h_pinned, p->P.q_best, sizeof(double) * NI, cudaMemcpyDeviceToHost, p->stream));
+    } else {
+        return fail(LRH_EINVAL, "unknown bound kind");
+    }
+    int rc = read_err(p);
+    if (rc) return rc;
+    std::copy(p->h_pinned, p->h_pinned + NI, out);
+    return LRH_OK;
+}
+
+int lrh_get_region_values(lrh_problem* p, int32_t kind, double* out) {
+    if (!p || !out) return fail(LRH_EINVAL, "NULL argument");
+    DeviceGuard dg(p->device);
+    const double* src = kind == LRH_BOUND_CERTIFIED ? p->P.val64 : (kind == LRH_BOUND_LAST ? p->P.val : nullptr);
+    if (!src) return fail(LRH_EINVAL, "kind must be LRH_BOUND_LAST or LRH_BOUND_CERTIFIED");
+    LRH_CK(cudaMemcpyAsync(out, src, sizeof(double) * p->n_inst * p->n_regions, cudaMemcpyDeviceToHost, p->stream));
+    return read_err(p);
+}
+
+static float2* msg_array(lrh_problem* p, int which) {
+    switch (which) {
+        case LRH_MSG_NU: return p->P.nu;
+        case LRH_MSG_ZETA: return p->P.zeta;
+        case LRH_MSG_NU_BEST: return p->P.nu_best;
+        case LRH_MSG_GRAD: return p->P.grad;
+        default: return nullptr;
+    }
+}
+
+int lrh_get_messages(lrh_problem* p, int32_t which, void* dst, int64_t bytes, int32_t dst_is_device) {
+    if (!p || !dst) return fail(LRH_EINVAL, "NULL argument");
+    float2* src = msg_array(p, which);
+    if (!src) return fail(LRH_EINVAL, "unknown message array");
+    const int64_t need = (int64_t)sizeof(float2) * p->n_inst * p->msg_elems;
+    if (bytes != need) return fail(LRH_EINVAL, "bytes must be n_instances * msg_elems * 8 = " + std::to_string(need));
+    DeviceGuard dg(p->device);
+    if (need == 0) return LRH_OK;
+    LRH_CK(cudaMemcpyAsync(dst, src, (size_t)need, dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    if (!dst_is_device) LRH_CK(cudaStreamSynchronize(p->stream));
+    return LRH_OK;
+}
+
+int lrh_set_messages(lrh_problem* p, int32_t which, const void* src, int64_t bytes, int32_t src_is_device) {
+    if (!p || !src) return fail(LRH_EINVAL, "NULL argument");
+    if (which == LRH_MSG_GRAD) return fail(LRH_EINVAL, "the gradient array is read only");
+    float2* dst = msg_array(p, which);
+    if (!dst) return fail(LRH_EINVAL, "unknown message array");
+    const int64_t need = (int64_t)sizeof(float2) * p->n_inst * p->msg_elems;
+    if (bytes != need) return fail(LRH_EINVAL, "bytes must be n_instances * msg_elems * 8 = " + std::to_string(need));
+    DeviceGuard dg(p->device);
+    if (need == 0) return LRH_OK;
+    LRH_CK(cudaMemcpyAsync(dst, src, (size_t)need, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+    if (!src_is_device) LRH_CK(cudaStreamSynchronize(p->stream));
+    return LRH_OK;
+}
+
+int lrh_synchronize(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    return read_err(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal device-side layout of an lrh problem (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lrh {
+
+// One region of the cluster family (identical for every batched instance).
+struct RegionInfo {
+    int64_t h_off;         // complex offset of D x D h_e in one instance's h arena, -1 = no term
+    int64_t rho_off;       // complex offset of D x D rho_e in one instance's state arena, -1 = no parent
+    int32_t child_begin;   // [child_begin, child_end) into child_pairs: pairs e->f with e = this
+    int32_t child_end;
+    int32_t parent_begin;  // [parent_begin, parent_end) into parent_pairs: pairs g->e with e = this
+    int32_t parent_end;
+};
+
+// One covering pair e -> f.
+struct PairInfo {
+    int64_t off;           // complex offset of the D_f x D_f message block in one instance
+    int32_t parent;
+    int32_t child;
+    int32_t mask;          // bits of the parent's basis index that carry the child's sites
+    int32_t kf;            // child sites
+};
+
+// Scalars of the iteration, double-buffered by iteration parity so that a captured
+// graph of iterations needs no host-side argument changes.
+struct IterState {
+    double theta[2];       // Alg. 2 theta_k
+    double t[2];           // iterations since the last restart (step-size rule)
+    double beta;
+    double inv_lhat;
+    double alpha;
+    double degen_tol;
+    int32_t variant;
+    int32_t step_rule;
+    int32_t max_sweeps;
+    int32_t pad;
+};
+
+// Error bits raised by kernels.
+enum : int32_t { DEV_ERR_NUMERIC = 1 };
+
+struct DevProblem {
+    int32_t n_inst;
+    int32_t n_regions;
+    int32_t n_pairs;
+    int32_t pad;
+    int64_t h_elems;       // complex entries per instance
+    int64_t rho_elems;
+    int64_t msg_elems;
+    const RegionInfo* reg;
+    const PairInfo* pair;
+    const int32_t* child_pairs;
+    const int32_t* parent_pairs;
+    const float2* h32;     // [n_inst][h_elems]
+    const double2* h64;    // [n_inst][h_elems]
+    float2* nu;            // [n_inst][msg_elems]
+    float2* zeta;
+    float2* nu_best;
+    float2* tr;            // Tr_{e\f} rho_e of the last pass, message layout
+    float2* rho;           // [n_inst][rho_elems] states of regions that have parents
+    float2* grad;          // gradient of the last lrh_evaluate
+    double* val;           // [n_inst][n_regions] per-region FP32 values of the last pass
+    double* val64;         // [n_inst][n_regions] per-region FP64 lambda_min of the last certify
+    double* q_sum;         // [n_inst] scratch sums
+    double* q_best;        // [n_inst]
+    int32_t* best_flag;    // [n_inst]
+    IterState* st;
+    int32_t* err;
+    unsigned long long* sweeps;   // [8] per size class (indexed by k)
+};
+
+// Kernel attributes (dynamic shared memory limits) for the current device; called once per
+// problem creation, outside any stream capture.
+cudaError_t prepare_kernels();
+
+// Launchers (lrh_kernels.cu).  All enqueue on `s` and return the launch status.
+cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* class_regions,
+                               int32_t class_count, int par, cudaStream_t s);
+cudaError_t launch_certify(const DevProblem& P, int k, const int32_t* class_regions,
+                           int32_t class_count, const float2* msg, cudaStream_t s);
+cudaError_t launch_update(const DevProblem& P, int par, int mode, cudaStream_t s);
+cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_best, cudaStream_t s);
+cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double t, int set_theta_t,
+                             double beta, double inv_lhat, double alpha, double degen_tol,
+                             int variant, int step_rule, int max_sweeps, cudaStream_t s);
+cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t s);
+
+// update modes
+enum : int { UPD_STEP = 0, UPD_GRAD_ONLY = 1 };
+
+}  // namespace lrh

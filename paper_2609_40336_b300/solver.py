@@ -1,0 +1,202 @@
+"""Python binding of the lrh C ABI: argument marshalling only.
+
+Every step of the solver runs in the CUDA library (``liblrh.so``); this module
+turns Python lists / numpy arrays into the flat host arrays of
+``lrh_problem_desc`` and wraps the handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib as L
+
+_VARIANTS = {"subgradient": L.SUBGRADIENT, "nesterov": L.NESTEROV}
+_RULES = {"const": L.STEP_CONST, "inv_sqrt": L.STEP_INV_SQRT}
+_MSGS = {"nu": L.MSG_NU, "zeta": L.MSG_ZETA, "nu_best": L.MSG_NU_BEST, "grad": L.MSG_GRAD}
+_BOUNDS = {"certified": L.BOUND_CERTIFIED, "last": L.BOUND_LAST, "best": L.BOUND_BEST}
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence[Sequence[int]],
+            term_mats: Sequence[np.ndarray]):
+    """Flat host arrays of lrh_problem_desc.  term_mats[t] has shape
+    (n_instances, 2^k, 2^k) or (2^k, 2^k)."""
+    region_ptr = np.zeros(len(regions) + 1, np.int64)
+    region_ptr[1:] = np.cumsum([len(r) for r in regions])
+    region_sites = np.ascontiguousarray([s for r in regions for s in r], np.int32)
+    term_ptr = np.zeros(len(term_sites) + 1, np.int64)
+    term_ptr[1:] = np.cumsum([len(t) for t in term_sites])
+    tsites = np.ascontiguousarray([s for t in term_sites for s in t], np.int32)
+    mats = [np.asarray(m) for m in term_mats]
+    mats = [m[None] if m.ndim == 2 else m for m in mats]
+    n_inst = mats[0].shape[0] if mats else 1
+    sizes = np.array([m.shape[1] * m.shape[2] for m in mats], np.int64)
+    off = np.zeros(len(mats), np.int64)
+    if len(mats):
+        off[1:] = np.cumsum(sizes)[:-1]
+    total = int(sizes.sum())
+    flat = np.zeros((n_inst, max(total, 1)), np.complex128)
+    for o, m in zip(off, mats):
+        if m.shape[0] != n_inst:
+            raise ValueError("all term matrices need the same number of instances")
+        flat[:, o:o + m.shape[1] * m.shape[2]] = m.reshape(n_inst, -1)
+    keep = dict(region_ptr=region_ptr, region_sites=region_sites, term_ptr=term_ptr, term_sites=tsites,
+                term_mat_off=off, term_mats=np.ascontiguousarray(flat).view(np.float64))
+    desc = L.ProblemDesc(n_sites=int(n_sites), n_regions=len(regions),
+                         region_ptr=_ptr(region_ptr, C.c_int64), region_sites=_ptr(region_sites, C.c_int32),
+                         n_terms=len(mats), term_ptr=_ptr(term_ptr, C.c_int64),
+                         term_sites=_ptr(tsites, C.c_int32), term_mat_off=_ptr(off, C.c_int64),
+                         term_mat_total=total, term_mats=_ptr(keep["term_mats"], C.c_double),
+                         n_instances=int(n_inst))
+    return desc, keep
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return C.c_void_p(0)
+
+
+class Solver:
+    """One (batched) relaxation problem on the GPU.
+
+    ``problem`` is any object with ``n_sites``, ``regions``, ``term_sites`` and
+    ``term_mats`` (see include/lrh.h for the conventions).
+    """
+
+    def __init__(self, problem, variant: str = "nesterov", beta: float = 1.0, lhat: Optional[float] = None,
+                 alpha: float = 1.0, step_rule: str = "inv_sqrt", degen_tol: float = 1e-5,
+                 max_sweeps: int = 15, use_graph: bool = True, stream=None):
+        self._lib = L.load()
+        self._h = C.c_void_p(0)
+        desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats)
+        self._opt = L.Options(variant=_VARIANTS[variant], step_rule=_RULES[step_rule], alpha=float(alpha),
+                              beta=float(beta), lhat=float(lhat) if lhat else 0.0, degen_tol=float(degen_tol),
+                              max_sweeps=int(max_sweeps), use_graph=int(bool(use_graph)))
+        st = _current_stream() if stream is None else C.c_void_p(int(stream))
+        L.check(self._lib.lrh_create(C.byref(desc), C.byref(self._opt), st, C.byref(self._h)), "lrh_create")
+        inf = self.info()
+        self.n_instances = inf["n_instances"]
+        self.n_regions = inf["n_regions"]
+        self.n_pairs = inf["n_pairs"]
+        self.msg_elems = inf["msg_elems"]
+        self.lambda_G = inf["lambda_G"]
+        self.gamma_G = inf["gamma_G"]
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self) -> None:
+        if self._h and self._h.value:
+            self._lib.lrh_destroy(self._h)
+            self._h = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ queries
+    def info(self) -> dict:
+        inf = L.Info()
+        L.check(self._lib.lrh_get_info(self._h, C.byref(inf)), "lrh_get_info")
+        nc = inf.n_classes
+        return dict(n_instances=inf.n_instances, n_regions=inf.n_regions, n_pairs=inf.n_pairs,
+                    max_region_sites=inf.max_region_sites, msg_elems=inf.msg_elems,
+                    lambda_G=inf.lambda_G, gamma_G=inf.gamma_G, iteration=inf.iteration,
+                    class_sites=list(inf.class_sites[:nc]), class_regions=list(inf.class_regions[:nc]),
+                    sweeps=[int(x) for x in inf.sweeps[:nc]])
+
+    def pairs(self):
+        par = np.zeros(self.n_pairs, np.int32)
+        chi = np.zeros(self.n_pairs, np.int32)
+        off = np.zeros(self.n_pairs, np.int64)
+        L.check(self._lib.lrh_get_pairs(self._h, par.ctypes.data, chi.ctypes.data, off.ctypes.data), "lrh_get_pairs")
+        return par, chi, off
+
+    # ------------------------------------------------------------ control
+    def set_options(self, **kw) -> None:
+        o = self._opt
+        if "variant" in kw: o.variant = _VARIANTS[kw.pop("variant")]
+        if "step_rule" in kw: o.step_rule = _RULES[kw.pop("step_rule")]
+        if "lhat" in kw:
+            v = kw.pop("lhat"); o.lhat = float(v) if v else 0.0
+        for k in ("alpha", "beta", "degen_tol"):
+            if k in kw: setattr(o, k, float(kw.pop(k)))
+        if "max_sweeps" in kw: o.max_sweeps = int(kw.pop("max_sweeps"))
+        if "use_graph" in kw: o.use_graph = int(bool(kw.pop("use_graph")))
+        if kw:
+            raise TypeError(f"unknown options {sorted(kw)}")
+        L.check(self._lib.lrh_set_options(self._h, C.byref(o)), "lrh_set_options")
+
+    def restart(self) -> None:
+        L.check(self._lib.lrh_restart(self._h), "lrh_restart")
+
+    def step(self, n: int = 1) -> None:
+        L.check(self._lib.lrh_step(self._h, int(n)), "lrh_step")
+
+    def evaluate(self) -> None:
+        L.check(self._lib.lrh_evaluate(self._h), "lrh_evaluate")
+
+    def launch_region_pass(self, k_sites: int) -> None:
+        """Region pass of one size class only (no update); used to time the dominant kernel."""
+        L.check(self._lib.lrh_launch_region_pass(self._h, int(k_sites)), "lrh_launch_region_pass")
+
+    def synchronize(self) -> None:
+        L.check(self._lib.lrh_synchronize(self._h), "lrh_synchronize")
+
+    def run_schedule(self, betas: Sequence[float], iters_per_stage: int) -> None:
+        """Alg. 2 under beta continuation: per beta, L_hat = beta Lambda_G / 2,
+        restart (theta = 1, zeta = nu), then iters_per_stage iterations."""
+        for b in betas:
+            self.set_options(beta=b, lhat=None)
+            self.restart()
+            self.step(iters_per_stage)
+
+    # ------------------------------------------------------------ data
+    def bound(self, kind: str = "certified") -> np.ndarray:
+        out = np.zeros(self.n_instances, np.float64)
+        L.check(self._lib.lrh_bound(self._h, _BOUNDS[kind], out.ctypes.data), "lrh_bound")
+        return out
+
+    def region_values(self, kind: str = "last") -> np.ndarray:
+        out = np.zeros((self.n_instances, self.n_regions), np.float64)
+        L.check(self._lib.lrh_get_region_values(self._h, _BOUNDS[kind], out.ctypes.data), "lrh_get_region_values")
+        return out
+
+    def messages(self, which: str = "nu", out=None):
+        """complex64 array (n_instances, msg_elems); ``out`` may be a CUDA torch tensor."""
+        nbytes = self.n_instances * self.msg_elems * 8
+        if out is not None and hasattr(out, "data_ptr") and getattr(out, "is_cuda", False):
+            assert out.numel() * out.element_size() == nbytes and out.is_contiguous()
+            L.check(self._lib.lrh_get_messages(self._h, _MSGS[which], C.c_void_p(out.data_ptr()), nbytes, 1),
+                    "lrh_get_messages")
+            return out
+        arr = np.zeros((self.n_instances, self.msg_elems), np.complex64)
+        L.check(self._lib.lrh_get_messages(self._h, _MSGS[which], arr.ctypes.data, nbytes, 0), "lrh_get_messages")
+        return arr
+
+    def set_messages(self, which: str, src) -> None:
+        nbytes = self.n_instances * self.msg_elems * 8
+        if hasattr(src, "data_ptr") and getattr(src, "is_cuda", False):
+            assert src.numel() * src.element_size() == nbytes and src.is_contiguous()
+            L.check(self._lib.lrh_set_messages(self._h, _MSGS[which], C.c_void_p(src.data_ptr()), nbytes, 1),
+                    "lrh_set_messages")
+            return
+        arr = np.ascontiguousarray(np.asarray(src, np.complex64).reshape(self.n_instances, self.msg_elems))
+        L.check(self._lib.lrh_set_messages(self._h, _MSGS[which], arr.ctypes.data, nbytes, 0), "lrh_set_messages")

@@ -1,0 +1,196 @@
+"""GPU (CUDA library, through the C ABI) vs the FP64 oracle on the same seeded inputs.
+
+Tolerances: per-step objective 1e-5 relative; gradient per grad_tol (1e-5, or the
+beta-dependent FP32 perturbation bound of the Gibbs state); certified bound vs the
+oracle's Q at the same multipliers 1e-12 per site; integer data (pairs) bit-exact.
+"""
+import numpy as np
+import pytest
+
+import lrh_gen as g
+from oracle import dual
+from oracle.poset import Poset
+from tests.gpu_helpers import grad_rel_err, grad_tol, random_traceless_messages, theta_norms
+
+pytestmark = pytest.mark.gpu
+L = g.lattices
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_40336_b300 import Solver  # noqa: E402
+
+CASES = {
+    "tfim16_level1": lambda: L.tfim_chain(16, 1001),
+    "heis8x8_level1": lambda: L.heisenberg_square(8),
+    "chain_L3_D8": lambda: L.random_chain(12, 5, L=3),
+    "chain_L4_D16": lambda: L.perturbed_chain(40, L=4, delta=0.3, seed=7),
+    "chain_L5_D32": lambda: L.random_chain(23, 9, L=5, scale=0.4),
+    "xxz_tri4_plaq": lambda: L.xxz_triangular(4, 3),
+    "j1j2_4_plaq": lambda: L.j1j2_square(4),
+}
+
+
+def setup(name):
+    p = CASES[name]()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    return p, P, h
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_pairs_and_constants_match_oracle(name):
+    p, P, _ = setup(name)
+    s = Solver(p)
+    par, chi, off = s.pairs()
+    assert np.array_equal(par, P.pair_parent) and np.array_equal(chi, P.pair_child)
+    assert np.array_equal(off, P.msg_off) and s.msg_elems == P.msg_total
+    assert s.lambda_G == P.lipschitz_lambda()
+    assert abs(s.gamma_G - P.gamma()) < 1e-9 * P.gamma()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("beta", [1.0, 16.0, 1024.0])
+def test_smoothed_region_pass_parity(name, beta):
+    """Per-region F_beta, Q_beta and the gradient rho_f - Tr rho_e at the same multipliers."""
+    p, P, h = setup(name)
+    nu = random_traceless_messages(P, p.n_instances, seed=11, scale=0.7)
+    s = Solver(p, variant="nesterov", beta=beta)
+    s.set_messages("nu", nu)
+    s.restart()                       # theta = 1, zeta = nu  ->  eta = nu
+    s.evaluate()
+    vals = s.region_values("last")
+    g_gpu = s.messages("grad")
+    ref = dual.region_pass(P, h, nu.astype(np.complex128), "smooth", beta=beta)
+    q_gpu, q_or = vals.sum(axis=1), ref.value.sum(axis=1)
+    assert np.all(np.abs(q_gpu - q_or) <= 1e-5 * np.maximum(1.0, np.abs(q_or)))
+    tn = theta_norms(P, h, nu)
+    assert np.max(np.abs(vals - ref.value)) <= 1e-5 * max(1.0, tn)
+    assert grad_rel_err(g_gpu, ref.grad, P.n_pairs) <= grad_tol(beta, tn)
+    assert np.allclose(s.bound("last"), q_gpu, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_subgradient_region_pass_parity(name):
+    """lambda_min per region and the subgradient mu_f - Tr mu_e (non-degenerate ground states)."""
+    p, P, h = setup(name)
+    nu = random_traceless_messages(P, p.n_instances, seed=12, scale=0.7)
+    s = Solver(p, variant="subgradient", alpha=0.1, step_rule="const")
+    s.set_messages("nu", nu)
+    s.evaluate()
+    vals = s.region_values("last")
+    ref = dual.region_pass(P, h, nu.astype(np.complex128), "ground", tol=1e-5)
+    tn = theta_norms(P, h, nu)
+    assert np.max(np.abs(vals - ref.value)) <= 1e-5 * max(1.0, tn)
+    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= 1e-4
+
+
+def test_degenerate_ground_space_at_zero_messages():
+    """TFIM edge terms -J ZZ are exactly 2-fold degenerate at nu = 0: both sides take the
+    uniform mixture over the ground space."""
+    p, P, h = setup("tfim16_level1")
+    s = Solver(p, variant="subgradient")
+    s.evaluate()
+    ref = dual.region_pass(P, h, dual.zeros_messages(P, 1), "ground", tol=1e-5)
+    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= 1e-5
+    assert abs(s.bound("last")[0] - (-sum(p.meta["J"]) - sum(p.meta["h"]))) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["heis8x8_level1", "chain_L4_D16", "xxz_tri4_plaq", "chain_L5_D32"])
+def test_nesterov_steps_match_oracle_from_same_state(name):
+    """Two Alg. 2 iterations from a set state (theta_0 = 1, then theta_1)."""
+    p, P, h = setup(name)
+    beta = 4.0
+    nu = random_traceless_messages(P, p.n_instances, seed=13, scale=0.5)
+    s = Solver(p, variant="nesterov", beta=beta, use_graph=False)
+    s.set_messages("nu", nu)
+    s.restart()
+    s.step(2)
+    st = dual.NesterovState(nu=nu.astype(np.complex128), zeta=nu.astype(np.complex128))
+    lhat = beta * P.lipschitz_lambda() / 2
+    dual.nesterov_step(P, h, st, beta, lhat)
+    dual.nesterov_step(P, h, st, beta, lhat)
+    for which, ref in (("nu", st.nu), ("zeta", st.zeta)):
+        got = s.messages(which).astype(np.complex128)
+        assert np.linalg.norm(got - ref) <= 1e-5 * max(1.0, np.linalg.norm(ref)), which
+
+
+def test_subgradient_steps_match_oracle_and_track_best():
+    p, P, h = setup("tfim16_level1")
+    nu = random_traceless_messages(P, 1, seed=14, scale=0.3)
+    s = Solver(p, variant="subgradient", alpha=0.5, step_rule="inv_sqrt", use_graph=False)
+    s.set_messages("nu", nu)
+    st = dual.SubgradientState(nu=nu.astype(np.complex128))
+    for _ in range(3):
+        s.step(1)
+        dual.subgradient_step(P, h, st, "sqrt", 0.5, tol=1e-5)
+    got = s.messages("nu").astype(np.complex128)
+    assert np.linalg.norm(got - st.nu) <= 1e-5 * max(1.0, np.linalg.norm(st.nu))
+    assert abs(s.bound("best")[0] - st.q_best[0]) <= 1e-5 * abs(st.q_best[0])
+    best = s.messages("nu_best").astype(np.complex128)
+    assert np.linalg.norm(best - st.nu_best) <= 1e-5 * max(1.0, np.linalg.norm(st.nu_best))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_certified_bound_matches_oracle_dual_value(name):
+    """FP64 certification at the GPU's FP32 multipliers = oracle Q(nu) at the same nu (1e-12/site)."""
+    p, P, h = setup(name)
+    s = Solver(p, variant="nesterov", beta=8.0)
+    s.step(30)
+    nu = s.messages("nu")
+    cert = s.bound("certified")
+    ref = dual.dual_value(P, h, nu.astype(np.complex128))
+    assert np.all(np.abs(cert - ref) / p.n_sites <= 1e-12)
+
+
+def test_graph_replay_is_bitwise_identical_to_eager():
+    p, _, _ = setup("xxz_tri4_plaq")
+    a = Solver(p, beta=2.0, use_graph=True)
+    b = Solver(p, beta=2.0, use_graph=False)
+    for s in (a, b):
+        s.step(3)       # odd start: eager, then graph chunks from an even iteration
+        s.step(37)
+    assert np.array_equal(a.messages("nu"), b.messages("nu"))
+    assert np.array_equal(a.messages("zeta"), b.messages("zeta"))
+
+
+def test_batched_instances_equal_single_instances():
+    p, _, _ = setup("xxz_tri4_plaq")
+    batch = Solver(p, beta=2.0)
+    batch.step(10)
+    nb = batch.messages("nu")
+    for i in range(p.n_instances):
+        single = g.Problem(p.n_sites, p.regions, p.term_sites, [m[i:i + 1] for m in p.term_mats])
+        s = Solver(single, beta=2.0)
+        s.step(10)
+        assert np.array_equal(s.messages("nu")[0], nb[i])
+
+
+def test_bound_below_exact_energy_and_schedule_tfim():
+    """Alg. 1 on the n = 16 TFIM chain: certified bound <= E_0 (free fermions)."""
+    from oracle import exact
+    p = L.tfim_chain(16, 1001)
+    e0 = exact.tfim_free_fermion_e0(p.meta["J"], p.meta["h"])
+    s = Solver(p, variant="subgradient", alpha=1.0, step_rule="inv_sqrt")
+    s.step(2000)
+    cert = s.bound("certified")[0]
+    assert cert <= e0 and cert >= s.bound("best")[0] - 1e-4
+
+
+def test_single_region_without_pairs():
+    p = g.Problem(2, [(0, 1)], [(0, 1)], [L.XX[None]])
+    s = Solver(p)
+    s.step(4)
+    assert abs(s.bound("certified")[0] - (-1.0)) < 1e-12
+
+
+def test_messages_stay_traceless_on_gpu():
+    p, P, _ = setup("chain_L4_D16")
+    s = Solver(p, beta=8.0)
+    s.step(50)
+    nu = s.messages("nu")[0]
+    for q in range(P.n_pairs):
+        Df = int(P.D[P.pair_child[q]])
+        M = nu[P.msg_off[q]:P.msg_off[q] + Df * Df].reshape(Df, Df)
+        assert abs(np.trace(M)) < 1e-5 * max(1.0, np.abs(M).max())
