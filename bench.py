@@ -49,7 +49,7 @@ def workload():
 def config(extra=None):
     c = {"workload": f"heisenberg_square_{L_SIDE}x{L_SIDE}_periodic_level1_nesterov_beta1-1024",
          "n_sites": L_SIDE * L_SIDE, "regions": {"4x4": 2 * L_SIDE * L_SIDE, "2x2": L_SIDE * L_SIDE},
-         "iterations_per_step": len(BETAS) * ITERS_PER_STAGE, "betas": "2^0..2^10",
+         "iterations_per_step": len(BETAS) * ITERS_PER_STAGE, "betas": f"2^0..2^{len(BETAS) - 1}",
          "iters_per_stage": ITERS_PER_STAGE, "l2": "flushed between steps (256 MiB write)"}
     if extra:
         c.update(extra)
@@ -236,13 +236,19 @@ def run_reference(args):
 
 
 def main():
+    global ITERS_PER_STAGE, BETAS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrh", choices=["lrh", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / CPU baseline / e2e legs")
+    ap.add_argument("--iters-per-stage", type=int, default=ITERS_PER_STAGE,
+                    help="smaller values only for profiling runs (the benchmark uses 200)")
+    ap.add_argument("--stages", type=int, default=len(BETAS), help="beta stages (profiling runs only)")
     args = ap.parse_args()
+    ITERS_PER_STAGE = args.iters_per_stage
+    BETAS = BETAS[:args.stages]
     if args.impl == "reference":
         return run_reference(args)
 

@@ -188,6 +188,28 @@ int lrh_get_region_values(lrh_problem* p, int32_t kind, double* out);
 int lrh_get_messages(lrh_problem* p, int32_t which, void* dst, int64_t bytes, int32_t dst_is_device);
 int lrh_set_messages(lrh_problem* p, int32_t which, const void* src, int64_t bytes, int32_t src_is_device);
 
+/* Replace the term matrices (same sites, offsets and instance count as at creation; host
+ * pointer, layout of lrh_problem_desc.term_mats).  Used to differentiate with respect to
+ * couplings.  Synchronises. */
+int lrh_set_terms(lrh_problem* p, const double* term_mats);
+
+/* Reverse-mode derivative (adjoint) of the smoothed evaluation done by lrh_evaluate, at the
+ * same point eta = (1-theta) nu + theta zeta (Nesterov problems, regions of <= 5 sites).
+ * The evaluation maps term matrices T and multipliers to Q_beta (per instance) and the
+ * gradient g (message layout) (Sec. 4.1.2, 4.2).  Given cotangents q_bar (host double
+ * [n_instances]) and g_bar (complex64 message layout, device if g_bar_is_device, NULL = 0)
+ * it writes nu_bar (complex64, message layout) and term_bar (complex64, layout of the term
+ * matrices, [n_instances][term_mat_total]) under the inner product Re Tr(A^dagger B):
+ *   rho_bar_e = sum_parents g_bar - sum_children 1 (x) g_bar,
+ *   theta_bar = V[(V^dagger rho_bar V) o K + (beta <rho_bar, rho> + q_bar) diag(p)] V^dagger,
+ *   K_kl = (p_k - p_l)/(lambda_k - lambda_l), K_kk = -beta p_k  (eigenbasis recomputed),
+ *   nu_bar_{e->f} = theta_bar_f - Tr_{e} theta_bar_e,  term_bar_t = Tr_{R	} theta_bar_R.
+ * The derivative with respect to nu_{e->f} of eta-evaluated quantities is returned for eta
+ * itself.  Outputs are device pointers when out_is_device (each may be NULL).
+ * The first call allocates the adjoint buffers.  Synchronises. */
+int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_bar_is_device, void* nu_bar,
+            void* term_bar, int32_t out_is_device);
+
 /* Wait for the problem's stream and report any device-side numeric error (LRH_ENUMERIC). */
 int lrh_synchronize(lrh_problem* p);
 

@@ -43,7 +43,7 @@ struct VecHash {
 };
 
 constexpr int kMaxSites = 7;     // region size limit of the data layout (D <= 128)
-constexpr int kMaxKernelSites = 5;  // sizes with a region-pass kernel in this build (D <= 32)
+constexpr int kMaxKernelSites = 7;  // sizes with a region-pass kernel in this build (D <= 128)
 constexpr int kGraphChunk = 8;   // iterations per captured graph (even: parity returns to 0)
 
 struct DeviceGuard {
@@ -55,6 +55,8 @@ struct DeviceGuard {
 };
 
 }  // namespace
+
+int lrh::set_last_error(int code, const std::string& msg) { return fail(code, msg); }
 
 struct lrh_problem {
     int device = 0;
@@ -80,6 +82,15 @@ struct lrh_problem {
     int64_t h_pinned_len = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    // term structure (for lrh_set_terms and the adjoint)
+    int32_t n_terms = 0;
+    int64_t term_total = 0;
+    std::vector<int32_t> term_region, term_mask, term_kt;
+    std::vector<int64_t> term_off, region_h_off;
+    std::vector<int32_t> region_k;
+    int64_t all_elems = 0;
+    float2* vjp_nubar = nullptr;    // adjoint outputs staged on the device
+    float2* vjp_termbar = nullptr;
 
     template <typename T>
     int dalloc(T** ptr, int64_t count) {
@@ -120,6 +131,63 @@ int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
     const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
     LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), theta, t, set_theta_t ? 1 : 0, o.beta,
                             1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, p->stream));
+    return LRH_OK;
+}
+
+// Hermitian part of every term matrix (exactly: (m + m^dagger)/2) embedded into the dense
+// region terms h_e in FP64, instance-major, at the offsets of region_h_off.
+void embed_terms(const lrh_problem* p, const double* term_mats, std::vector<double>& h64) {
+    auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 7; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
+    h64.assign((size_t)(2 * p->n_inst * std::max<int64_t>(p->h_elems, 1)), 0.0);
+    for (int t = 0; t < p->n_terms; ++t) {
+        const int e = p->term_region[t];
+        const int k = p->region_k[e];
+        const int64_t D = (int64_t)1 << k;
+        const int M = p->term_mask[t];
+        const int64_t Dt = (int64_t)1 << p->term_kt[t];
+        for (int inst = 0; inst < p->n_inst; ++inst) {
+            const double* m = term_mats + 2 * ((int64_t)inst * p->term_total + p->term_off[t]);
+            double* h = h64.data() + 2 * ((int64_t)inst * p->h_elems + p->region_h_off[e]);
+            for (int i = 0; i < D; ++i)
+                for (int j = 0; j < D; ++j) {
+                    if (((i ^ j) & ~M) != 0) continue;
+                    const int64_t a = pext(i, M), c = pext(j, M);
+                    const double re = 0.5 * (m[2 * (a * Dt + c)] + m[2 * (c * Dt + a)]);
+                    const double im = (a == c) ? 0.0 : 0.5 * (m[2 * (a * Dt + c) + 1] - m[2 * (c * Dt + a) + 1]);
+                    h[2 * (i * D + j)] += re;
+                    h[2 * (i * D + j) + 1] += im;
+                }
+        }
+    }
+}
+
+int upload_terms(lrh_problem* p, const std::vector<double>& h64) {
+    if (!p->h_elems) return LRH_OK;
+    std::vector<float> h32h(h64.size());
+    for (size_t i = 0; i < h64.size(); ++i) h32h[i] = (float)h64[i];
+    LRH_CK(cudaMemcpyAsync(const_cast<float2*>(p->P.h32), h32h.data(), sizeof(float) * h32h.size(), cudaMemcpyHostToDevice, p->stream));
+    LRH_CK(cudaMemcpyAsync(const_cast<double2*>(p->P.h64), h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice, p->stream));
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    return LRH_OK;
+}
+
+int check_terms(const lrh_problem* p, const int64_t* term_ptr, const double* term_mats) {
+    for (int t = 0; t < p->n_terms; ++t) {
+        const int64_t Dt = (int64_t)1 << (term_ptr[t + 1] - term_ptr[t]);
+        for (int i = 0; i < p->n_inst; ++i) {
+            const double* m = term_mats + 2 * ((int64_t)i * p->term_total + p->term_off[t]);
+            double mx = 0;
+            for (int64_t a = 0; a < Dt * Dt; ++a) mx = std::max(mx, std::fabs(m[2 * a]) + std::fabs(m[2 * a + 1]));
+            for (int64_t a = 0; a < Dt; ++a)
+                for (int64_t c = 0; c < Dt; ++c) {
+                    const double dr = m[2 * (a * Dt + c)] - m[2 * (c * Dt + a)];
+                    const double di = m[2 * (a * Dt + c) + 1] + m[2 * (c * Dt + a) + 1];
+                    if (!std::isfinite(dr) || !std::isfinite(di)) return fail(LRH_EINVAL, "non-finite term entry");
+                    if (std::fabs(dr) + std::fabs(di) > 1e-10 * std::max(1.0, mx))
+                        return fail(LRH_ENOTHERM, "term " + std::to_string(t) + " is not Hermitian");
+                }
+        }
+    }
     return LRH_OK;
 }
 
@@ -293,6 +361,8 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     for (int e = 0; e < R; ++e) for (int32_t s : regs[e]) by_site[s].push_back(e);
     std::vector<int> place(d->n_terms, -1);
     std::vector<char> has_term(R, 0);
+    p->n_terms = d->n_terms;
+    p->term_total = d->term_mat_total;
     for (int t = 0; t < d->n_terms; ++t) {
         const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
         if (en - b < 1 || en - b > kMaxSites) return fail(LRH_EINVAL, "term " + std::to_string(t) + " has a bad site count");
@@ -312,58 +382,41 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         const int64_t Dt = (int64_t)1 << ts.size();
         const int64_t off = d->term_mat_off[t];
         if (off < 0 || off + Dt * Dt > d->term_mat_total) return fail(LRH_EINVAL, "term matrix offset out of range");
-        for (int i = 0; i < d->n_instances; ++i) {
-            const double* m = d->term_mats + 2 * ((int64_t)i * d->term_mat_total + off);
-            double mx = 0;
-            for (int64_t a = 0; a < Dt * Dt; ++a) mx = std::max(mx, std::fabs(m[2 * a]) + std::fabs(m[2 * a + 1]));
-            for (int64_t a = 0; a < Dt; ++a)
-                for (int64_t c = 0; c < Dt; ++c) {
-                    const double dr = m[2 * (a * Dt + c)] - m[2 * (c * Dt + a)];
-                    const double di = m[2 * (a * Dt + c) + 1] + m[2 * (c * Dt + a) + 1];
-                    if (!std::isfinite(dr) || !std::isfinite(di)) return fail(LRH_EINVAL, "non-finite term entry");
-                    if (std::fabs(dr) + std::fabs(di) > 1e-10 * std::max(1.0, mx))
-                        return fail(LRH_ENOTHERM, "term " + std::to_string(t) + " is not Hermitian");
-                }
+        const int k = (int)regs[bestr].size();
+        int M = 0;
+        for (int32_t site : ts) {
+            const int pos = (int)(std::find(regs[bestr].begin(), regs[bestr].end(), site) - regs[bestr].begin());
+            M |= 1 << (k - 1 - pos);
         }
+        p->term_region.push_back(bestr);
+        p->term_mask.push_back(M);
+        p->term_kt.push_back((int32_t)ts.size());
+        p->term_off.push_back(off);
     }
-    int64_t hoff = 0, roff = 0;
+    if (d->n_terms > 0 && (rc = check_terms(p, d->term_ptr, d->term_mats))) return rc;
+    int64_t hoff = 0, roff = 0, aoff = 0;
+    p->region_h_off.assign(R, -1);
+    p->region_k.assign(R, 0);
     for (int e = 0; e < R; ++e) {
         const int64_t D = (int64_t)1 << regs[e].size();
+        p->region_k[e] = (int32_t)regs[e].size();
         rinfo[e].h_off = has_term[e] ? hoff : -1;
+        p->region_h_off[e] = rinfo[e].h_off;
         if (has_term[e]) hoff += D * D;
         rinfo[e].rho_off = parent_of[e].empty() ? -1 : roff;
         if (!parent_of[e].empty()) roff += D * D;
+        rinfo[e].all_off = aoff;
+        aoff += D * D;
     }
     p->h_elems = hoff;
     p->rho_elems = roff;
-    std::vector<double> h64((size_t)(2 * p->n_inst * std::max<int64_t>(hoff, 1)), 0.0);
-    for (int t = 0; t < d->n_terms; ++t) {
-        const int e = place[t];
-        const int k = (int)regs[e].size();
-        const int64_t D = (int64_t)1 << k;
-        const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
-        int M = 0;
-        for (int64_t i = b; i < en; ++i) {
-            const int pos = (int)(std::find(regs[e].begin(), regs[e].end(), d->term_sites[i]) - regs[e].begin());
-            M |= 1 << (k - 1 - pos);
-        }
-        auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 7; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
-        const int64_t Dt = (int64_t)1 << (en - b);
-        for (int inst = 0; inst < p->n_inst; ++inst) {
-            const double* m = d->term_mats + 2 * ((int64_t)inst * d->term_mat_total + d->term_mat_off[t]);
-            double* h = h64.data() + 2 * ((int64_t)inst * hoff + rinfo[e].h_off);
-            for (int i = 0; i < D; ++i)
-                for (int j = 0; j < D; ++j) {
-                    if (((i ^ j) & ~M) != 0) continue;
-                    const int64_t src = pext(i, M) * Dt + pext(j, M);
-                    h[2 * (i * D + j)] += m[2 * src];
-                    h[2 * (i * D + j) + 1] += m[2 * src + 1];
-                }
-        }
-    }
+    p->all_elems = aoff;
+    std::vector<double> h64;
+    embed_terms(p, d->term_mats, h64);
 
     // ---------------------------------------------------------------- device state
     LRH_CK(prepare_kernels());
+    LRH_CK(prepare_vjp_kernels());
     if (stream) {
         p->stream = (cudaStream_t)stream;
     } else {
@@ -378,10 +431,20 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     P.rho_elems = roff;
     P.msg_elems = moff;
     const int64_t NI = p->n_inst;
-    RegionInfo* dreg; PairInfo* dpair; int32_t *dcp, *dpp;
+    RegionInfo* dreg; PairInfo* dpair; int32_t *dcp, *dpp, *dchunk;
     if ((rc = p->dalloc(&dreg, R)) || (rc = p->dalloc(&dpair, p->n_pairs)) || (rc = p->dalloc(&dcp, p->n_pairs)) ||
-        (rc = p->dalloc(&dpp, p->n_pairs)))
+        (rc = p->dalloc(&dpp, p->n_pairs)) || (rc = p->dalloc(&dchunk, moff / 4)))
         return rc;
+    {
+        std::vector<int32_t> chunk((size_t)(moff / 4));
+        for (size_t q = 0; q < pairs.size(); ++q) {
+            const int64_t n4 = ((int64_t)1 << (2 * pairs[q].kf)) / 4;
+            for (int64_t c = 0; c < n4; ++c) chunk[(size_t)(pairs[q].off / 4 + c)] = (int32_t)q;
+        }
+        if (!chunk.empty())
+            LRH_CK(cudaMemcpy(dchunk, chunk.data(), sizeof(int32_t) * chunk.size(), cudaMemcpyHostToDevice));
+    }
+    P.chunk_pair = dchunk;
     float2* h32; double2* dh64;
     if ((rc = p->dalloc(&h32, NI * hoff)) || (rc = p->dalloc(&dh64, NI * hoff))) return rc;
     if ((rc = p->dalloc(&P.nu, NI * moff)) || (rc = p->dalloc(&P.zeta, NI * moff)) || (rc = p->dalloc(&P.nu_best, NI * moff)) ||
@@ -392,18 +455,16 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)))
         return rc;
     P.reg = dreg; P.pair = dpair; P.child_pairs = dcp; P.parent_pairs = dpp; P.h32 = h32; P.h64 = dh64;
+    P.all_elems = p->all_elems;
+    P.n_terms = p->n_terms;
+    P.term_total = p->term_total;
     LRH_CK(cudaMemcpy(dreg, rinfo.data(), sizeof(RegionInfo) * R, cudaMemcpyHostToDevice));
     if (p->n_pairs) {
         LRH_CK(cudaMemcpy(dpair, pairs.data(), sizeof(PairInfo) * pairs.size(), cudaMemcpyHostToDevice));
         LRH_CK(cudaMemcpy(dcp, child_pairs.data(), sizeof(int32_t) * child_pairs.size(), cudaMemcpyHostToDevice));
         LRH_CK(cudaMemcpy(dpp, parent_pairs.data(), sizeof(int32_t) * parent_pairs.size(), cudaMemcpyHostToDevice));
     }
-    if (hoff) {
-        std::vector<float> h32h(h64.size());
-        for (size_t i = 0; i < h64.size(); ++i) h32h[i] = (float)h64[i];
-        LRH_CK(cudaMemcpy(h32, h32h.data(), sizeof(float) * h32h.size(), cudaMemcpyHostToDevice));
-        LRH_CK(cudaMemcpy(dh64, h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice));
-    }
+    if ((rc = upload_terms(p, h64))) return rc;
     LRH_CK(cudaMemset(P.nu, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
     LRH_CK(cudaMemset(P.zeta, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
     LRH_CK(cudaMemset(P.nu_best, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
@@ -603,6 +664,67 @@ int lrh_set_messages(lrh_problem* p, int32_t which, const void* src, int64_t byt
     LRH_CK(cudaMemcpyAsync(dst, src, (size_t)need, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
     if (!src_is_device) LRH_CK(cudaStreamSynchronize(p->stream));
     return LRH_OK;
+}
+
+int lrh_set_terms(lrh_problem* p, const double* term_mats) {
+    if (!p || (!term_mats && p->n_terms > 0)) return fail(LRH_EINVAL, "NULL argument");
+    DeviceGuard dg(p->device);
+    std::vector<int64_t> tptr(p->n_terms + 1, 0);
+    for (int t = 0; t < p->n_terms; ++t) tptr[t + 1] = tptr[t] + p->term_kt[t];
+    int rc = check_terms(p, tptr.data(), term_mats);
+    if (rc) return rc;
+    std::vector<double> h64;
+    embed_terms(p, term_mats, h64);
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    return upload_terms(p, h64);
+}
+
+int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_bar_is_device, void* nu_bar,
+            void* term_bar, int32_t out_is_device) {
+    if (!p || !q_bar) return fail(LRH_EINVAL, "NULL argument");
+    if (p->opt.variant != LRH_NESTEROV) return fail(LRH_EINVAL, "lrh_vjp differentiates the smoothed objective (LRH_NESTEROV)");
+    if (p->max_k > 5) return fail(LRH_EUNSUPPORTED, "the adjoint kernels handle regions of at most 5 sites");
+    DeviceGuard dg(p->device);
+    const int64_t NI = p->n_inst;
+    DevProblem& P = p->P;
+    if (!P.thb) {
+        int rc;
+        if ((rc = p->dalloc(&P.thb, NI * p->all_elems)) || (rc = p->dalloc(&P.gbar, NI * p->msg_elems)) ||
+            (rc = p->dalloc(&P.qbar, NI)) || (rc = p->dalloc(&p->vjp_nubar, NI * p->msg_elems)) ||
+            (rc = p->dalloc(&p->vjp_termbar, NI * p->term_total)))
+            return rc;
+        std::vector<TermInfo> ti(std::max(p->n_terms, 1));
+        for (int t = 0; t < p->n_terms; ++t) {
+            ti[t].out_off = p->term_off[t];
+            ti[t].region = p->term_region[t];
+            ti[t].mask = p->term_mask[t];
+            ti[t].kt = p->term_kt[t];
+            ti[t].dr = 1 << p->region_k[p->term_region[t]];
+        }
+        TermInfo* dti;
+        if ((rc = p->dalloc(&dti, (int64_t)ti.size()))) return rc;
+        LRH_CK(cudaMemcpy(dti, ti.data(), sizeof(TermInfo) * ti.size(), cudaMemcpyHostToDevice));
+        P.terms = dti;
+        if (p->graph_exec) {   // captured graphs hold a copy of P without the adjoint buffers: rebuild
+            cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr;
+            cudaGraphDestroy(p->graph); p->graph = nullptr;
+        }
+    }
+    LRH_CK(cudaMemcpyAsync(P.qbar, q_bar, sizeof(double) * NI, cudaMemcpyHostToDevice, p->stream));
+    const size_t mbytes = sizeof(float2) * NI * p->msg_elems;
+    if (mbytes) {
+        if (g_bar) LRH_CK(cudaMemcpyAsync(P.gbar, g_bar, mbytes, g_bar_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
+        else LRH_CK(cudaMemsetAsync(P.gbar, 0, mbytes, p->stream));
+    }
+    const int par = (int)(p->iteration & 1);
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        LRH_CK(launch_vjp_region(P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+    LRH_CK(launch_vjp_outputs(P, p->vjp_nubar, p->vjp_termbar, p->stream));
+    const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (nu_bar && mbytes) LRH_CK(cudaMemcpyAsync(nu_bar, p->vjp_nubar, mbytes, kind, p->stream));
+    if (term_bar && p->term_total)
+        LRH_CK(cudaMemcpyAsync(term_bar, p->vjp_termbar, sizeof(float2) * NI * p->term_total, kind, p->stream));
+    return read_err(p);
 }
 
 int lrh_synchronize(lrh_problem* p) {

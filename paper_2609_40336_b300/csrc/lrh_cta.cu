@@ -1,0 +1,521 @@
+// CTA-level region pass for D = 64 and D = 128 (regions of 6 and 7 sites), sm_103a.
+//
+// One CTA owns one region.  theta is kept as a packed Hermitian upper triangle in shared
+// memory (D(D+1)/2 complex entries: 66 KB in FP32, 132 KB in FP64 at D = 128).  A sweep of
+// the cyclic two-sided Jacobi method runs D-1 rounds of the round-robin tournament; instead
+// of moving matrix entries, a slot -> index map (two small arrays in shared memory) is
+// rotated each round.  Every round:
+//   1. D/2 threads compute the rotation (c, w) of the pair in slots (2k, 2k+1);
+//   2. the 2x2 blocks (k <= l) of the D/2 x D/2 block grid are updated in ONE pass,
+//      B' = J_k^H B J_l: the blocks partition the unordered index pairs, so no two threads
+//      touch the same packed entry and no second pass (row vs column) is needed;
+//   3. V (in registers, 4 threads per row, columns in slot order) gets the column rotation
+//      and then the tournament's column permutation, which moves one complex value across
+//      each chunk boundary (two neighbour shuffles).
+// The Gibbs / ground state rho = W W^dagger, W = V diag(sqrt p), is formed from W^T staged
+// in the same shared-memory buffer, with register tiles; then made exactly Hermitian, traced
+// onto the children and written out.  The FP64 certification kernel reuses the Jacobi part
+// (no V) to return lambda_min.
+#include "lrh_internal.cuh"
+
+#include <cmath>
+#include <cstdint>
+
+namespace lrh {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__host__ __device__ constexpr int rr_src_c(int s, int D) {
+    return s == 0 ? 0 : (s == 2 ? 1 : ((s & 1) == 0 ? s - 2 : (s == D - 1 ? D - 2 : s + 2)));
+}
+
+__device__ __forceinline__ int pext7(int x, int m) {
+    int r = 0, k = 0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+        if ((m >> b) & 1) { r |= ((x >> b) & 1) << k; ++k; }
+    return r;
+}
+
+__device__ __forceinline__ int pdep7(int x, int m) {
+    int r = 0, k = 0;
+#pragma unroll
+    for (int b = 0; b < 7; ++b)
+        if ((m >> b) & 1) { r |= ((x >> k) & 1) << b; ++k; }
+    return r;
+}
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+template <typename T> struct alignas(4 * sizeof(T)) RotC { T c, wr, wi, pad; };
+
+template <typename T>
+__device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ void rot_params_c(T app, T aqq, T br, T bi, RotC<T>& R) {
+    const T h = aqq - app;
+    const T b2 = br * br + bi * bi;
+    const T r = sqrt_t<T>(h * h + T(4) * b2);
+    const T den = fabs(h) + r;
+    const T sg = h >= T(0) ? T(1) : T(-1);
+    T t = T(0), sig = T(0);
+    if (den > T(0)) t = -sg * T(2) * sqrt_t<T>(b2) / den;
+    const T c = T(1) / sqrt_t<T>(T(1) + t * t);
+    if (den > T(0)) sig = -sg * T(2) * c / den;
+    R.c = c;
+    R.wr = sig * br;
+    R.wi = sig * bi;
+    R.pad = T(0);
+}
+
+__device__ __forceinline__ int tri(int i, int j, int D) { return i * D - ((i * (i - 1)) >> 1) + (j - i); }
+
+template <typename T>
+struct Packed {
+    using C2 = typename V2<T>::t;
+    C2* a;
+    int D;
+    __device__ __forceinline__ C2 get(int i, int j) const {
+        if (i <= j) return a[tri(i, j, D)];
+        C2 v = a[tri(j, i, D)];
+        v.y = -v.y;
+        return v;
+    }
+    __device__ __forceinline__ void set(int i, int j, C2 v) const {
+        if (i <= j) { a[tri(i, j, D)] = v; } else { v.y = -v.y; a[tri(j, i, D)] = v; }
+    }
+};
+
+// B' = J_k^H B J_l on a 2x2 block, J = [[c, -w], [conj(w), c]].
+template <typename T, typename C2>
+__device__ __forceinline__ void two_sided(C2& b00, C2& b01, C2& b10, C2& b11, const RotC<T>& K, const RotC<T>& Lr) {
+    // C = B J_l : x_p' = c x_p + conj(w) x_q ; x_q' = -w x_p + c x_q   (per row)
+    auto colmix = [&](C2& xp, C2& xq) {
+        const T pr = Lr.c * xp.x + (Lr.wr * xq.x + Lr.wi * xq.y);
+        const T pi = Lr.c * xp.y + (Lr.wr * xq.y - Lr.wi * xq.x);
+        const T qr = Lr.c * xq.x - (Lr.wr * xp.x - Lr.wi * xp.y);
+        const T qi = Lr.c * xq.y - (Lr.wr * xp.y + Lr.wi * xp.x);
+        xp.x = pr; xp.y = pi; xq.x = qr; xq.y = qi;
+    };
+    colmix(b00, b01);
+    colmix(b10, b11);
+    // J_k^H C : y_p' = c y_p + w y_q ; y_q' = -conj(w) y_p + c y_q   (per column)
+    auto rowmix = [&](C2& yp, C2& yq) {
+        const T pr = K.c * yp.x + (K.wr * yq.x - K.wi * yq.y);
+        const T pi = K.c * yp.y + (K.wr * yq.y + K.wi * yq.x);
+        const T qr = K.c * yq.x - (K.wr * yp.x + K.wi * yp.y);
+        const T qi = K.c * yq.y - (K.wr * yp.y - K.wi * yp.x);
+        yp.x = pr; yp.y = pi; yq.x = qr; yq.y = qi;
+    };
+    rowmix(b00, b10);
+    rowmix(b01, b11);
+}
+
+template <int NT, typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+    return s;
+}
+
+template <int D> struct CtaCfg;
+template <> struct CtaCfg<64> { static constexpr int NT = 256; static constexpr int TR = 4, TC = 4; };
+template <> struct CtaCfg<128> { static constexpr int NT = 512; static constexpr int TR = 4, TC = 8; };
+
+template <int D, typename T>
+struct CtaSmem {
+    static constexpr int n = D / 2;
+    static constexpr int NB = n * (n + 1) / 2;
+    static constexpr int NT = CtaCfg<D>::NT;
+    static constexpr size_t tri_elems = (size_t)D * (D + 1) / 2;
+    // FP32 kernel also stages W^T and rho (D x D) in the same buffer
+    static constexpr size_t buf_bytes_f = ((sizeof(float2) * (size_t)D * D) + 15) / 16 * 16;
+    static constexpr size_t buf_bytes_d = ((sizeof(double2) * tri_elems) + 15) / 16 * 16;
+    static constexpr size_t buf_bytes = sizeof(T) == 4 ? buf_bytes_f : buf_bytes_d;
+    static constexpr size_t off_prm = buf_bytes;
+    static constexpr size_t off_idx = off_prm + sizeof(RotC<T>) * n;
+    static constexpr size_t off_tab = off_idx + sizeof(int) * 2 * D;
+    static constexpr size_t off_lam = off_tab + ((sizeof(unsigned short) * NB + 15) / 16 * 16);
+    static constexpr size_t off_red = off_lam + sizeof(float) * 2 * D;
+    static constexpr size_t bytes = off_red + sizeof(double) * (NT / 32) + 16;
+};
+
+// Cyclic Jacobi on the packed matrix; V (if WANT_V) holds row `row`, columns
+// [chunk * W, chunk * W + W) in slot order.  Returns the sweeps run.
+template <int D, typename T, bool WANT_V>
+__device__ int jacobi_cta(Packed<T> A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
+                          T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out) {
+    constexpr int NT = CtaCfg<D>::NT;
+    constexpr int n = D / 2;
+    constexpr int NB = n * (n + 1) / 2;
+    constexpr int CH = 4;
+    constexpr int W = D / CH;
+    const int t = threadIdx.x;
+    const int chunk = t % CH;
+    T n2 = T(0);
+    for (int e = t; e < (int)(D * (D + 1) / 2); e += NT) {
+        const auto v = A.a[e];
+        n2 += v.x * v.x + v.y * v.y;   // diagonal counted once, off-diagonal below
+    }
+    // off-diagonal entries appear once in the triangle but twice in ||A||_F^2
+    T offd = T(0);
+    for (int i = t; i < D; i += NT) {
+        const auto v = A.a[tri(i, i, D)];
+        offd += v.x * v.x + v.y * v.y;
+    }
+    const T norm2 = T(2) * block_sum<NT>(n2, red) - block_sum<NT>(offd, red);
+    norm2_out = norm2;
+    const T thresh = tol2 * norm2;
+    int* ix = idx0;
+    int* ixn = idx1;
+    int sweeps = 0;
+    for (;;) {
+        T diag = T(0), tot = T(0);
+        for (int e = t; e < (int)(D * (D + 1) / 2); e += NT) {
+            const auto v = A.a[e];
+            tot += v.x * v.x + v.y * v.y;
+        }
+        for (int i = t; i < D; i += NT) {
+            const auto v = A.a[tri(i, i, D)];
+            diag += v.x * v.x + v.y * v.y;
+        }
+        const T off = T(2) * (block_sum<NT>(tot, red) - block_sum<NT>(diag, red));
+        if (off <= thresh || sweeps >= max_sweeps) break;
+        ++sweeps;
+        for (int r = 0; r < D - 1; ++r) {
+            if (t < n) {
+                const int p = ix[2 * t], q = ix[2 * t + 1];
+                const auto b = A.get(p, q);
+                rot_params_c<T>(A.a[tri(p, p, D)].x, A.a[tri(q, q, D)].x, b.x, b.y, prm[t]);
+            }
+            __syncthreads();
+            if (WANT_V) {
+#pragma unroll
+                for (int m = 0; m < W / 2; ++m) {
+                    const RotC<T> Rk = prm[(chunk * W) / 2 + m];
+                    T& pr = vr[2 * m]; T& pi = vi[2 * m]; T& qr = vr[2 * m + 1]; T& qi = vi[2 * m + 1];
+                    const T npr = Rk.c * pr + (Rk.wr * qr + Rk.wi * qi);
+                    const T npi = Rk.c * pi + (Rk.wr * qi - Rk.wi * qr);
+                    const T nqr = Rk.c * qr - (Rk.wr * pr - Rk.wi * pi);
+                    const T nqi = Rk.c * qi - (Rk.wr * pi + Rk.wi * pr);
+                    pr = npr; pi = npi; qr = nqr; qi = nqi;
+                }
+            }
+            for (int bidx = t; bidx < NB; bidx += NT) {
+                const int kl = tab[bidx];
+                const int kk = kl >> 8, ll = kl & 255;
+                const RotC<T> K = prm[kk];
+                const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
+                if (kk == ll) {
+                    auto b00 = A.a[tri(pk, pk, D)];
+                    auto b11 = A.a[tri(qk, qk, D)];
+                    auto b01 = A.get(pk, qk);
+                    auto b10 = b01; b10.y = -b10.y;
+                    b00.y = T(0); b11.y = T(0);
+                    two_sided<T>(b00, b01, b10, b11, K, K);
+                    b00.y = T(0); b11.y = T(0);
+                    A.a[tri(pk, pk, D)] = b00;
+                    A.a[tri(qk, qk, D)] = b11;
+                    auto z = b01; z.x = T(0); z.y = T(0);
+                    A.set(pk, qk, z);
+                } else {
+                    const RotC<T> Lr = prm[ll];
+                    const int pl = ix[2 * ll], ql = ix[2 * ll + 1];
+                    auto b00 = A.get(pk, pl), b01 = A.get(pk, ql), b10 = A.get(qk, pl), b11 = A.get(qk, ql);
+                    two_sided<T>(b00, b01, b10, b11, K, Lr);
+                    A.set(pk, pl, b00); A.set(pk, ql, b01); A.set(qk, pl, b10); A.set(qk, ql, b11);
+                }
+            }
+            __syncthreads();
+            if (t < D) ixn[t] = ix[rr_src_c(t, D)];
+            if (WANT_V) {
+                // new[c] = old[rr_src(c)] over global slots; chunk boundaries move one value each way
+                const T flr = __shfl_up_sync(kFull, vr[W - 2], 1);
+                const T fli = __shfl_up_sync(kFull, vi[W - 2], 1);
+                const T frr = __shfl_down_sync(kFull, vr[1], 1);
+                const T fri = __shfl_down_sync(kFull, vi[1], 1);
+                T nr[W], ni[W];
+                nr[0] = chunk == 0 ? vr[0] : flr;
+                ni[0] = chunk == 0 ? vi[0] : fli;
+                nr[2] = chunk == 0 ? vr[1] : vr[0];
+                ni[2] = chunk == 0 ? vi[1] : vi[0];
+#pragma unroll
+                for (int e = 4; e < W; e += 2) { nr[e] = vr[e - 2]; ni[e] = vi[e - 2]; }
+#pragma unroll
+                for (int o = 1; o <= W - 3; o += 2) { nr[o] = vr[o + 2]; ni[o] = vi[o + 2]; }
+                nr[W - 1] = chunk == CH - 1 ? vr[W - 2] : frr;
+                ni[W - 1] = chunk == CH - 1 ? vi[W - 2] : fri;
+#pragma unroll
+                for (int e = 0; e < W; ++e) { vr[e] = nr[e]; vi[e] = ni[e]; }
+            }
+            __syncthreads();
+            int* tmp = ix; ix = ixn; ixn = tmp;
+        }
+    }
+    return sweeps;
+}
+
+// theta entries (i <= j) into the packed triangle: h_e - sum_children 1 (x) m + sum_parents m,
+// m = (1 - th) nu + th zeta (zeta == nullptr: m = nu).  FP64 path reads h64.
+template <int D, typename T>
+__device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int inst, Packed<T> A,
+                                const float2* __restrict__ nu, const float2* __restrict__ zeta, float th, bool use_h64) {
+    constexpr int NT = CtaCfg<D>::NT;
+    const int64_t mbase = (int64_t)inst * P.msg_elems;
+    const float om = 1.0f - th;
+    for (int e = threadIdx.x; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        if (i > j) continue;
+        T re = T(0), im = T(0);
+        if (R.h_off >= 0) {
+            if (use_h64) {
+                const double2 v = P.h64[(int64_t)inst * P.h_elems + R.h_off + e];
+                re = T(v.x); im = T(v.y);
+            } else {
+                const float2 v = P.h32[(int64_t)inst * P.h_elems + R.h_off + e];
+                re = T(v.x); im = T(v.y);
+            }
+        }
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.pair[P.child_pairs[q]];
+            if (((i ^ j) & ~pi.mask) != 0) continue;
+            const int Df = 1 << pi.kf;
+            const int64_t o = mbase + pi.off + (int64_t)pext7(i, pi.mask) * Df + pext7(j, pi.mask);
+            float2 m = nu[o];
+            if (zeta) { const float2 z = zeta[o]; m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y; }
+            re -= T(m.x); im -= T(m.y);
+        }
+        for (int q = R.parent_begin; q < R.parent_end; ++q) {
+            const PairInfo pi = P.pair[P.parent_pairs[q]];
+            const int64_t o = mbase + pi.off + e;
+            float2 m = nu[o];
+            if (zeta) { const float2 z = zeta[o]; m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y; }
+            re += T(m.x); im += T(m.y);
+        }
+        if (i == j) im = T(0);
+        typename V2<T>::t v; v.x = re; v.y = im;
+        A.a[tri(i, j, D)] = v;
+    }
+}
+
+template <int D, typename T>
+__device__ void build_table(unsigned short* tab) {
+    constexpr int n = D / 2;
+    const int t = threadIdx.x;
+    if (t < n) {
+        const int off = t * n - ((t * (t - 1)) >> 1);
+        for (int l = t; l < n; ++l) tab[off + (l - t)] = (unsigned short)((t << 8) | l);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const DevProblem P, const int32_t* __restrict__ cls,
+                                                                        const int32_t count, const int par, const int k) {
+    using S = CtaSmem<D, float>;
+    constexpr int NT = CtaCfg<D>::NT;
+    constexpr int W = D / 4;
+    constexpr int TR = CtaCfg<D>::TR, TC = CtaCfg<D>::TC;
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2* buf = reinterpret_cast<float2*>(sm);
+    RotC<float>* prm = reinterpret_cast<RotC<float>*>(sm + S::off_prm);
+    int* idx0 = reinterpret_cast<int*>(sm + S::off_idx);
+    int* idx1 = idx0 + D;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(sm + S::off_tab);
+    float* lam = reinterpret_cast<float*>(sm + S::off_lam);
+    float* pw = lam + D;
+    float* red = reinterpret_cast<float*>(sm + S::off_red);
+    const int t = threadIdx.x;
+    const int inst = blockIdx.x / count;
+    const int r = cls[blockIdx.x % count];
+    const RegionInfo R = P.reg[r];
+    const bool nest = P.st->variant == 1;
+    const float th = nest ? (float)P.st->theta[par] : 0.0f;
+    build_table<D, float>(tab);
+    if (t < D) idx0[t] = t;
+    Packed<float> A{buf, D};
+    assemble_packed<D, float>(P, R, inst, A, P.nu, nest ? P.zeta : nullptr, th, false);
+    __syncthreads();
+    const int row = t / 4, chunk = t % 4;
+    float vr[W], vi[W];
+#pragma unroll
+    for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
+    float norm2;
+    const int sweeps = jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2);
+    // the slot maps are back to the identity after whole sweeps: diag = eigenvalues
+    if (t < D) lam[t] = buf[tri(t, t, D)].x;
+    __syncthreads();
+    float lmin = lam[0];
+    for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
+    float F, Z = 0.f;
+    if (nest) {
+        const float beta = (float)P.st->beta;
+        for (int i = 0; i < D; ++i) Z += expf(-beta * (lam[i] - lmin));
+        F = lmin - logf(Z) / beta;
+        if (t < D) pw[t] = sqrtf(expf(-beta * (lam[t] - lmin)) / Z);
+    } else {
+        const float tau = (float)P.st->degen_tol * fmaxf(1.0f, sqrtf(norm2));
+        for (int i = 0; i < D; ++i) Z += (lam[i] - lmin <= tau) ? 1.f : 0.f;
+        F = lmin;
+        if (t < D) pw[t] = (lam[t] - lmin <= tau) ? sqrtf(1.0f / Z) : 0.f;
+    }
+    __syncthreads();
+    // W^T[c][row] = V[row][c] sqrt(p_c)   (overwrites the triangle, no longer needed)
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+        const int c = chunk * W + m;
+        const float q = pw[c];
+        buf[c * D + row] = make_float2(vr[m] * q, vi[m] * q);
+    }
+    __syncthreads();
+    // rho = W W^dagger in TR x TC register tiles: rho[i][c] = sum_k W[i][k] conj(W[c][k])
+    const int rb = t / (D / TC), cb = t % (D / TC);
+    const int i0 = rb * TR, c0 = cb * TC;
+    float accr[TR][TC], acci[TR][TC];
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) { accr[a][b] = 0.f; acci[a][b] = 0.f; }
+    for (int kk = 0; kk < D; ++kk) {
+        const float2* wk = buf + kk * D;
+        float2 wi[TR], wc[TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a) wi[a] = wk[i0 + a];
+#pragma unroll
+        for (int b = 0; b < TC; ++b) wc[b] = wk[c0 + b];
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) {
+                accr[a][b] += wi[a].x * wc[b].x + wi[a].y * wc[b].y;
+                acci[a][b] += wi[a].y * wc[b].x - wi[a].x * wc[b].y;
+            }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) buf[(i0 + a) * D + c0 + b] = make_float2(accr[a][b], acci[a][b]);
+    __syncthreads();
+    // exact Hermitian symmetry: lower triangle := conj(upper), real diagonal
+    for (int e = t; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        if (i > j) { const float2 u = buf[j * D + i]; buf[e] = make_float2(u.x, -u.y); }
+        else if (i == j) buf[e].y = 0.f;
+    }
+    __syncthreads();
+    if (R.rho_off >= 0) {
+        float4* dst = reinterpret_cast<float4*>(P.rho + (int64_t)inst * P.rho_elems + R.rho_off);
+        const float4* srcv = reinterpret_cast<const float4*>(buf);
+        for (int e = t; e < D * D / 2; e += NT) dst[e] = srcv[e];
+    }
+    float2* trb = P.tr + (int64_t)inst * P.msg_elems;
+    for (int q = R.child_begin; q < R.child_end; ++q) {
+        const PairInfo pi = P.pair[P.child_pairs[q]];
+        const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
+        for (int o = t; o < Df * Df; o += NT) {
+            const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
+            float sr = 0.f, si = 0.f;
+            for (int c = 0; c < nrest; ++c) {
+                const int x = pdep7(c, Mc);
+                const float2 v = buf[(ra | x) * D + (rbb | x)];
+                sr += v.x; si += v.y;
+            }
+            trb[pi.off + o] = make_float2(sr, si);
+        }
+    }
+    if (t == 0) {
+        P.val[(int64_t)inst * P.n_regions + r] = (double)F;
+        if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        atomicAdd(&P.sweeps[k], (unsigned long long)sweeps);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevProblem P, const int32_t* __restrict__ cls,
+                                                                    const int32_t count, const float2* __restrict__ msg) {
+    using S = CtaSmem<D, double>;
+    constexpr int W = D / 4;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2* buf = reinterpret_cast<double2*>(sm);
+    RotC<double>* prm = reinterpret_cast<RotC<double>*>(sm + S::off_prm);
+    int* idx0 = reinterpret_cast<int*>(sm + S::off_idx);
+    int* idx1 = idx0 + D;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(sm + S::off_tab);
+    double* red = reinterpret_cast<double*>(sm + S::off_red);
+    const int t = threadIdx.x;
+    const int inst = blockIdx.x / count;
+    const int r = cls[blockIdx.x % count];
+    const RegionInfo R = P.reg[r];
+    build_table<D, double>(tab);
+    if (t < D) idx0[t] = t;
+    Packed<double> A{buf, D};
+    assemble_packed<D, double>(P, R, inst, A, msg, nullptr, 0.0f, true);
+    __syncthreads();
+    double vr[W], vi[W];
+    double norm2;
+    jacobi_cta<D, double, false>(A, prm, idx0, idx1, tab, red, vr, vi, 40, 1e-28, norm2);
+    double lmin = buf[0].x;
+    for (int i = 1; i < D; ++i) lmin = fmin(lmin, buf[tri(i, i, D)].x);
+    if (t == 0) {
+        P.val64[(int64_t)inst * P.n_regions + r] = lmin;
+        if (!isfinite(lmin)) atomicOr(P.err, DEV_ERR_NUMERIC);
+    }
+}
+
+template <int D>
+cudaError_t pass_cta(const DevProblem& P, const int32_t* cls, int32_t count, int par, int k, cudaStream_t s) {
+    const int64_t blocks = (int64_t)P.n_inst * count;
+    region_pass_cta_kernel<D><<<(unsigned)blocks, CtaCfg<D>::NT, CtaSmem<D, float>::bytes, s>>>(P, cls, count, par, k);
+    return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t cert_cta(const DevProblem& P, const int32_t* cls, int32_t count, const float2* msg, cudaStream_t s) {
+    const int64_t blocks = (int64_t)P.n_inst * count;
+    certify_cta_kernel<D><<<(unsigned)blocks, CtaCfg<D>::NT, CtaSmem<D, double>::bytes, s>>>(P, cls, count, msg);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t prepare_cta_kernels() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(region_pass_cta_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CtaSmem<64, float>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(region_pass_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CtaSmem<128, float>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(certify_cta_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CtaSmem<64, double>::bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(certify_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)CtaSmem<128, double>::bytes);
+}
+
+cudaError_t launch_region_pass_cta(const DevProblem& P, int k, const int32_t* cls, int32_t count, int par, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (k == 6) return pass_cta<64>(P, cls, count, par, k, s);
+    if (k == 7) return pass_cta<128>(P, cls, count, par, k, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* cls, int32_t count, const float2* msg,
+                               cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    if (k == 6) return cert_cta<64>(P, cls, count, msg, s);
+    if (k == 7) return cert_cta<128>(P, cls, count, msg, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lrh

@@ -1,6 +1,7 @@
 // Internal device-side layout of an lrh problem (not part of the C ABI).
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace lrh {
@@ -13,6 +14,16 @@ struct RegionInfo {
     int32_t child_end;
     int32_t parent_begin;  // [parent_begin, parent_end) into parent_pairs: pairs g->e with e = this
     int32_t parent_end;
+    int64_t all_off;       // complex offset of D x D in an arena holding every region (adjoint)
+};
+
+// One Hamiltonian term, for the adjoint's term cotangents.
+struct TermInfo {
+    int64_t out_off;       // complex offset of the D_t x D_t block in one instance's term array
+    int32_t region;        // region the term is placed in
+    int32_t mask;          // bits of the region's basis index that carry the term's sites
+    int32_t kt;            // term sites
+    int32_t dr;            // D of the region holding the term
 };
 
 // One covering pair e -> f.
@@ -54,6 +65,7 @@ struct DevProblem {
     const PairInfo* pair;
     const int32_t* child_pairs;
     const int32_t* parent_pairs;
+    const int32_t* chunk_pair;   // [msg_elems / 4] pair owning complex entries 4c .. 4c+3
     const float2* h32;     // [n_inst][h_elems]
     const double2* h64;    // [n_inst][h_elems]
     float2* nu;            // [n_inst][msg_elems]
@@ -70,11 +82,28 @@ struct DevProblem {
     IterState* st;
     int32_t* err;
     unsigned long long* sweeps;   // [8] per size class (indexed by k)
+    // adjoint (allocated on the first lrh_vjp call)
+    int64_t all_elems;     // complex entries of the every-region arena per instance
+    int32_t n_terms;
+    int32_t pad2;
+    int64_t term_total;    // complex entries of one instance's term array
+    const TermInfo* terms;
+    float2* thb;           // [n_inst][all_elems] theta_bar of every region
+    float2* gbar;          // [n_inst][msg_elems] cotangent of the gradient output
+    double* qbar;          // [n_inst] cotangent of Q_beta
 };
+
+// Record `msg` as the thread-local detail returned by lrh_last_error; returns `code`.
+int set_last_error(int code, const std::string& msg);
 
 // Kernel attributes (dynamic shared memory limits) for the current device; called once per
 // problem creation, outside any stream capture.
 cudaError_t prepare_kernels();
+cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128)
+cudaError_t launch_region_pass_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
+                                   int par, cudaStream_t s);
+cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
+                               const float2* msg, cudaStream_t s);
 
 // Launchers (lrh_kernels.cu).  All enqueue on `s` and return the launch status.
 cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* class_regions,
@@ -87,6 +116,12 @@ cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double 
                              double beta, double inv_lhat, double alpha, double degen_tol,
                              int variant, int step_rule, int max_sweeps, cudaStream_t s);
 cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t s);
+
+// Adjoint (lrh_vjp.cu): theta_bar per region for the classes, then nu_bar and term cotangents.
+cudaError_t prepare_vjp_kernels();
+cudaError_t launch_vjp_region(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count, int par,
+                              cudaStream_t s);
+cudaError_t launch_vjp_outputs(const DevProblem& P, float2* nu_bar, float2* term_bar, cudaStream_t s);
 
 // update modes
 enum : int { UPD_STEP = 0, UPD_GRAD_ONLY = 1 };

@@ -21,6 +21,7 @@
 // D = 2 uses the closed form of a 2 x 2 Hermitian matrix.  FP64 is used only by the
 // certification pass (lambda_min of theta rebuilt in FP64) and by the bound reduction.
 #include "lrh_internal.cuh"
+#include "lrh_device.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -30,252 +31,8 @@ namespace lrh {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 128;
-
-// Source slot of the round-robin tournament: after a round, slot s receives the content of
-// slot rr_src(s).  Slot 0 is fixed, the other D-1 slots form one cycle, so D-1 rounds visit
-// every unordered pair exactly once and restore the natural order.
-__host__ __device__ constexpr int rr_src(int s, int D) {
-    return s == 0 ? 0 : (s == 2 ? 1 : ((s & 1) == 0 ? s - 2 : (s == D - 1 ? D - 2 : s + 2)));
-}
-
-__device__ __forceinline__ int pext_bits(int x, int m) {
-    int r = 0, k = 0;
-#pragma unroll
-    for (int b = 0; b < 7; ++b) {
-        if ((m >> b) & 1) { r |= ((x >> b) & 1) << k; ++k; }
-    }
-    return r;
-}
-
-__device__ __forceinline__ int pdep_bits(int x, int m) {
-    int r = 0, k = 0;
-#pragma unroll
-    for (int b = 0; b < 7; ++b) {
-        if ((m >> b) & 1) { r |= ((x >> k) & 1) << b; ++k; }
-    }
-    return r;
-}
-
-template <int W, typename T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o, W);
-    return v;
-}
-
-template <int W, typename T>
-__device__ __forceinline__ T group_min(T v) {
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) {
-        T u = __shfl_xor_sync(kFull, v, o, W);
-        v = u < v ? u : v;
-    }
-    return v;
-}
-
-template <typename T> struct alignas(4 * sizeof(T)) Rot { T c, wr, wi, pad; };
-
-__device__ __forceinline__ float my_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double my_sqrt(double x) { return sqrt(x); }
-
-// Jacobi rotation of the Hermitian 2x2 block [[app, b], [conj(b), aqq]]:
-// J = [[c, -w], [conj(w), c]] with w = sigma b, sigma real, makes (J^H A J)_pq = 0.
-// With h = aqq - app and r = sqrt(h^2 + 4|b|^2): t = -sgn(h) 2|b| / (|h| + r),
-// c = 1 / sqrt(1 + t^2), sigma = -sgn(h) 2 c / (|h| + r)  (no division by |b|).
-template <typename T>
-__device__ __forceinline__ void rot_params(T app, T aqq, T br, T bi, T& c, T& wr, T& wi) {
-    const T h = aqq - app;
-    const T b2 = br * br + bi * bi;
-    const T r = my_sqrt(h * h + T(4) * b2);
-    const T den = fabs(h) + r;
-    const T sg = h >= T(0) ? T(1) : T(-1);
-    T t = T(0), sig = T(0);
-    if (den > T(0)) t = -sg * T(2) * my_sqrt(b2) / den;
-    c = T(1) / my_sqrt(T(1) + t * t);
-    if (den > T(0)) sig = -sg * T(2) * c / den;
-    wr = sig * br;
-    wi = sig * bi;
-}
-
-// x[s & ~1] and x[s | 1] of a register row, by a select tree on the bits of s above bit 0.
-// Template recursion keeps every register index a compile-time constant.
-template <int HALF, int D, typename T>
-struct PickLevel {
-    static __device__ __forceinline__ void run(T (&t)[D], int s) {
-        const bool hi = (s & HALF) != 0;
-#pragma unroll
-        for (int j = 0; j < HALF; ++j) t[j] = hi ? t[j + HALF] : t[j];
-        PickLevel<HALF / 2, D, T>::run(t, s);
-    }
-};
-template <int D, typename T>
-struct PickLevel<1, D, T> {
-    static __device__ __forceinline__ void run(T (&)[D], int) {}
-};
-
-template <int D, typename T>
-__device__ __forceinline__ void pick_pair(const T (&x)[D], int s, T& x0, T& x1) {
-    T t[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) t[j] = x[j];
-    PickLevel<D / 2, D, T>::run(t, s);
-    x0 = t[0];
-    x1 = t[1];
-}
-
-// Column rotation of slots (p, q) = (2k, 2k+1): x_p' = c x_p + conj(w) x_q, x_q' = -w x_p + c x_q.
-template <typename T>
-__device__ __forceinline__ void mix_cols(T& pr, T& pi, T& qr, T& qi, T c, T wr, T wi) {
-    const T npr = c * pr + (wr * qr + wi * qi);
-    const T npi = c * pi + (wr * qi - wi * qr);
-    const T nqr = c * qr - (wr * pr - wi * pi);
-    const T nqi = c * qi - (wr * pi + wi * pr);
-    pr = npr; pi = npi; qr = nqr; qi = nqi;
-}
-
-// Cyclic complex Jacobi on the D x D Hermitian matrix held by a group of D lanes (row per
-// lane).  Returns the sweeps run (uniform over the warp).  On return the slots are in natural
-// order: lane s holds lambda_s on its diagonal entry and, if WANT_V, row s of V whose column c
-// is the eigenvector of lambda_c.  `norm2` receives ||theta||_F^2.
-template <int D, typename T, bool WANT_V>
-__device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], T (&vi)[D], const int s,
-                                            Rot<T>* prm, const int max_sweeps, const T tol2, T& norm2) {
-    T n2 = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) n2 += ar[c] * ar[c] + ai[c] * ai[c];
-    n2 = group_sum<D>(n2);
-    norm2 = n2;
-    const T thresh = tol2 * n2;
-    int sweeps = 0;
-    for (;;) {
-        T off = T(0);
-#pragma unroll
-        for (int c = 0; c < D; ++c) off += (c == s) ? T(0) : (ar[c] * ar[c] + ai[c] * ai[c]);
-        off = group_sum<D>(off);
-        const bool done = (off <= thresh) || (sweeps >= max_sweeps);
-        if (__all_sync(kFull, done)) break;
-        ++sweeps;
-        for (int r = 0; r < D - 1; ++r) {
-            // (1) parameters of pair k = s >> 1 (both lanes of the pair compute them from the
-            //     same shuffled values, so they agree bit for bit)
-            T e0r, e1r, e0i, e1i;
-            pick_pair<D>(ar, s, e0r, e1r);
-            pick_pair<D>(ai, s, e0i, e1i);
-            const bool odd = (s & 1) != 0;
-            const T mydiag = odd ? e1r : e0r;
-            const T offr = odd ? e0r : e1r;
-            const T offi = odd ? e0i : e1i;
-            const T pdiag = __shfl_xor_sync(kFull, mydiag, 1, D);
-            const T br = __shfl_sync(kFull, offr, s & ~1, D);
-            const T bi = __shfl_sync(kFull, offi, s & ~1, D);
-            const T app = odd ? pdiag : mydiag;
-            const T aqq = odd ? mydiag : pdiag;
-            T c, wr, wi;
-            rot_params(app, aqq, br, bi, c, wr, wi);
-            if (!odd) prm[s >> 1] = Rot<T>{c, wr, wi, T(0)};
-            __syncwarp();
-            // (2) column rotations of A and V (all pairs)
-#pragma unroll
-            for (int k = 0; k < D / 2; ++k) {
-                const Rot<T> P = prm[k];
-                mix_cols(ar[2 * k], ai[2 * k], ar[2 * k + 1], ai[2 * k + 1], P.c, P.wr, P.wi);
-                if (WANT_V) mix_cols(vr[2 * k], vi[2 * k], vr[2 * k + 1], vi[2 * k + 1], P.c, P.wr, P.wi);
-            }
-            // (3) row rotation fused with the tournament permutation of rows and columns:
-            //     new A[s][c] = (J^H A)[o][rr_src(c)] with o = rr_src(s)
-            const int o = rr_src(s, D);
-            const Rot<T> Q = prm[o >> 1];
-            const bool oodd = (o & 1) != 0;
-            const T sgn = oodd ? T(-1) : T(1);
-            const T qwi = oodd ? -Q.wi : Q.wi;
-            T nr[D], ni[D];
-#pragma unroll
-            for (int cc = 0; cc < D; ++cc) {
-                const int sc = rr_src(cc, D);
-                const T r1r = __shfl_sync(kFull, ar[sc], o, D);
-                const T r1i = __shfl_sync(kFull, ai[sc], o, D);
-                const T r2r = __shfl_sync(kFull, ar[sc], o ^ 1, D);
-                const T r2i = __shfl_sync(kFull, ai[sc], o ^ 1, D);
-                nr[cc] = Q.c * r1r + sgn * (Q.wr * r2r - qwi * r2i);
-                ni[cc] = Q.c * r1i + sgn * (Q.wr * r2i + qwi * r2r);
-            }
-#pragma unroll
-            for (int cc = 0; cc < D; ++cc) { ar[cc] = nr[cc]; ai[cc] = ni[cc]; }
-            if (WANT_V) {
-                T tr_[D], ti_[D];
-#pragma unroll
-                for (int cc = 0; cc < D; ++cc) { tr_[cc] = vr[rr_src(cc, D)]; ti_[cc] = vi[rr_src(cc, D)]; }
-#pragma unroll
-                for (int cc = 0; cc < D; ++cc) { vr[cc] = tr_[cc]; vi[cc] = ti_[cc]; }
-            }
-            __syncwarp();
-        }
-    }
-    return sweeps;
-}
-
-// Gather row s of theta_e = h_e - sum_children 1 (x) m_{e->f} + sum_parents m_{g->e}, with the
-// message m = (1 - th) nu + th zeta (th = 0 for nu alone).  Source element type S, target T.
-template <int D, typename T>
-__device__ __forceinline__ void assemble_row(const DevProblem& P, const RegionInfo& R, int inst, int s,
-                                             const float2* __restrict__ nu, const float2* __restrict__ zeta,
-                                             float th, bool use_h64, T (&ar)[D], T (&ai)[D]) {
-    if (R.h_off >= 0) {
-        if (use_h64) {
-            const double2* hrow = P.h64 + (int64_t)inst * P.h_elems + R.h_off + (int64_t)s * D;
-#pragma unroll
-            for (int c = 0; c < D; ++c) { const double2 v = hrow[c]; ar[c] = T(v.x); ai[c] = T(v.y); }
-        } else {
-            const float4* hrow = reinterpret_cast<const float4*>(P.h32 + (int64_t)inst * P.h_elems + R.h_off + (int64_t)s * D);
-#pragma unroll
-            for (int c = 0; c < D / 2; ++c) {
-                const float4 v = hrow[c];
-                ar[2 * c] = T(v.x); ai[2 * c] = T(v.y); ar[2 * c + 1] = T(v.z); ai[2 * c + 1] = T(v.w);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < D; ++c) { ar[c] = T(0); ai[c] = T(0); }
-    }
-    const int64_t mbase = (int64_t)inst * P.msg_elems;
-    const float om = 1.0f - th;
-    for (int q = R.child_begin; q < R.child_end; ++q) {
-        const PairInfo pi = P.pair[P.child_pairs[q]];
-        const int M = pi.mask;
-        const int Df = 1 << pi.kf;
-        const int a = pext_bits(s, M);
-        const int rest = s & ~M;
-        const float2* nb = nu + mbase + pi.off + (int64_t)a * Df;
-        const float2* zb = zeta ? zeta + mbase + pi.off + (int64_t)a * Df : nullptr;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            if ((c & ~M) == rest) {
-                const int b = pext_bits(c, M);
-                float2 m = nb[b];
-                if (zb) { const float2 z = zb[b]; m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y; }
-                ar[c] -= T(m.x);
-                ai[c] -= T(m.y);
-            }
-        }
-    }
-    for (int q = R.parent_begin; q < R.parent_end; ++q) {
-        const PairInfo pi = P.pair[P.parent_pairs[q]];
-        const float4* nb = reinterpret_cast<const float4*>(nu + mbase + pi.off + (int64_t)s * D);
-        const float4* zb = zeta ? reinterpret_cast<const float4*>(zeta + mbase + pi.off + (int64_t)s * D) : nullptr;
-#pragma unroll
-        for (int c = 0; c < D / 2; ++c) {
-            float4 m = nb[c];
-            if (zb) {
-                const float4 z = zb[c];
-                m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y;
-                m.z = om * m.z + th * z.z; m.w = om * m.w + th * z.w;
-            }
-            ar[2 * c] += T(m.x); ai[2 * c] += T(m.y); ar[2 * c + 1] += T(m.z); ai[2 * c + 1] += T(m.w);
-        }
-    }
-}
+using namespace dev;
 
 template <int D>
 struct PassSmem {
@@ -366,6 +123,24 @@ __global__ void __launch_bounds__(kBlock) region_pass_kernel(const DevProblem P,
             acci += ai[2 * c + 1] * x.z - ar[2 * c + 1] * x.w;
         }
         Rb[s * D + j] = make_float2(accr, acci);
+    }
+    __syncwarp();
+    // Make rho exactly Hermitian (the two triangles come from differently rounded sums):
+    // row s keeps its upper part, takes the conjugate of the upper part for j < s, and a
+    // real diagonal.  Exactly Hermitian states keep every message exactly Hermitian.
+    {
+        float2 fix[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float2 up = Rb[j * D + s];
+            fix[j] = make_float2(up.x, -up.y);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            if (j < s) Rb[s * D + j] = fix[j];
+            if (j == s) Rb[s * D + j].y = 0.f;
+        }
     }
     __syncwarp();
     if (valid) {
@@ -529,15 +304,6 @@ __global__ void certify_d2_kernel(const DevProblem P, const int32_t* __restrict_
 }
 
 // ---------------------------------------------------------------- message update
-__device__ __forceinline__ int find_pair(const PairInfo* __restrict__ pairs, int n, int64_t e) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (pairs[mid].off <= e) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // One thread per two consecutive complex entries of one instance's message array (every
 // block holds D_f^2 >= 4 entries, so the two never straddle pairs).
 __global__ void update_kernel(const DevProblem P, const int par, const int mode) {
@@ -553,7 +319,7 @@ __global__ void update_kernel(const DevProblem P, const int par, const int mode)
     if (tid >= (int64_t)P.n_inst * halfm) return;
     const int inst = (int)(tid / halfm);
     const int64_t e = (tid % halfm) * 2;
-    const int p = find_pair(P.pair, P.n_pairs, e);
+    const int p = P.chunk_pair[e >> 2];
     const PairInfo pi = P.pair[p];
     const RegionInfo Rf = P.reg[pi.child];
     const int64_t mi = (int64_t)inst * P.msg_elems + e;
@@ -657,7 +423,8 @@ cudaError_t prepare_kernels() {
     if ((e = set_pass_attr<4>()) != cudaSuccess) return e;
     if ((e = set_pass_attr<8>()) != cudaSuccess) return e;
     if ((e = set_pass_attr<16>()) != cudaSuccess) return e;
-    return set_pass_attr<32>();
+    if ((e = set_pass_attr<32>()) != cudaSuccess) return e;
+    return prepare_cta_kernels();
 }
 
 cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* cls, int32_t count, int par,
@@ -673,6 +440,8 @@ cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* cls, i
         case 3: return launch_pass_D<8>(P, cls, count, par, k, s);
         case 4: return launch_pass_D<16>(P, cls, count, par, k, s);
         case 5: return launch_pass_D<32>(P, cls, count, par, k, s);
+        case 6:
+        case 7: return launch_region_pass_cta(P, k, cls, count, par, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -690,6 +459,8 @@ cudaError_t launch_certify(const DevProblem& P, int k, const int32_t* cls, int32
         case 3: return launch_cert_D<8>(P, cls, count, msg, s);
         case 4: return launch_cert_D<16>(P, cls, count, msg, s);
         case 5: return launch_cert_D<32>(P, cls, count, msg, s);
+        case 6:
+        case 7: return launch_certify_cta(P, k, cls, count, msg, s);
         default: return cudaErrorInvalidValue;
     }
 }

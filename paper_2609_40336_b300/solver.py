@@ -191,6 +191,52 @@ class Solver:
         L.check(self._lib.lrh_get_messages(self._h, _MSGS[which], arr.ctypes.data, nbytes, 0), "lrh_get_messages")
         return arr
 
+    def set_terms(self, term_mats) -> None:
+        """Replace the term matrices (same supports as at creation); list of
+        (n_instances, D_t, D_t) arrays, or the flat float64 host layout."""
+        if isinstance(term_mats, np.ndarray) and term_mats.dtype == np.float64 and term_mats.ndim == 1:
+            flat = np.ascontiguousarray(term_mats)
+        else:
+            mats = [np.asarray(m) for m in term_mats]
+            mats = [m[None] if m.ndim == 2 else m for m in mats]
+            flat = np.ascontiguousarray(np.concatenate([m.reshape(self.n_instances, -1) for m in mats], axis=1)
+                                        .astype(np.complex128)).view(np.float64).reshape(-1)
+        L.check(self._lib.lrh_set_terms(self._h, flat.ctypes.data), "lrh_set_terms")
+
+    def vjp(self, q_bar, g_bar=None):
+        """Adjoint of the smoothed evaluation at the current point: returns
+        (nu_bar complex64 (n_instances, msg_elems), term_bar complex64 (n_instances, term_total))."""
+        q = np.ascontiguousarray(np.broadcast_to(np.asarray(q_bar, np.float64), (self.n_instances,)))
+        nu_bar = np.zeros((self.n_instances, self.msg_elems), np.complex64)
+        total = int(self._keep["term_mats"].size // (2 * self.n_instances))
+        term_bar = np.zeros((self.n_instances, total), np.complex64)
+        gb = None
+        if g_bar is not None:
+            gb = np.ascontiguousarray(np.asarray(g_bar, np.complex64).reshape(self.n_instances, self.msg_elems))
+        L.check(self._lib.lrh_vjp(self._h, q.ctypes.data, gb.ctypes.data if gb is not None else None, 0,
+                                  nu_bar.ctypes.data, term_bar.ctypes.data, 0), "lrh_vjp")
+        return nu_bar, term_bar
+
+    def vjp_device(self, q_bar, g_bar=None):
+        """Adjoint with device tensors: q_bar (n_instances,) any tensor/array, g_bar a CUDA
+        complex64 tensor (n_instances, msg_elems) or None.  Returns CUDA complex64 tensors
+        (nu_bar, term_bar)."""
+        import torch
+        q = np.ascontiguousarray(np.broadcast_to(np.asarray(
+            q_bar.detach().cpu().numpy() if hasattr(q_bar, "detach") else q_bar, np.float64), (self.n_instances,)))
+        total = int(self._keep["term_mats"].size // (2 * self.n_instances))
+        dev = g_bar.device if g_bar is not None else torch.device("cuda", torch.cuda.current_device())
+        nu_bar = torch.empty((self.n_instances, self.msg_elems), dtype=torch.complex64, device=dev)
+        term_bar = torch.empty((self.n_instances, total), dtype=torch.complex64, device=dev)
+        gptr = None
+        if g_bar is not None:
+            g_bar = g_bar.contiguous()
+            assert g_bar.dtype == torch.complex64 and g_bar.is_cuda
+            gptr = C.c_void_p(g_bar.data_ptr())
+        L.check(self._lib.lrh_vjp(self._h, q.ctypes.data, gptr, 1, C.c_void_p(nu_bar.data_ptr()),
+                                  C.c_void_p(term_bar.data_ptr()), 1), "lrh_vjp")
+        return nu_bar, term_bar
+
     def set_messages(self, which: str, src) -> None:
         nbytes = self.n_instances * self.msg_elems * 8
         if hasattr(src, "data_ptr") and getattr(src, "is_cuda", False):

@@ -59,9 +59,9 @@ def _code(p):
     return ei.value.code
 
 
-def test_unsupported_region_size_is_rejected():
-    p = g.Problem(6, [tuple(range(6))], [(0, 1)], [g.lattices.ZZ[None]])
-    assert _code(p) == -8
+def test_region_beyond_seven_sites_is_rejected():
+    p = g.Problem(8, [tuple(range(8))], [(0, 1)], [g.lattices.ZZ[None]])
+    assert _code(p) == -1
 
 
 def test_duplicate_region_is_rejected():

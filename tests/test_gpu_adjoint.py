@@ -1,0 +1,76 @@
+"""GPU adjoint (lrh_vjp) vs the FP64 oracle's reverse-mode derivative on the same state.
+
+Tolerance: relative 1e-4 in the Frobenius norm (FP32 eigensolve; the derivative of the
+Gibbs state carries the beta/2 Lipschitz factor of its lemma)."""
+import numpy as np
+import pytest
+
+import lrh_gen as g
+from oracle import adjoint, dual
+from oracle.poset import Poset
+from tests.gpu_helpers import random_traceless_messages
+
+pytestmark = pytest.mark.gpu
+L = g.lattices
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2609_40336_b300 import Solver  # noqa: E402
+
+CASES = {
+    "j1j2_4_plaq": (lambda: L.j1j2_square(4), 4.0),
+    "chain_L3_D8": (lambda: L.random_chain(10, 5, L=3), 2.0),
+    "xxz_tri4": (lambda: L.xxz_triangular(4, 2), 3.0),
+    "chain_L5_D32": (lambda: L.random_chain(12, 9, L=5, scale=0.4), 1.5),
+}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-6))
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_vjp_matches_oracle(name):
+    build, beta = CASES[name]
+    p = build()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    nu = random_traceless_messages(P, p.n_instances, seed=31, scale=0.5)
+    gb = random_traceless_messages(P, p.n_instances, seed=32, scale=1.0)
+    qb = np.linspace(0.5, 1.5, p.n_instances)
+    s = Solver(p, variant="nesterov", beta=beta)
+    s.set_messages("nu", nu)
+    s.restart()
+    nu_bar, term_bar = s.vjp(qb, gb)
+    r_nu, r_T, _ = adjoint.smoothed_vjp(p, P, h, nu.astype(np.complex128), beta, qb, gb.astype(np.complex128))
+    assert rel(nu_bar.astype(np.complex128), r_nu) <= 1e-4
+    flat_T = np.concatenate([t.reshape(p.n_instances, -1) for t in r_T], axis=1)
+    assert rel(term_bar.astype(np.complex128), flat_T) <= 1e-4
+
+
+def test_vjp_envelope_equals_gradient():
+    """g_bar = 0, q_bar = 1: nu_bar is the gradient of Q_beta (lrh_evaluate's g)."""
+    p = L.j1j2_square(4, J2s=(0.5,))
+    P = Poset(p.regions)
+    nu = random_traceless_messages(P, 1, seed=33, scale=0.5)
+    s = Solver(p, variant="nesterov", beta=8.0)
+    s.set_messages("nu", nu)
+    s.restart()
+    s.evaluate()
+    gref = s.messages("grad")
+    nu_bar, _ = s.vjp(np.ones(1), None)
+    assert rel(nu_bar, gref) <= 1e-5
+
+
+def test_set_terms_changes_the_evaluation_like_the_oracle():
+    p = L.j1j2_square(4, J2s=(0.25,))
+    P = Poset(p.regions)
+    s = Solver(p, variant="nesterov", beta=4.0)
+    p2 = L.j1j2_square(4, J2s=(0.5,))
+    s.set_terms(p2.term_mats)
+    s.evaluate()
+    h2 = dual.local_terms(p2, P)
+    ref = dual.region_pass(P, h2, dual.zeros_messages(P, 1), "smooth", beta=4.0)
+    assert abs(s.bound("last")[0] - ref.value.sum()) <= 1e-5 * abs(ref.value.sum())

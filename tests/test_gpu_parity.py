@@ -27,6 +27,8 @@ CASES = {
     "chain_L3_D8": lambda: L.random_chain(12, 5, L=3),
     "chain_L4_D16": lambda: L.perturbed_chain(40, L=4, delta=0.3, seed=7),
     "chain_L5_D32": lambda: L.random_chain(23, 9, L=5, scale=0.4),
+    "chain_L6_D64": lambda: L.random_chain(9, 15, L=6, scale=0.3),
+    "chain_L7_D128": lambda: L.perturbed_chain(9, L=7, delta=0.5, seed=3),
     "xxz_tri4_plaq": lambda: L.xxz_triangular(4, 3),
     "j1j2_4_plaq": lambda: L.j1j2_square(4),
 }
