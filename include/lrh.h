@@ -213,6 +213,32 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
 /* Wait for the problem's stream and report any device-side numeric error (LRH_ENUMERIC). */
 int lrh_synchronize(lrh_problem* p);
 
+/* Allocation-free evaluation of a pairwise (level-1: edges + sites) smoothed dual.
+ * The paper has no counterpart of this entry point; it exists for callers that cannot call
+ * cudaMalloc (code inside another runtime's allocator or memory pool, processes whose device
+ * memory is reserved up front) and therefore cannot use lrh_create.  It computes what
+ * lrh_evaluate computes for a Nesterov problem whose regions are the given edges and all
+ * sites (with eta = nu): Q_beta = sum of F_beta over edges and sites, and the gradient
+ * g_{e->v} = rho_v - Tr_{e} rho_e, using only caller-owned buffers plus a fixed scratch
+ * array compiled into the library (about 5.5 MB of device memory on every GPU that loads the
+ * library, held until the process exits).  Limits: n_sites <= 65536, n_edges <= 131072;
+ * larger sizes return LRH_EINVAL.
+ *   edges    device int32 [n_edges][2]: the two DISTINCT sites of each edge; the first one
+ *            is the most significant factor of the edge's 4 x 4 index
+ *   h_edge   device complex64 [n_edges][4][4] edge terms in that order, or NULL (zero)
+ *   h_site   device complex64 [n_sites][2][2] site terms, or NULL (zero)
+ *   nu       device complex64 [n_edges][2][2][2]: nu_{e->first site}, then nu_{e->second site}
+ *   beta     smoothing inverse temperature (> 0)
+ *   value_out device double [1] receives Q_beta; grad_out device complex64 [n_edges][2][2][2]
+ * Every matrix must be Hermitian (only upper triangles of 2 x 2 blocks are read for sites).
+ * Asynchronous on `stream` (a cudaStream_t or NULL).  Calls share the scratch array: calls that
+ * may overlap on the GPU race and must be ordered by the caller.  The first call on a device
+ * looks up the scratch address for that device; make it before any stream capture.  Calls no
+ * allocating routine. */
+int lrh_level1_eval_noalloc(int32_t n_sites, int32_t n_edges, const int32_t* edges, const void* h_edge,
+                            const void* h_site, const void* nu, double beta, double* value_out,
+                            void* grad_out, void* stream);
+
 /* Static message for an error code, and the thread-local detail of the last failure. */
 const char* lrh_strerror(int code);
 const char* lrh_last_error(void);

@@ -90,6 +90,8 @@ SIGNATURES = {
     "lrh_synchronize": (C.c_int, [C.c_void_p]),
     "lrh_set_terms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lrh_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
+    "lrh_level1_eval_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lrh_strerror": (C.c_char_p, [C.c_int]),
     "lrh_last_error": (C.c_char_p, []),
 }

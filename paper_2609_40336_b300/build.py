@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblrh.so")
-SOURCES = ["lrh_api.cu", "lrh_kernels.cu", "lrh_cta.cu", "lrh_vjp.cu"]
+SOURCES = ["lrh_api.cu", "lrh_kernels.cu", "lrh_cta.cu", "lrh_vjp.cu", "lrh_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
