@@ -130,6 +130,9 @@ typedef struct {
     int32_t class_sites[8];       /* k of each class                                           */
     int32_t class_regions[8];     /* regions per instance of each class                        */
     uint64_t sweeps[8];           /* cumulative FP32 Jacobi sweeps x regions, per class        */
+    int32_t class_block[8];       /* threads per CTA of each class's region pass (autotuned);
+                                     negative: one thread per region (4 x 4 regions)            */
+    int32_t concurrent_classes;   /* 1: region classes run on forked streams within an iteration */
 } lrh_info;
 
 /* ---------------------------------------------------------------- entry points */
@@ -155,7 +158,8 @@ int lrh_get_pairs(const lrh_problem* p, int32_t* parent, int32_t* child, int64_t
 int lrh_set_options(lrh_problem* p, const lrh_options* opts);
 
 /* Start a new smoothing stage: theta = 1 and zeta = nu (beta-continuation restart), and
- * reset the step counter t used by LRH_STEP_INV_SQRT. Stream-ordered. */
+ * reset the step counter t used by LRH_STEP_INV_SQRT.  For LRH_SUBGRADIENT it also starts a
+ * new best-so-far record (q_best = -inf).  Stream-ordered (synchronises for LRH_SUBGRADIENT). */
 int lrh_restart(lrh_problem* p);
 
 /* Run n_iters iterations of the selected algorithm (asynchronous). */
@@ -209,6 +213,30 @@ int lrh_set_terms(lrh_problem* p, const double* term_mats);
  * The first call allocates the adjoint buffers.  Synchronises. */
 int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_bar_is_device, void* nu_bar,
             void* term_bar, int32_t out_is_device);
+
+/* Autotuner.  Times, on this problem's own data and stream, the launch shapes of every region
+ * class with at most 5 sites (64, 128 or 256 threads per CTA, i.e. 64/D .. 256/D regions per
+ * CTA) and whether the classes of one iteration run concurrently on forked streams, then
+ * keeps the fastest.  Choices are read from / appended to `cache_path` (JSON lines keyed by
+ * class size, region count and SM count; NULL = no cache); flags bit 0 forces re-measuring.
+ * Runs region passes at the current point (their outputs are recomputed by the next
+ * iteration), must not be called during stream capture, and synchronises. */
+int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
+
+/* Set the launch shape of one region class by hand (what lrh_autotune chooses): 64, 128 or
+ * 256 threads per CTA with 2^k_sites lanes per region, or for 4 x 4 regions -64, -128, -256 for
+ * one thread per region.  The lane layouts give bit-identical results; the one-thread layout
+ * rotates in another order and agrees to rounding. */
+int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block);
+
+/* Checkpoint / resume.  The state is the iteration scalars (theta_k, step counter, beta,
+ * L_hat, alpha, iteration parity), nu, zeta, nu_best and q_best, packed into one host buffer
+ * of lrh_state_bytes() bytes; lrh_set_state accepts only a buffer from a problem with the same
+ * instance count, message layout and variant.  Resuming from a saved state and iterating gives
+ * bit-identical messages to an uninterrupted run.  Both synchronise. */
+int64_t lrh_state_bytes(const lrh_problem* p);
+int lrh_get_state(lrh_problem* p, void* buf, int64_t bytes);
+int lrh_set_state(lrh_problem* p, const void* buf, int64_t bytes);
 
 /* Wait for the problem's stream and report any device-side numeric error (LRH_ENUMERIC). */
 int lrh_synchronize(lrh_problem* p);

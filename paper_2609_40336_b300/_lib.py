@@ -63,6 +63,8 @@ class Info(C.Structure):
         ("class_sites", C.c_int32 * 8),
         ("class_regions", C.c_int32 * 8),
         ("sweeps", C.c_uint64 * 8),
+        ("class_block", C.c_int32 * 8),
+        ("concurrent_classes", C.c_int32),
     ]
 
 
@@ -89,6 +91,11 @@ SIGNATURES = {
     "lrh_set_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrh_synchronize": (C.c_int, [C.c_void_p]),
     "lrh_set_terms": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lrh_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32]),
+    "lrh_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "lrh_state_bytes": (C.c_int64, [C.c_void_p]),
+    "lrh_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "lrh_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "lrh_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
     "lrh_level1_eval_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -80,8 +80,9 @@ struct lrh_problem {
     std::vector<void*> allocs;
     double* h_pinned = nullptr;   // host staging for bound / values
     int64_t h_pinned_len = 0;
-    cudaGraph_t graph = nullptr;
+    cudaGraph_t graph = nullptr;            // Alg. 1: graph of kGraphChunk iterations
     cudaGraphExec_t graph_exec = nullptr;
+    std::vector<std::pair<int, cudaGraphExec_t>> nest_graphs;   // Alg. 2: one per n_iters
     // term structure (for lrh_set_terms and the adjoint)
     int32_t n_terms = 0;
     int64_t term_total = 0;
@@ -91,6 +92,14 @@ struct lrh_problem {
     int64_t all_elems = 0;
     float2* vjp_nubar = nullptr;    // adjoint outputs staged on the device
     float2* vjp_termbar = nullptr;
+    // region classes after the first run on forked streams (joined before the update)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
+    // launch shape per class (threads per CTA of the lane kernels) and stream concurrency,
+    // chosen by lrh_autotune (defaults: 128 threads, concurrent classes)
+    std::vector<int> class_block;
+    bool concurrent = true;
 
     template <typename T>
     int dalloc(T** ptr, int64_t count) {
@@ -104,6 +113,10 @@ struct lrh_problem {
         return LRH_OK;
     }
     ~lrh_problem() {
+        for (auto& g : nest_graphs) cudaGraphExecDestroy(g.second);
+        for (cudaStream_t a : aux) cudaStreamDestroy(a);
+        for (cudaEvent_t e : ev_join) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         for (void* p : allocs) cudaFree(p);
@@ -191,9 +204,112 @@ int check_terms(const lrh_problem* p, const int64_t* term_ptr, const double* ter
     return LRH_OK;
 }
 
+PassIO plain_io(const lrh_problem* p) {
+    PassIO io{};
+    io.nu_in = p->P.nu;
+    io.zeta_in = p->opt.variant == LRH_NESTEROV ? p->P.zeta : nullptr;
+    io.rho_out = p->P.rho;
+    io.tr_out = p->P.tr;
+    return io;
+}
+
+// Region pass of every size class: class 0 on the problem's stream, the others on forked
+// streams (independent work: disjoint outputs, read-only inputs; in a pending pass every
+// updated message has exactly one owner), joined afterwards.  Only class 0 may be `writer`.
+int launch_all_classes(lrh_problem* p, const PassIO& io0) {
+    const size_t nc = p->class_k.size();
+    PassIO io = io0;
+    io.writer = 0;
+    if (!p->concurrent || nc < 2) {
+        for (size_t c = 0; c < nc; ++c)
+            LRH_CK(launch_region_pass(p->P, c == 0 ? io0 : io, p->class_k[c], p->class_list[c], p->class_count[c],
+                                      p->stream, p->class_block[c]));
+        return LRH_OK;
+    }
+    LRH_CK(cudaEventRecord(p->ev_fork, p->stream));
+    for (size_t c = 1; c < nc; ++c) {
+        LRH_CK(cudaStreamWaitEvent(p->aux[c - 1], p->ev_fork, 0));
+        LRH_CK(launch_region_pass(p->P, io, p->class_k[c], p->class_list[c], p->class_count[c], p->aux[c - 1],
+                                  p->class_block[c]));
+        LRH_CK(cudaEventRecord(p->ev_join[c - 1], p->aux[c - 1]));
+    }
+    LRH_CK(launch_region_pass(p->P, io0, p->class_k[0], p->class_list[0], p->class_count[0], p->stream, p->class_block[0]));
+    for (size_t c = 1; c < nc; ++c) LRH_CK(cudaStreamWaitEvent(p->stream, p->ev_join[c - 1], 0));
+    return LRH_OK;
+}
+
+// Alg. 2, n iterations as n region passes: pass 0 reads the canonical nu, zeta; pass j >= 1
+// first applies iteration j-1's pending update (owners write it to the other buffer:
+// odd j -> B, even j -> A) and writes its states to X (even j) or Y (odd j); then the
+// pending update of the last pass is written into the canonical A, and t0 advances by n.
+int enqueue_nesterov(lrh_problem* p, int n) {
+    DevProblem& P = p->P;
+    float2* nuA = P.nu; float2* zA = P.zeta; float2* nuB = P.nu_b; float2* zB = P.zeta_b;
+    float2* rX = P.rho; float2* tX = P.tr; float2* rY = P.rho_b; float2* tY = P.tr_b;
+    PassIO io{};
+    for (int j = 0; j < n; ++j) {
+        io = PassIO{};
+        io.rel = j;
+        io.writer = 1;
+        io.pending = j > 0;
+        io.nu_in = (j % 2 == 1 || j == 0) ? nuA : nuB;
+        io.zeta_in = (j % 2 == 1 || j == 0) ? zA : zB;
+        if (j > 0) {
+            io.rho_in = (j % 2 == 1) ? rX : rY;
+            io.tr_in = (j % 2 == 1) ? tX : tY;
+            io.nu_out = (j % 2 == 1) ? nuB : nuA;
+            io.zeta_out = (j % 2 == 1) ? zB : zA;
+        }
+        io.rho_out = (j % 2 == 0) ? rX : rY;
+        io.tr_out = (j % 2 == 0) ? tX : tY;
+        int rc = launch_all_classes(p, io);
+        if (rc) return rc;
+    }
+    PassIO fin{};
+    fin.rel = n - 1;
+    fin.nu_in = (n == 1) ? nuA : ((n - 1) % 2 == 1 ? nuB : nuA);
+    fin.zeta_in = (n == 1) ? zA : ((n - 1) % 2 == 1 ? zB : zA);
+    fin.rho_in = ((n - 1) % 2 == 0) ? rX : rY;
+    fin.tr_in = ((n - 1) % 2 == 0) ? tX : tY;
+    fin.nu_out = nuA;
+    fin.zeta_out = zA;
+    LRH_CK(launch_finalize(P, fin, p->stream));
+    LRH_CK(launch_advance(P, n, p->stream));
+    return LRH_OK;
+}
+
+void drop_graphs(lrh_problem* p) {
+    if (p->graph_exec) { cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr; }
+    if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+    for (auto& g : p->nest_graphs) cudaGraphExecDestroy(g.second);
+    p->nest_graphs.clear();
+}
+
+int step_nesterov(lrh_problem* p, int n) {
+    if (n <= 0) return LRH_OK;
+    if (!p->opt.use_graph || n < 2) return enqueue_nesterov(p, n);
+    cudaGraphExec_t ge = nullptr;
+    for (auto& g : p->nest_graphs) if (g.first == n) ge = g.second;
+    if (!ge) {
+        LRH_CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_nesterov(p, n);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+        if (rc != LRH_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return fail(LRH_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(LRH_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        if (p->nest_graphs.size() >= 8) { cudaGraphExecDestroy(p->nest_graphs.front().second); p->nest_graphs.erase(p->nest_graphs.begin()); }
+        p->nest_graphs.emplace_back(n, ge);
+    }
+    LRH_CK(cudaGraphLaunch(ge, p->stream));
+    return LRH_OK;
+}
+
 int run_iteration(lrh_problem* p, int par) {
-    for (size_t c = 0; c < p->class_k.size(); ++c)
-        LRH_CK(launch_region_pass(p->P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+    int rc = launch_all_classes(p, plain_io(p));
+    if (rc) return rc;
     if (p->opt.variant == LRH_SUBGRADIENT) LRH_CK(launch_reduce(p->P, p->P.val, 1, p->stream));
     LRH_CK(launch_update(p->P, par, UPD_STEP, p->stream));
     return LRH_OK;
@@ -411,6 +527,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     p->h_elems = hoff;
     p->rho_elems = roff;
     p->all_elems = aoff;
+    for (auto& pi : pairs) pi.child_rho = rinfo[pi.child].rho_off;
     std::vector<double> h64;
     embed_terms(p, d->term_mats, h64);
 
@@ -445,11 +562,36 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
             LRH_CK(cudaMemcpy(dchunk, chunk.data(), sizeof(int32_t) * chunk.size(), cudaMemcpyHostToDevice));
     }
     P.chunk_pair = dchunk;
+    {
+        std::vector<int64_t> crho((size_t)std::max<int64_t>(moff / 4, 1));
+        for (size_t q = 0; q < pairs.size(); ++q) {
+            const int64_t n4 = ((int64_t)1 << (2 * pairs[q].kf)) / 4;
+            for (int64_t c = 0; c < n4; ++c) crho[(size_t)(pairs[q].off / 4 + c)] = rinfo[pairs[q].child].rho_off - pairs[q].off;
+        }
+        std::vector<PairInfo> cinfo, pinfo;
+        for (int32_t q : child_pairs) cinfo.push_back(pairs[q]);
+        for (int32_t q : parent_pairs) pinfo.push_back(pairs[q]);
+        int64_t* dcr; PairInfo *dci, *dpi;
+        if ((rc = p->dalloc(&dcr, (int64_t)crho.size())) || (rc = p->dalloc(&dci, (int64_t)cinfo.size())) ||
+            (rc = p->dalloc(&dpi, (int64_t)pinfo.size())))
+            return rc;
+        LRH_CK(cudaMemcpy(dcr, crho.data(), sizeof(int64_t) * crho.size(), cudaMemcpyHostToDevice));
+        if (!cinfo.empty()) LRH_CK(cudaMemcpy(dci, cinfo.data(), sizeof(PairInfo) * cinfo.size(), cudaMemcpyHostToDevice));
+        if (!pinfo.empty()) LRH_CK(cudaMemcpy(dpi, pinfo.data(), sizeof(PairInfo) * pinfo.size(), cudaMemcpyHostToDevice));
+        P.chunk_rho = dcr;
+        P.child_info = dci;
+        P.parent_info = dpi;
+    }
     float2* h32; double2* dh64;
     if ((rc = p->dalloc(&h32, NI * hoff)) || (rc = p->dalloc(&dh64, NI * hoff))) return rc;
     if ((rc = p->dalloc(&P.nu, NI * moff)) || (rc = p->dalloc(&P.zeta, NI * moff)) || (rc = p->dalloc(&P.nu_best, NI * moff)) ||
         (rc = p->dalloc(&P.tr, NI * moff)) || (rc = p->dalloc(&P.grad, NI * moff)) || (rc = p->dalloc(&P.rho, NI * roff)))
         return rc;
+    if (p->opt.variant == LRH_NESTEROV || true) {
+        if ((rc = p->dalloc(&P.nu_b, NI * moff)) || (rc = p->dalloc(&P.zeta_b, NI * moff)) ||
+            (rc = p->dalloc(&P.rho_b, NI * roff)) || (rc = p->dalloc(&P.tr_b, NI * moff)))
+            return rc;
+    }
     if ((rc = p->dalloc(&P.val, NI * R)) || (rc = p->dalloc(&P.val64, NI * R)) || (rc = p->dalloc(&P.q_sum, NI)) ||
         (rc = p->dalloc(&P.q_best, NI)) || (rc = p->dalloc(&P.best_flag, NI)) || (rc = p->dalloc(&P.st, 1)) ||
         (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)))
@@ -491,6 +633,29 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         p->class_count.push_back((int32_t)lst.size());
         p->class_list.push_back(dl);
     }
+    // most expensive class first (it stays on the problem's stream)
+    {
+        std::vector<size_t> order(p->class_k.size());
+        for (size_t c = 0; c < order.size(); ++c) order[c] = c;
+        std::sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+            const double ca = (double)p->class_count[a] * std::pow(8.0, p->class_k[a]);
+            const double cb = (double)p->class_count[b] * std::pow(8.0, p->class_k[b]);
+            return ca > cb;
+        });
+        std::vector<int> k2; std::vector<int32_t> c2; std::vector<int32_t*> l2;
+        for (size_t c : order) { k2.push_back(p->class_k[c]); c2.push_back(p->class_count[c]); l2.push_back(p->class_list[c]); }
+        p->class_k = k2; p->class_count = c2; p->class_list = l2;
+    }
+    p->class_block.assign(p->class_k.size(), 128);
+    LRH_CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+    for (size_t c = 1; c < p->class_k.size(); ++c) {
+        cudaStream_t a;
+        cudaEvent_t e;
+        LRH_CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+        p->aux.push_back(a);
+        LRH_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->ev_join.push_back(e);
+    }
     p->h_pinned_len = std::max<int64_t>(NI * R, 16);
     LRH_CK(cudaMallocHost(&p->h_pinned, sizeof(double) * p->h_pinned_len));
     if ((rc = push_state(p, true, 1.0, 0.0))) return rc;
@@ -526,7 +691,9 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
         info->class_sites[c] = p->class_k[c];
         info->class_regions[c] = p->class_count[c];
         info->sweeps[c] = sw[p->class_k[c]];
+        info->class_block[c] = p->class_block[c];
     }
+    info->concurrent_classes = p->concurrent ? 1 : 0;
     return LRH_OK;
 }
 
@@ -552,6 +719,12 @@ int lrh_restart(lrh_problem* p) {
     DeviceGuard dg(p->device);
     int rc = push_state(p, true, 1.0, 0.0);
     if (rc) return rc;
+    if (p->opt.variant == LRH_SUBGRADIENT) {   // a new Alg. 1 run: q_best = -inf
+        std::vector<double> ninf(p->n_inst, -std::numeric_limits<double>::infinity());
+        LRH_CK(cudaMemcpyAsync(p->P.q_best, ninf.data(), sizeof(double) * p->n_inst, cudaMemcpyHostToDevice, p->stream));
+        LRH_CK(cudaMemsetAsync(p->P.best_flag, 0, sizeof(int32_t) * p->n_inst, p->stream));
+        LRH_CK(cudaStreamSynchronize(p->stream));
+    }
     LRH_CK(cudaMemcpyAsync(p->P.zeta, p->P.nu, sizeof(float2) * p->n_inst * p->msg_elems, cudaMemcpyDeviceToDevice, p->stream));
     return LRH_OK;
 }
@@ -560,6 +733,11 @@ int lrh_step(lrh_problem* p, int32_t n_iters) {
     if (!p || n_iters < 0) return fail(LRH_EINVAL, "bad arguments to lrh_step");
     DeviceGuard dg(p->device);
     int rc;
+    if (p->opt.variant == LRH_NESTEROV) {
+        if ((rc = step_nesterov(p, n_iters))) return rc;
+        p->iteration += n_iters;
+        return LRH_OK;
+    }
     while (n_iters > 0) {
         if (p->opt.use_graph && (p->iteration & 1) == 0 && n_iters >= kGraphChunk) {
             if (!p->graph_exec && (rc = build_graph(p))) return rc;
@@ -579,8 +757,8 @@ int lrh_evaluate(lrh_problem* p) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
     DeviceGuard dg(p->device);
     const int par = (int)(p->iteration & 1);
-    for (size_t c = 0; c < p->class_k.size(); ++c)
-        LRH_CK(launch_region_pass(p->P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+    int rc = launch_all_classes(p, plain_io(p));
+    if (rc) return rc;
     LRH_CK(launch_update(p->P, par, UPD_GRAD_ONLY, p->stream));
     return LRH_OK;
 }
@@ -590,7 +768,8 @@ int lrh_launch_region_pass(lrh_problem* p, int32_t k_sites) {
     DeviceGuard dg(p->device);
     for (size_t c = 0; c < p->class_k.size(); ++c)
         if (p->class_k[c] == k_sites) {
-            LRH_CK(launch_region_pass(p->P, k_sites, p->class_list[c], p->class_count[c], (int)(p->iteration & 1), p->stream));
+            LRH_CK(launch_region_pass(p->P, plain_io(p), k_sites, p->class_list[c], p->class_count[c], p->stream,
+                                      p->class_block[c]));
             return LRH_OK;
         }
     return fail(LRH_EINVAL, "no region class with " + std::to_string(k_sites) + " sites");
@@ -705,10 +884,7 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
         if ((rc = p->dalloc(&dti, (int64_t)ti.size()))) return rc;
         LRH_CK(cudaMemcpy(dti, ti.data(), sizeof(TermInfo) * ti.size(), cudaMemcpyHostToDevice));
         P.terms = dti;
-        if (p->graph_exec) {   // captured graphs hold a copy of P without the adjoint buffers: rebuild
-            cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr;
-            cudaGraphDestroy(p->graph); p->graph = nullptr;
-        }
+        drop_graphs(p);   // captured graphs hold a copy of P without the adjoint buffers
     }
     LRH_CK(cudaMemcpyAsync(P.qbar, q_bar, sizeof(double) * NI, cudaMemcpyHostToDevice, p->stream));
     const size_t mbytes = sizeof(float2) * NI * p->msg_elems;
@@ -716,15 +892,207 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
         if (g_bar) LRH_CK(cudaMemcpyAsync(P.gbar, g_bar, mbytes, g_bar_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
         else LRH_CK(cudaMemsetAsync(P.gbar, 0, mbytes, p->stream));
     }
-    const int par = (int)(p->iteration & 1);
     for (size_t c = 0; c < p->class_k.size(); ++c)
-        LRH_CK(launch_vjp_region(P, p->class_k[c], p->class_list[c], p->class_count[c], par, p->stream));
+        LRH_CK(launch_vjp_region(P, p->class_k[c], p->class_list[c], p->class_count[c], p->stream));
     LRH_CK(launch_vjp_outputs(P, p->vjp_nubar, p->vjp_termbar, p->stream));
     const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (nu_bar && mbytes) LRH_CK(cudaMemcpyAsync(nu_bar, p->vjp_nubar, mbytes, kind, p->stream));
     if (term_bar && p->term_total)
         LRH_CK(cudaMemcpyAsync(term_bar, p->vjp_termbar, sizeof(float2) * NI * p->term_total, kind, p->stream));
     return read_err(p);
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic;        // "LRHSTAT1"
+    int32_t n_inst;
+    int32_t variant;
+    int64_t msg_elems;
+    int64_t iteration;
+    lrh::IterState st;
+};
+constexpr uint64_t kStateMagic = 0x3154415453485231ull;
+}  // namespace
+
+int64_t lrh_state_bytes(const lrh_problem* p) {
+    if (!p) return 0;
+    return (int64_t)sizeof(StateHeader) + 3 * (int64_t)sizeof(float2) * p->n_inst * p->msg_elems +
+           (int64_t)sizeof(double) * p->n_inst;
+}
+
+int lrh_get_state(lrh_problem* p, void* buf, int64_t bytes) {
+    if (!p || !buf) return fail(LRH_EINVAL, "NULL argument");
+    if (bytes != lrh_state_bytes(p)) return fail(LRH_EINVAL, "bytes must equal lrh_state_bytes()");
+    DeviceGuard dg(p->device);
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.n_inst = p->n_inst;
+    h.variant = p->opt.variant;
+    h.msg_elems = p->msg_elems;
+    h.iteration = p->iteration;
+    char* out = static_cast<char*>(buf);
+    const size_t m = sizeof(float2) * p->n_inst * p->msg_elems;
+    LRH_CK(cudaMemcpyAsync(&h.st, p->P.st, sizeof(IterState), cudaMemcpyDeviceToHost, p->stream));
+    char* q = out + sizeof(StateHeader);
+    if (m) {
+        LRH_CK(cudaMemcpyAsync(q, p->P.nu, m, cudaMemcpyDeviceToHost, p->stream));
+        LRH_CK(cudaMemcpyAsync(q + m, p->P.zeta, m, cudaMemcpyDeviceToHost, p->stream));
+        LRH_CK(cudaMemcpyAsync(q + 2 * m, p->P.nu_best, m, cudaMemcpyDeviceToHost, p->stream));
+    }
+    LRH_CK(cudaMemcpyAsync(q + 3 * m, p->P.q_best, sizeof(double) * p->n_inst, cudaMemcpyDeviceToHost, p->stream));
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    std::memcpy(out, &h, sizeof(h));
+    return LRH_OK;
+}
+
+int lrh_set_state(lrh_problem* p, const void* buf, int64_t bytes) {
+    if (!p || !buf) return fail(LRH_EINVAL, "NULL argument");
+    if (bytes != lrh_state_bytes(p)) return fail(LRH_EINVAL, "bytes must equal lrh_state_bytes()");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic || h.n_inst != p->n_inst || h.msg_elems != p->msg_elems || h.variant != p->opt.variant)
+        return fail(LRH_EINVAL, "state does not belong to a problem of this shape and variant");
+    DeviceGuard dg(p->device);
+    const char* q = static_cast<const char*>(buf) + sizeof(StateHeader);
+    const size_t m = sizeof(float2) * p->n_inst * p->msg_elems;
+    LRH_CK(cudaMemcpyAsync(p->P.st, &h.st, sizeof(IterState), cudaMemcpyHostToDevice, p->stream));
+    if (m) {
+        LRH_CK(cudaMemcpyAsync(p->P.nu, q, m, cudaMemcpyHostToDevice, p->stream));
+        LRH_CK(cudaMemcpyAsync(p->P.zeta, q + m, m, cudaMemcpyHostToDevice, p->stream));
+        LRH_CK(cudaMemcpyAsync(p->P.nu_best, q + 2 * m, m, cudaMemcpyHostToDevice, p->stream));
+    }
+    LRH_CK(cudaMemcpyAsync(p->P.q_best, q + 3 * m, sizeof(double) * p->n_inst, cudaMemcpyHostToDevice, p->stream));
+    LRH_CK(cudaStreamSynchronize(p->stream));
+    p->iteration = h.iteration;
+    return LRH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Cache format: one JSON object per line, {"key": "...", "block": B} or {"key": "...", "concurrent": 0|1}.
+std::vector<std::pair<std::string, int>> read_cache(const char* path) {
+    std::vector<std::pair<std::string, int>> out;
+    if (!path) return out;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return out;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        const size_t k0 = l.find("\"key\": \"");
+        if (k0 == std::string::npos) continue;
+        const size_t ks = k0 + 8, ke = l.find('"', ks);      // 8 = strlen("\"key\": \"")
+        if (ke == std::string::npos) continue;
+        const size_t c = l.find(':', ke + 1);               // the value after "block" / "concurrent"
+        if (c == std::string::npos) continue;
+        out.emplace_back(l.substr(ks, ke - ks), std::atoi(l.c_str() + c + 1));
+    }
+    std::fclose(f);
+    return out;
+}
+
+int cache_lookup(const std::vector<std::pair<std::string, int>>& c, const std::string& key, int* val) {
+    for (auto it = c.rbegin(); it != c.rend(); ++it)
+        if (it->first == key) { *val = it->second; return 1; }
+    return 0;
+}
+
+// Time `reps` calls of fn on the problem's stream with CUDA events (milliseconds per call).
+template <typename F>
+int time_ms(lrh_problem* p, int reps, F fn, float* ms) {
+    cudaEvent_t a, b;
+    LRH_CK(cudaEventCreate(&a));
+    LRH_CK(cudaEventCreate(&b));
+    int rc = fn();
+    if (!rc) {
+        LRH_CK(cudaEventRecord(a, p->stream));
+        for (int i = 0; i < reps && !rc; ++i) rc = fn();
+        LRH_CK(cudaEventRecord(b, p->stream));
+        LRH_CK(cudaEventSynchronize(b));
+        float t = 0;
+        LRH_CK(cudaEventElapsedTime(&t, a, b));
+        *ms = t / reps;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    int sms = 0;
+    LRH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    const bool force = (flags & 1) != 0;
+    auto cache = force ? std::vector<std::pair<std::string, int>>() : read_cache(cache_path);
+    std::vector<std::string> new_lines;
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
+        const int k = p->class_k[c];
+        if (k > 5) continue;   // CTA classes: one region per CTA, nothing to choose
+        const std::string key = "region_pass k=" + std::to_string(k) + " units=" +
+                                std::to_string((int64_t)p->class_count[c] * p->n_inst) + " sms=" + std::to_string(sms);
+        int blk = 0;
+        if (!cache_lookup(cache, key, &blk)) {
+            float best = 1e30f;
+            for (int cand : {64, 128, 256, -64, -128, -256}) {
+                if (cand > 0 && cand < (1 << k)) continue;
+                if (cand < 0 && k != 2) continue;   // thread-per-region layout: 4 x 4 regions
+                float ms = 0;
+                int rc = time_ms(p, 3, [&]() -> int {
+                    LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, cand));
+                    return LRH_OK; }, &ms);
+                if (rc) return rc;
+                if (ms < best) { best = ms; blk = cand; }
+            }
+            new_lines.push_back("{\"key\": \"" + key + "\", \"block\": " + std::to_string(blk) + "}");
+        }
+        p->class_block[c] = blk;
+    }
+    if (p->class_k.size() > 1) {
+        std::string key = "concurrent classes";
+        for (size_t c = 0; c < p->class_k.size(); ++c)
+            key += " k" + std::to_string(p->class_k[c]) + "=" + std::to_string((int64_t)p->class_count[c] * p->n_inst);
+        key += " sms=" + std::to_string(sms);
+        int conc = 1;
+        if (!cache_lookup(cache, key, &conc)) {
+            float ms_seq = 0, ms_con = 0;
+            p->concurrent = false;
+            int rc = time_ms(p, 3, [&]() { return launch_all_classes(p, plain_io(p)); }, &ms_seq);
+            if (rc) return rc;
+            p->concurrent = true;
+            rc = time_ms(p, 3, [&]() { return launch_all_classes(p, plain_io(p)); }, &ms_con);
+            if (rc) return rc;
+            conc = ms_con <= ms_seq ? 1 : 0;
+            new_lines.push_back("{\"key\": \"" + key + "\", \"concurrent\": " + std::to_string(conc) + "}");
+        }
+        p->concurrent = conc != 0;
+    }
+    if (cache_path && !new_lines.empty()) {
+        FILE* f = std::fopen(cache_path, "a");
+        if (!f) return fail(LRH_EINVAL, std::string("cannot write the autotune cache ") + cache_path);
+        for (auto& l : new_lines) std::fprintf(f, "%s\n", l.c_str());
+        std::fclose(f);
+    }
+    drop_graphs(p);   // captured launch shapes are stale
+    return read_err(p);
+}
+
+int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    const bool ok = block == 64 || block == 128 || block == 256 || (k_sites == 2 && (block == -64 || block == -128 || block == -256));
+    if (!ok || (block > 0 && block < (1 << k_sites))) return fail(LRH_EINVAL, "unsupported launch shape for this region size");
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        if (p->class_k[c] == k_sites) {
+            p->class_block[c] = block;
+            drop_graphs(p);
+            return LRH_OK;
+        }
+    return fail(LRH_EINVAL, "no region class with " + std::to_string(k_sites) + " sites");
 }
 
 int lrh_synchronize(lrh_problem* p) {

@@ -16,6 +16,7 @@
 // in the same shared-memory buffer, with register tiles; then made exactly Hermitian, traced
 // onto the children and written out.  The FP64 certification kernel reuses the Jacobi part
 // (no V) to return lambda_min.
+#include "lrh_device.cuh"
 #include "lrh_internal.cuh"
 
 #include <cmath>
@@ -290,7 +291,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
             }
         }
         for (int q = R.child_begin; q < R.child_end; ++q) {
-            const PairInfo pi = P.pair[P.child_pairs[q]];
+            const PairInfo pi = P.child_info[q];
             if (((i ^ j) & ~pi.mask) != 0) continue;
             const int Df = 1 << pi.kf;
             const int64_t o = mbase + pi.off + (int64_t)pext7(i, pi.mask) * Df + pext7(j, pi.mask);
@@ -299,7 +300,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
             re -= T(m.x); im -= T(m.y);
         }
         for (int q = R.parent_begin; q < R.parent_end; ++q) {
-            const PairInfo pi = P.pair[P.parent_pairs[q]];
+            const PairInfo pi = P.parent_info[q];
             const int64_t o = mbase + pi.off + e;
             float2 m = nu[o];
             if (zeta) { const float2 z = zeta[o]; m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y; }
@@ -308,6 +309,47 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
         if (i == j) im = T(0);
         typename V2<T>::t v; v.x = re; v.y = im;
         A.a[tri(i, j, D)] = v;
+    }
+}
+
+// FP32 pass version: message entries from pass_entry (pending Alg. 2 update applied); the
+// region owns its parent messages and also stores the conjugate (lower-triangle) entries.
+template <int D>
+__device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Packed<float> A, const PassIO& io,
+                                   const dev::Thetas& T) {
+    constexpr int NT = CtaCfg<D>::NT;
+    const int64_t mbase = (int64_t)inst * P.msg_elems;
+    const int64_t rbase = (int64_t)inst * P.rho_elems;
+    const bool owner_writes = io.zeta_in && io.pending;
+    for (int e = threadIdx.x; e < D * D; e += NT) {
+        const int i = e / D, j = e % D;
+        if (i > j) continue;
+        float re = 0.f, im = 0.f;
+        if (R.h_off >= 0) {
+            const float2 v = P.h32[(int64_t)inst * P.h_elems + R.h_off + e];
+            re = v.x; im = v.y;
+        }
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            if (((i ^ j) & ~pi.mask) != 0) continue;
+            const int Df = 1 << pi.kf;
+            const int64_t x = (int64_t)pext7(i, pi.mask) * Df + pext7(j, pi.mask);
+            const float2 m = dev::pass_entry(io, T, mbase + pi.off + x, rbase + pi.child_rho + x, false);
+            re -= m.x; im -= m.y;
+        }
+        for (int q = R.parent_begin; q < R.parent_end; ++q) {
+            const PairInfo pi = P.parent_info[q];
+            float2 n, z;
+            const float2 m = dev::pass_entry(io, T, mbase + pi.off + e, rbase + R.rho_off + e, true, &n, &z);
+            if (owner_writes && i < j) {
+                const int64_t et = mbase + pi.off + (int64_t)j * D + i;
+                io.nu_out[et] = make_float2(n.x, -n.y);
+                io.zeta_out[et] = make_float2(z.x, -z.y);
+            }
+            re += m.x; im += m.y;
+        }
+        if (i == j) im = 0.f;
+        A.a[tri(i, j, D)] = make_float2(re, im);
     }
 }
 
@@ -322,8 +364,9 @@ __device__ void build_table(unsigned short* tab) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const DevProblem P, const int32_t* __restrict__ cls,
-                                                                        const int32_t count, const int par, const int k) {
+__global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const DevProblem P, const PassIO io,
+                                                                        const int32_t* __restrict__ cls,
+                                                                        const int32_t count, const int k) {
     using S = CtaSmem<D, float>;
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int W = D / 4;
@@ -342,11 +385,12 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     const int r = cls[blockIdx.x % count];
     const RegionInfo R = P.reg[r];
     const bool nest = P.st->variant == 1;
-    const float th = nest ? (float)P.st->theta[par] : 0.0f;
+    const dev::Thetas Th = dev::pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && t == 0) dev::advance_theta(P, io);
     build_table<D, float>(tab);
     if (t < D) idx0[t] = t;
     Packed<float> A{buf, D};
-    assemble_packed<D, float>(P, R, inst, A, P.nu, nest ? P.zeta : nullptr, th, false);
+    assemble_packed_io<D>(P, R, inst, A, io, Th);
     __syncthreads();
     const int row = t / 4, chunk = t % 4;
     float vr[W], vi[W];
@@ -417,13 +461,13 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     }
     __syncthreads();
     if (R.rho_off >= 0) {
-        float4* dst = reinterpret_cast<float4*>(P.rho + (int64_t)inst * P.rho_elems + R.rho_off);
+        float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off);
         const float4* srcv = reinterpret_cast<const float4*>(buf);
         for (int e = t; e < D * D / 2; e += NT) dst[e] = srcv[e];
     }
-    float2* trb = P.tr + (int64_t)inst * P.msg_elems;
+    float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
     for (int q = R.child_begin; q < R.child_end; ++q) {
-        const PairInfo pi = P.pair[P.child_pairs[q]];
+        const PairInfo pi = P.child_info[q];
         const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
         for (int o = t; o < Df * Df; o += NT) {
             const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
@@ -476,9 +520,9 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
 }
 
 template <int D>
-cudaError_t pass_cta(const DevProblem& P, const int32_t* cls, int32_t count, int par, int k, cudaStream_t s) {
+cudaError_t pass_cta(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k, cudaStream_t s) {
     const int64_t blocks = (int64_t)P.n_inst * count;
-    region_pass_cta_kernel<D><<<(unsigned)blocks, CtaCfg<D>::NT, CtaSmem<D, float>::bytes, s>>>(P, cls, count, par, k);
+    region_pass_cta_kernel<D><<<(unsigned)blocks, CtaCfg<D>::NT, CtaSmem<D, float>::bytes, s>>>(P, io, cls, count, k);
     return cudaGetLastError();
 }
 
@@ -503,10 +547,11 @@ cudaError_t prepare_cta_kernels() {
                                 (int)CtaSmem<128, double>::bytes);
 }
 
-cudaError_t launch_region_pass_cta(const DevProblem& P, int k, const int32_t* cls, int32_t count, int par, cudaStream_t s) {
+cudaError_t launch_region_pass_cta(const DevProblem& P, const PassIO& io, int k, const int32_t* cls, int32_t count,
+                                   cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    if (k == 6) return pass_cta<64>(P, cls, count, par, k, s);
-    if (k == 7) return pass_cta<128>(P, cls, count, par, k, s);
+    if (k == 6) return pass_cta<64>(P, io, cls, count, k, s);
+    if (k == 7) return pass_cta<128>(P, io, cls, count, k, s);
     return cudaErrorInvalidValue;
 }
 

@@ -220,7 +220,7 @@ __device__ __forceinline__ void assemble_row(const DevProblem& P, const RegionIn
     const int64_t mbase = (int64_t)inst * P.msg_elems;
     const float om = 1.0f - th;
     for (int q = R.child_begin; q < R.child_end; ++q) {
-        const PairInfo pi = P.pair[P.child_pairs[q]];
+        const PairInfo pi = P.child_info[q];
         const int M = pi.mask;
         const int Df = 1 << pi.kf;
         const int a = pext_bits(s, M);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void assemble_row(const DevProblem& P, const RegionIn
         }
     }
     for (int q = R.parent_begin; q < R.parent_end; ++q) {
-        const PairInfo pi = P.pair[P.parent_pairs[q]];
+        const PairInfo pi = P.parent_info[q];
         const float4* nb = reinterpret_cast<const float4*>(nu + mbase + pi.off + (int64_t)s * D);
         const float4* zb = zeta ? reinterpret_cast<const float4*>(zeta + mbase + pi.off + (int64_t)s * D) : nullptr;
 #pragma unroll
@@ -251,6 +251,113 @@ __device__ __forceinline__ void assemble_row(const DevProblem& P, const RegionIn
                 m.z = om * m.z + th * z.z; m.w = om * m.w + th * z.w;
             }
             ar[2 * c] += T(m.x); ai[2 * c] += T(m.y); ar[2 * c + 1] += T(m.z); ai[2 * c + 1] += T(m.w);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fused Alg. 2 passes
+struct Thetas {
+    float cur;    // theta_t of this pass (extrapolation eta = (1 - theta_t) nu + theta_t zeta)
+    float prev;   // theta_{t-1} of the pending update
+    float kz;     // 1 / (theta_{t-1} L_hat)
+};
+
+__device__ __forceinline__ Thetas pass_thetas(const DevProblem& P, const PassIO& io) {
+    Thetas T{0.f, 0.f, 0.f};
+    if (!io.zeta_in) return T;
+    const long long t = P.st->t0 + io.rel;
+    T.cur = (float)P.st->th3[t % 3];
+    if (io.pending) {
+        const double tp = P.st->th3[(t + 2) % 3];
+        T.prev = (float)tp;
+        T.kz = (float)(P.st->inv_lhat / tp);
+    }
+    return T;
+}
+
+// The launch marked `writer` of a pass stores theta_{t+1} = (sqrt(theta^4 + 4 theta^2) - theta^2)/2
+// (Alg. 2) in slot (t + 1) mod 3; the pass itself reads slots t and t - 1 only.
+__device__ __forceinline__ void advance_theta(const DevProblem& P, const PassIO& io) {
+    if (!io.zeta_in) return;
+    const long long t = P.st->t0 + io.rel;
+    const double th = P.st->th3[t % 3];
+    P.st->th3[(t + 1) % 3] = (sqrt(th * th * th * th + 4.0 * th * th) - th * th) * 0.5;
+}
+
+// Alg. 2 update of one message entry: zeta += kz g, nu = (1 - theta) nu + theta zeta.
+__device__ __forceinline__ void nesterov_update(float2& n, float2& z, float gx, float gy, float th, float kz) {
+    z.x = fmaf(kz, gx, z.x);
+    z.y = fmaf(kz, gy, z.y);
+    const float om = 1.0f - th;
+    n.x = fmaf(th, z.x, om * n.x);
+    n.y = fmaf(th, z.y, om * n.y);
+}
+
+__device__ __forceinline__ float2 extrapolate(float2 n, float2 z, float th) {
+    const float om = 1.0f - th;
+    return make_float2(fmaf(th, z.x, om * n.x), fmaf(th, z.y, om * n.y));
+}
+
+// Message entry seen by a pass: nu (Alg. 1), or eta after applying the pending update
+// (Alg. 2).  `mi` indexes the message arrays, `ri` the child's state of the previous pass.
+// The owner (the pair's child region) stores the updated nu, zeta; n_out / z_out return them.
+__device__ __forceinline__ float2 pass_entry(const PassIO& io, const Thetas& T, int64_t mi, int64_t ri, bool owner,
+                                             float2* n_out = nullptr, float2* z_out = nullptr) {
+    float2 n = io.nu_in[mi];
+    if (!io.zeta_in) return n;
+    float2 z = io.zeta_in[mi];
+    if (io.pending) {
+        const float2 r = io.rho_in[ri], t = io.tr_in[mi];
+        nesterov_update(n, z, r.x - t.x, r.y - t.y, T.prev, T.kz);
+        if (owner) { io.nu_out[mi] = n; io.zeta_out[mi] = z; }
+    }
+    if (n_out) *n_out = n;
+    if (z_out) *z_out = z;
+    return extrapolate(n, z, T.cur);
+}
+
+// Row s of theta_e for an FP32 pass: h_e - sum_children 1 (x) m + sum_parents m with the
+// message entries of pass_entry.
+template <int D>
+__device__ __forceinline__ void assemble_row_io(const DevProblem& P, const RegionInfo& R, int inst, int s,
+                                                const PassIO& io, const Thetas& T, float (&ar)[D], float (&ai)[D]) {
+    if (R.h_off >= 0) {
+        const float4* hrow = reinterpret_cast<const float4*>(P.h32 + (int64_t)inst * P.h_elems + R.h_off + (int64_t)s * D);
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) {
+            const float4 v = hrow[c];
+            ar[2 * c] = v.x; ai[2 * c] = v.y; ar[2 * c + 1] = v.z; ai[2 * c + 1] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
+    }
+    const int64_t mbase = (int64_t)inst * P.msg_elems;
+    const int64_t rbase = (int64_t)inst * P.rho_elems;
+    for (int q = R.child_begin; q < R.child_end; ++q) {
+        const PairInfo pi = P.child_info[q];
+        const int M = pi.mask;
+        const int Df = 1 << pi.kf;
+        const int a = pext_bits(s, M);
+        const int rest = s & ~M;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            if ((c & ~M) == rest) {
+                const int x = a * Df + pext_bits(c, M);
+                const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + pi.child_rho + x, false);
+                ar[c] -= m.x;
+                ai[c] -= m.y;
+            }
+        }
+    }
+    for (int q = R.parent_begin; q < R.parent_end; ++q) {
+        const PairInfo pi = P.parent_info[q];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const int64_t x = (int64_t)s * D + c;
+            const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+            ar[c] += m.x;
+            ai[c] += m.y;
         }
     }
 }

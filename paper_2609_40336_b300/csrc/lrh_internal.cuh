@@ -33,13 +33,16 @@ struct PairInfo {
     int32_t child;
     int32_t mask;          // bits of the parent's basis index that carry the child's sites
     int32_t kf;            // child sites
+    int64_t child_rho;     // offset of the child's state rho_f in one instance's state arena
 };
 
 // Scalars of the iteration, double-buffered by iteration parity so that a captured
 // graph of iterations needs no host-side argument changes.
 struct IterState {
-    double theta[2];       // Alg. 2 theta_k
-    double t[2];           // iterations since the last restart (step-size rule)
+    double theta[2];       // Alg. 1 path: parity slots (unused by Alg. 2)
+    double t[2];           // iterations since the last restart (Alg. 1 step-size rule)
+    double th3[3];         // Alg. 2: theta_t in slot t mod 3 (a pass reads t-1 and t, writes t+1)
+    long long t0;          // Alg. 2: iterations since the last restart, before the current lrh_step
     double beta;
     double inv_lhat;
     double alpha;
@@ -47,6 +50,25 @@ struct IterState {
     int32_t variant;
     int32_t step_rule;
     int32_t max_sweeps;
+    int32_t pad;
+};
+
+// Inputs and outputs of one region pass.  A "pending" pass first applies the previous
+// iteration's Alg. 2 update to every message it gathers (g = rho_in_f - tr_in, zeta += g /
+// (theta_{t-1} L_hat), nu = (1 - theta_{t-1}) nu + theta_{t-1} zeta); the region that is the
+// child of a pair owns that message and writes the updated nu, zeta to nu_out / zeta_out.
+struct PassIO {
+    const float2* nu_in;
+    const float2* zeta_in;   // nullptr: Alg. 1 (eta = nu)
+    const float2* rho_in;
+    const float2* tr_in;
+    float2* nu_out;
+    float2* zeta_out;
+    float2* rho_out;
+    float2* tr_out;
+    int32_t rel;             // iteration t = st->t0 + rel
+    int32_t pending;
+    int32_t writer;          // this launch writes th3[(t + 1) mod 3]
     int32_t pad;
 };
 
@@ -66,6 +88,9 @@ struct DevProblem {
     const int32_t* child_pairs;
     const int32_t* parent_pairs;
     const int32_t* chunk_pair;   // [msg_elems / 4] pair owning complex entries 4c .. 4c+3
+    const int64_t* chunk_rho;    // [msg_elems / 4] child-state offset minus message offset of that pair
+    const PairInfo* child_info;  // PairInfo in child CSR order (child_pairs[q] resolved)
+    const PairInfo* parent_info; // PairInfo in parent CSR order
     const float2* h32;     // [n_inst][h_elems]
     const double2* h64;    // [n_inst][h_elems]
     float2* nu;            // [n_inst][msg_elems]
@@ -74,6 +99,10 @@ struct DevProblem {
     float2* tr;            // Tr_{e\f} rho_e of the last pass, message layout
     float2* rho;           // [n_inst][rho_elems] states of regions that have parents
     float2* grad;          // gradient of the last lrh_evaluate
+    float2* nu_b;          // second buffers of the fused Alg. 2 iteration (ping-pong)
+    float2* zeta_b;
+    float2* rho_b;
+    float2* tr_b;
     double* val;           // [n_inst][n_regions] per-region FP32 values of the last pass
     double* val64;         // [n_inst][n_regions] per-region FP64 lambda_min of the last certify
     double* q_sum;         // [n_inst] scratch sums
@@ -100,14 +129,18 @@ int set_last_error(int code, const std::string& msg);
 // problem creation, outside any stream capture.
 cudaError_t prepare_kernels();
 cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128)
-cudaError_t launch_region_pass_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
-                                   int par, cudaStream_t s);
+cudaError_t launch_region_pass_cta(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
+                                   int32_t class_count, cudaStream_t s);
 cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
                                const float2* msg, cudaStream_t s);
 
 // Launchers (lrh_kernels.cu).  All enqueue on `s` and return the launch status.
-cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* class_regions,
-                               int32_t class_count, int par, cudaStream_t s);
+cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
+                               int32_t class_count, cudaStream_t s, int block = 128);
+// Alg. 2: apply the pending update of iteration t0 + rel into the canonical nu, zeta.
+cudaError_t launch_finalize(const DevProblem& P, const PassIO& io, cudaStream_t s);
+// Alg. 2: t0 += n.
+cudaError_t launch_advance(const DevProblem& P, int n, cudaStream_t s);
 cudaError_t launch_certify(const DevProblem& P, int k, const int32_t* class_regions,
                            int32_t class_count, const float2* msg, cudaStream_t s);
 cudaError_t launch_update(const DevProblem& P, int par, int mode, cudaStream_t s);
@@ -119,7 +152,7 @@ cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t 
 
 // Adjoint (lrh_vjp.cu): theta_bar per region for the classes, then nu_bar and term cotangents.
 cudaError_t prepare_vjp_kernels();
-cudaError_t launch_vjp_region(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count, int par,
+cudaError_t launch_vjp_region(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
                               cudaStream_t s);
 cudaError_t launch_vjp_outputs(const DevProblem& P, float2* nu_bar, float2* term_bar, cudaStream_t s);
 

@@ -34,22 +34,23 @@ namespace {
 constexpr int kBlock = 128;
 using namespace dev;
 
-template <int D>
+template <int D, int BLOCK>
 struct PassSmem {
-    static constexpr int kGroups = kBlock / D;
+    static constexpr int kGroups = BLOCK / D;
     static constexpr size_t per_group = (D / 2) * sizeof(Rot<float>) + D * sizeof(float) + 2 * D * D * sizeof(float2);
     static constexpr size_t bytes = kGroups * per_group + 16;
 };
 
-// FP32 region pass for 4 <= D <= 32.
-template <int D>
-__global__ void __launch_bounds__(kBlock) region_pass_kernel(const DevProblem P, const int32_t* __restrict__ cls,
-                                                             const int32_t count, const int par, const int k) {
+// FP32 region pass for 4 <= D <= 32; BLOCK threads = BLOCK / D regions per CTA (autotuned).
+template <int D, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, const PassIO io,
+                                                            const int32_t* __restrict__ cls, const int32_t count,
+                                                            const int k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int G = kBlock / D;
+    constexpr int G = BLOCK / D;
     const int g = threadIdx.x / D;
     const int s = threadIdx.x % D;
-    unsigned char* base = smem_raw + g * PassSmem<D>::per_group;
+    unsigned char* base = smem_raw + g * PassSmem<D, BLOCK>::per_group;
     Rot<float>* prm = reinterpret_cast<Rot<float>*>(base);
     float2* Wb = reinterpret_cast<float2*>(base + (D / 2) * sizeof(Rot<float>));
     float2* Rb = Wb + D * D;
@@ -62,16 +63,17 @@ __global__ void __launch_bounds__(kBlock) region_pass_kernel(const DevProblem P,
     const int inst = valid ? (int)(unit / count) : 0;
     const int r = valid ? cls[unit % count] : 0;
     const bool nest = P.st->variant == 1;
-    const float th = nest ? (float)P.st->theta[par] : 0.0f;
     const int max_sweeps = P.st->max_sweeps;
+    const Thetas T = pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
 
     float ar[D], ai[D], vr[D], vi[D];
     RegionInfo R;
     if (valid) {
         R = P.reg[r];
-        assemble_row<D, float>(P, R, inst, s, P.nu, nest ? P.zeta : nullptr, th, false, ar, ai);
+        assemble_row_io<D>(P, R, inst, s, io, T, ar, ai);
     } else {
-        R = RegionInfo{-1, -1, 0, 0, 0, 0};
+        R = RegionInfo{-1, -1, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
     }
@@ -145,14 +147,14 @@ __global__ void __launch_bounds__(kBlock) region_pass_kernel(const DevProblem P,
     __syncwarp();
     if (valid) {
         if (R.rho_off >= 0) {
-            float4* dst = reinterpret_cast<float4*>(P.rho + (int64_t)inst * P.rho_elems + R.rho_off + (int64_t)s * D);
+            float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off + (int64_t)s * D);
             const float4* srcr = reinterpret_cast<const float4*>(Rb + s * D);
 #pragma unroll
             for (int c = 0; c < D / 2; ++c) dst[c] = srcr[c];
         }
-        float2* trb = P.tr + (int64_t)inst * P.msg_elems;
+        float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
         for (int q = R.child_begin; q < R.child_end; ++q) {
-            const PairInfo pi = P.pair[P.child_pairs[q]];
+            const PairInfo pi = P.child_info[q];
             const int M = pi.mask;
             const int Mc = (D - 1) & ~M;
             const int kf = pi.kf;
@@ -187,14 +189,15 @@ __global__ void __launch_bounds__(kBlock) region_pass_kernel(const DevProblem P,
 // K^2 = r^2 I with r = sqrt(hh^2 + |b|^2): lambda = m -+ r,
 // Gibbs state (1/2)(I - tanh(beta r) K / r), F_beta = m - r - log(1 + e^{-2 beta r}) / beta,
 // ground projector (1/2)(I - K / r), or I/2 when 2r is within the degeneracy tolerance.
-__global__ void __launch_bounds__(kBlock) region_pass_d2_kernel(const DevProblem P, const int32_t* __restrict__ cls,
-                                                               const int32_t count, const int par) {
+__global__ void __launch_bounds__(256) region_pass_d2_kernel(const DevProblem P, const PassIO io,
+                                                            const int32_t* __restrict__ cls, const int32_t count) {
+    const Thetas T = pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
     const int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (unit >= (int64_t)P.n_inst * count) return;
     const int inst = (int)(unit / count);
     const int r = cls[unit % count];
     const bool nest = P.st->variant == 1;
-    const float th = nest ? (float)P.st->theta[par] : 0.0f;
     const RegionInfo R = P.reg[r];
     float a = 0.f, d = 0.f, br = 0.f, bi = 0.f;
     if (R.h_off >= 0) {
@@ -202,18 +205,13 @@ __global__ void __launch_bounds__(kBlock) region_pass_d2_kernel(const DevProblem
         a = h[0].x; br = h[1].x; bi = h[1].y; d = h[3].x;
     }
     const int64_t mbase = (int64_t)inst * P.msg_elems;
-    const float om = 1.0f - th;
+    const int64_t rbase = (int64_t)inst * P.rho_elems;
     for (int q = R.parent_begin; q < R.parent_end; ++q) {
-        const PairInfo pi = P.pair[P.parent_pairs[q]];
-        const float4* nb = reinterpret_cast<const float4*>(P.nu + mbase + pi.off);
-        float4 m0 = nb[0], m1 = nb[1];
-        if (nest) {
-            const float4* zb = reinterpret_cast<const float4*>(P.zeta + mbase + pi.off);
-            const float4 z0 = zb[0], z1 = zb[1];
-            m0.x = om * m0.x + th * z0.x; m0.z = om * m0.z + th * z0.z; m0.w = om * m0.w + th * z0.w;
-            m1.z = om * m1.z + th * z1.z;
-        }
-        a += m0.x; br += m0.z; bi += m0.w; d += m1.z;
+        const PairInfo pi = P.parent_info[q];
+        float2 m[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) m[x] = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+        a += m[0].x; br += m[1].x; bi += m[1].y; d += m[3].x;
     }
     // children of a one-site region do not exist (no proper non-empty subset)
     const float m = 0.5f * (a + d);
@@ -232,12 +230,209 @@ __global__ void __launch_bounds__(kBlock) region_pass_d2_kernel(const DevProblem
         F = lmin;
     }
     if (R.rho_off >= 0) {
-        float4* dst = reinterpret_cast<float4*>(P.rho + (int64_t)inst * P.rho_elems + R.rho_off);
+        float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off);
         dst[0] = make_float4(0.5f * (1.f - kap * hh), 0.f, -0.5f * kap * br, -0.5f * kap * bi);
         dst[1] = make_float4(-0.5f * kap * br, 0.5f * kap * bi, 0.5f * (1.f + kap * hh), 0.f);
     }
     P.val[(int64_t)inst * P.n_regions + r] = (double)F;
     if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+}
+
+// 4 x 4 regions, one thread per region: the whole cyclic Jacobi runs in registers with
+// compile-time indices (six rotations per sweep, in the two-pair rounds (0,1)(2,3),
+// (0,2)(1,3), (0,3)(1,2)), so the only dependencies are ALU latencies.  Same inputs,
+// outputs and arithmetic conventions as region_pass_kernel<4>.
+__device__ __forceinline__ void t4_rotate(float (&ar)[4][4], float (&ai)[4][4], float (&vr)[4][4], float (&vi)[4][4],
+                                          int p, int q) {
+    float c, wr, wi;
+    rot_params(ar[p][p], ar[q][q], ar[p][q], ai[p][q], c, wr, wi);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {   // A <- A J  (columns p, q)
+        mix_cols(ar[r][p], ai[r][p], ar[r][q], ai[r][q], c, wr, wi);
+        mix_cols(vr[r][p], vi[r][p], vr[r][q], vi[r][q], c, wr, wi);
+    }
+#pragma unroll
+    for (int col = 0; col < 4; ++col) {   // A <- J^H A  (rows p, q): y_p' = c y_p + w y_q, y_q' = -conj(w) y_p + c y_q
+        const float ypr = ar[p][col], ypi = ai[p][col], yqr = ar[q][col], yqi = ai[q][col];
+        ar[p][col] = c * ypr + (wr * yqr - wi * yqi);
+        ai[p][col] = c * ypi + (wr * yqi + wi * yqr);
+        ar[q][col] = c * yqr - (wr * ypr + wi * ypi);
+        ai[q][col] = c * yqi - (wr * ypi - wi * ypr);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem P, const PassIO io,
+                                                               const int32_t* __restrict__ cls, const int32_t count,
+                                                               const int k) {
+    __shared__ unsigned long long blk_sweeps;
+    if (threadIdx.x == 0) blk_sweeps = 0ull;
+    const Thetas T = pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+    __syncthreads();
+    const int64_t unit = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+    int sweeps = 0;
+    if (unit < (int64_t)P.n_inst * count) {
+        const int inst = (int)(unit / count);
+        const int r = cls[unit % count];
+        const RegionInfo R = P.reg[r];
+        const bool nest = P.st->variant == 1;
+        float ar[4][4], ai[4][4], vr[4][4], vi[4][4];
+        if (R.h_off >= 0) {
+            const float4* h = reinterpret_cast<const float4*>(P.h32 + (int64_t)inst * P.h_elems + R.h_off);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const float4 v = h[2 * i + j];
+                    ar[i][2 * j] = v.x; ai[i][2 * j] = v.y; ar[i][2 * j + 1] = v.z; ai[i][2 * j + 1] = v.w;
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { ar[i][j] = 0.f; ai[i][j] = 0.f; }
+        }
+        const int64_t mbase = (int64_t)inst * P.msg_elems;
+        const int64_t rbase = (int64_t)inst * P.rho_elems;
+        // children of a two-site region are its sites: mask 2 = first site (nu (x) 1), mask 1 = second (1 (x) nu)
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            float2 m[2][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const int x = 2 * a + b;
+                    m[a][b] = pass_entry(io, T, mbase + pi.off + x, rbase + pi.child_rho + x, false);
+                }
+            if (pi.mask == 2) {   // nu (x) 1
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+#pragma unroll
+                        for (int o = 0; o < 2; ++o) { ar[2 * a + o][2 * b + o] -= m[a][b].x; ai[2 * a + o][2 * b + o] -= m[a][b].y; }
+            } else {              // 1 (x) nu
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+#pragma unroll
+                        for (int o = 0; o < 2; ++o) { ar[2 * o + a][2 * o + b] -= m[a][b].x; ai[2 * o + a][2 * o + b] -= m[a][b].y; }
+            }
+        }
+        for (int q = R.parent_begin; q < R.parent_end; ++q) {
+            const PairInfo pi = P.parent_info[q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int x = 4 * i + j;
+                    const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                    ar[i][j] += m.x;
+                    ai[i][j] += m.y;
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { vr[i][j] = (i == j) ? 1.f : 0.f; vi[i][j] = 0.f; }
+        float n2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) n2 += ar[i][j] * ar[i][j] + ai[i][j] * ai[i][j];
+        const float thresh = 1e-12f * n2;
+        const int max_sweeps = P.st->max_sweeps;
+        for (;;) {
+            float off = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) off += (i == j) ? 0.f : ar[i][j] * ar[i][j] + ai[i][j] * ai[i][j];
+            if (off <= thresh || sweeps >= max_sweeps) break;
+            ++sweeps;
+            t4_rotate(ar, ai, vr, vi, 0, 1);
+            t4_rotate(ar, ai, vr, vi, 2, 3);
+            t4_rotate(ar, ai, vr, vi, 0, 2);
+            t4_rotate(ar, ai, vr, vi, 1, 3);
+            t4_rotate(ar, ai, vr, vi, 0, 3);
+            t4_rotate(ar, ai, vr, vi, 1, 2);
+        }
+        float lam[4], w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lam[i] = ar[i][i];
+        const float lmin = fminf(fminf(lam[0], lam[1]), fminf(lam[2], lam[3]));
+        float F;
+        if (nest) {
+            const float beta = (float)P.st->beta;
+            float Z = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { w[i] = expf(-beta * (lam[i] - lmin)); Z += w[i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] /= Z;
+            F = lmin - logf(Z) / beta;
+        } else {
+            const float tau = (float)P.st->degen_tol * fmaxf(1.0f, sqrtf(n2));
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { w[i] = (lam[i] - lmin <= tau) ? 1.f : 0.f; m += w[i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) w[i] /= m;
+            F = lmin;
+        }
+        // rho = V diag(w) V^dagger, upper triangle computed, lower = conjugate, real diagonal
+        float rr[4][4], ri[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = i; j < 4; ++j) {
+                float sr = 0.f, si = 0.f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float xr = w[c] * vr[j][c], xi = w[c] * vi[j][c];
+                    sr += vr[i][c] * xr + vi[i][c] * xi;
+                    si += vi[i][c] * xr - vr[i][c] * xi;
+                }
+                rr[i][j] = sr; ri[i][j] = (i == j) ? 0.f : si;
+                rr[j][i] = sr; ri[j][i] = (i == j) ? 0.f : -si;
+            }
+        if (R.rho_off >= 0) {
+            float4* dst = reinterpret_cast<float4*>(io.rho_out + rbase + R.rho_off);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    dst[2 * i + j] = make_float4(rr[i][2 * j], ri[i][2 * j], rr[i][2 * j + 1], ri[i][2 * j + 1]);
+        }
+        float2* trb = io.tr_out + mbase;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            float2 tt[2][2];
+            if (pi.mask == 2) {   // keep the first site: trace out the second
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+                        tt[a][b] = make_float2(rr[2 * a][2 * b] + rr[2 * a + 1][2 * b + 1], ri[2 * a][2 * b] + ri[2 * a + 1][2 * b + 1]);
+            } else {              // keep the second site
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int b = 0; b < 2; ++b)
+                        tt[a][b] = make_float2(rr[a][b] + rr[2 + a][2 + b], ri[a][b] + ri[2 + a][2 + b]);
+            }
+            float4* tdst = reinterpret_cast<float4*>(trb + pi.off);
+            tdst[0] = make_float4(tt[0][0].x, tt[0][0].y, tt[0][1].x, tt[0][1].y);
+            tdst[1] = make_float4(tt[1][0].x, tt[1][0].y, tt[1][1].x, tt[1][1].y);
+        }
+        P.val[(int64_t)inst * P.n_regions + r] = (double)F;
+        if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
 }
 
 // ---------------------------------------------------------------- FP64 certification
@@ -293,7 +488,7 @@ __global__ void certify_d2_kernel(const DevProblem P, const int32_t* __restrict_
     }
     const int64_t mbase = (int64_t)inst * P.msg_elems;
     for (int q = R.parent_begin; q < R.parent_end; ++q) {
-        const PairInfo pi = P.pair[P.parent_pairs[q]];
+        const PairInfo pi = P.parent_info[q];
         const float2* nb = msg + mbase + pi.off;
         a += (double)nb[0].x; br += (double)nb[1].x; bi += (double)nb[1].y; d += (double)nb[3].x;
     }
@@ -306,24 +501,20 @@ __global__ void certify_d2_kernel(const DevProblem P, const int32_t* __restrict_
 // ---------------------------------------------------------------- message update
 // One thread per two consecutive complex entries of one instance's message array (every
 // block holds D_f^2 >= 4 entries, so the two never straddle pairs).
+// Alg. 1 update (and the gradient-only mode of lrh_evaluate), one thread per two consecutive
+// complex entries of one instance's message array (every block holds D_f^2 >= 4 entries, so
+// the two never straddle pairs): g = rho_f - Tr_{e\f} rho_e; nu += alpha_t g, with nu_best
+// copied first when the previous pass set a new best q.
 __global__ void update_kernel(const DevProblem P, const int par, const int mode) {
     const int64_t halfm = P.msg_elems >> 1;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double thd = P.st->theta[par];
     const double td = P.st->t[par];
-    if (tid == 0 && mode == UPD_STEP) {
-        // scalars of the next iteration (other parity slot)
-        P.st->theta[par ^ 1] = (sqrt(thd * thd * thd * thd + 4.0 * thd * thd) - thd * thd) * 0.5;
-        P.st->t[par ^ 1] = td + 1.0;
-    }
+    if (tid == 0 && mode == UPD_STEP) P.st->t[par ^ 1] = td + 1.0;
     if (tid >= (int64_t)P.n_inst * halfm) return;
     const int inst = (int)(tid / halfm);
     const int64_t e = (tid % halfm) * 2;
-    const int p = P.chunk_pair[e >> 2];
-    const PairInfo pi = P.pair[p];
-    const RegionInfo Rf = P.reg[pi.child];
     const int64_t mi = (int64_t)inst * P.msg_elems + e;
-    const float4 rf = *reinterpret_cast<const float4*>(P.rho + (int64_t)inst * P.rho_elems + Rf.rho_off + (e - pi.off));
+    const float4 rf = *reinterpret_cast<const float4*>(P.rho + (int64_t)inst * P.rho_elems + P.chunk_rho[e >> 2] + e);
     const float4 tv = *reinterpret_cast<const float4*>(P.tr + mi);
     const float4 gv = make_float4(rf.x - tv.x, rf.y - tv.y, rf.z - tv.z, rf.w - tv.w);
     if (mode == UPD_GRAD_ONLY) {
@@ -331,25 +522,41 @@ __global__ void update_kernel(const DevProblem P, const int par, const int mode)
         return;
     }
     float4 nv = *reinterpret_cast<const float4*>(P.nu + mi);
-    if (P.st->variant == 1) {
-        const float th = (float)thd;
-        const float kz = (float)(P.st->inv_lhat / thd);
-        float4 z = *reinterpret_cast<const float4*>(P.zeta + mi);
-        z.x = fmaf(kz, gv.x, z.x); z.y = fmaf(kz, gv.y, z.y); z.z = fmaf(kz, gv.z, z.z); z.w = fmaf(kz, gv.w, z.w);
-        const float om = 1.0f - th;
-        nv.x = fmaf(th, z.x, om * nv.x); nv.y = fmaf(th, z.y, om * nv.y);
-        nv.z = fmaf(th, z.z, om * nv.z); nv.w = fmaf(th, z.w, om * nv.w);
-        *reinterpret_cast<float4*>(P.zeta + mi) = z;
-    } else {
-        if (P.best_flag[inst]) *reinterpret_cast<float4*>(P.nu_best + mi) = nv;
-        const double a0 = P.st->alpha;
-        const float alpha = (float)(P.st->step_rule == 1 ? a0 / sqrt(td + 1.0) : a0);
-        nv.x = fmaf(alpha, gv.x, nv.x); nv.y = fmaf(alpha, gv.y, nv.y);
-        nv.z = fmaf(alpha, gv.z, nv.z); nv.w = fmaf(alpha, gv.w, nv.w);
-    }
+    if (P.best_flag[inst]) *reinterpret_cast<float4*>(P.nu_best + mi) = nv;
+    const double a0 = P.st->alpha;
+    const float alpha = (float)(P.st->step_rule == 1 ? a0 / sqrt(td + 1.0) : a0);
+    nv.x = fmaf(alpha, gv.x, nv.x); nv.y = fmaf(alpha, gv.y, nv.y);
+    nv.z = fmaf(alpha, gv.z, nv.z); nv.w = fmaf(alpha, gv.w, nv.w);
     if (!(isfinite(nv.x) && isfinite(nv.y) && isfinite(nv.z) && isfinite(nv.w))) atomicOr(P.err, DEV_ERR_NUMERIC);
     *reinterpret_cast<float4*>(P.nu + mi) = nv;
 }
+
+// Alg. 2: the pending update of iteration t = t0 + io.rel (its states in io.rho_in / tr_in, its
+// multipliers in io.nu_in / zeta_in) written to io.nu_out / zeta_out.
+__global__ void finalize_kernel(const DevProblem P, const PassIO io) {
+    const int64_t halfm = P.msg_elems >> 1;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)P.n_inst * halfm) return;
+    const long long t = P.st->t0 + io.rel;
+    const double thd = P.st->th3[t % 3];
+    const float th = (float)thd;
+    const float kz = (float)(P.st->inv_lhat / thd);
+    const int inst = (int)(tid / halfm);
+    const int64_t e = (tid % halfm) * 2;
+    const int64_t mi = (int64_t)inst * P.msg_elems + e;
+    const int64_t ri = (int64_t)inst * P.rho_elems + P.chunk_rho[e >> 2] + e;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        float2 n = io.nu_in[mi + j], z = io.zeta_in[mi + j];
+        const float2 r = io.rho_in[ri + j], tv = io.tr_in[mi + j];
+        nesterov_update(n, z, r.x - tv.x, r.y - tv.y, th, kz);
+        if (!(isfinite(n.x) && isfinite(n.y) && isfinite(z.x) && isfinite(z.y))) atomicOr(P.err, DEV_ERR_NUMERIC);
+        io.nu_out[mi + j] = n;
+        io.zeta_out[mi + j] = z;
+    }
+}
+
+__global__ void advance_kernel(IterState* st, int n) { st->t0 += n; }
 
 // Deterministic per-instance FP64 sum of per-region values (fixed strided partial sums and a
 // fixed tree), with optional Alg. 1 best-so-far tracking.
@@ -381,7 +588,12 @@ __global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, con
 __global__ void set_state_kernel(IterState* st, int par, double theta, double t, int set_theta_t, double beta,
                                  double inv_lhat, double alpha, double degen_tol, int variant, int step_rule,
                                  int max_sweeps) {
-    if (set_theta_t) { st->theta[par] = theta; st->t[par] = t; }
+    if (set_theta_t) {
+        st->theta[par] = theta;
+        st->t[par] = t;
+        st->t0 = 0;
+        st->th3[0] = theta;
+    }
     st->beta = beta;
     st->inv_lhat = inv_lhat;
     st->alpha = alpha;
@@ -391,20 +603,36 @@ __global__ void set_state_kernel(IterState* st, int par, double theta, double t,
     st->max_sweeps = max_sweeps;
 }
 
-template <int D>
+template <int D, int BLOCK>
 cudaError_t set_pass_attr() {
-    return cudaFuncSetAttribute(region_pass_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PassSmem<D>::bytes);
+    return cudaFuncSetAttribute(region_pass_kernel<D, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)PassSmem<D, BLOCK>::bytes);
+}
+
+template <int D, int BLOCK>
+cudaError_t launch_pass_DB(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k,
+                           cudaStream_t s) {
+    constexpr int G = BLOCK / D;
+    const int64_t units = (int64_t)P.n_inst * count;
+    const int64_t blocks = (units + G - 1) / G;
+    region_pass_kernel<D, BLOCK><<<(unsigned)blocks, BLOCK, PassSmem<D, BLOCK>::bytes, s>>>(P, io, cls, count, k);
+    return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_pass_D(const DevProblem& P, const int32_t* cls, int32_t count, int par, int k, cudaStream_t s) {
-    const size_t smem = PassSmem<D>::bytes;
-    constexpr int G = kBlock / D;
-    const int64_t units = (int64_t)P.n_inst * count;
-    const int64_t blocks = (units + G - 1) / G;
-    region_pass_kernel<D><<<(unsigned)blocks, kBlock, smem, s>>>(P, cls, count, par, k);
-    return cudaGetLastError();
+cudaError_t launch_pass_D(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k,
+                          cudaStream_t s, int block) {
+    if (block == 64) return launch_pass_DB<D, 64>(P, io, cls, count, k, s);
+    if (block == 256) return launch_pass_DB<D, 256>(P, io, cls, count, k, s);
+    return launch_pass_DB<D, 128>(P, io, cls, count, k, s);
+}
+
+template <int D>
+cudaError_t set_pass_attrs() {
+    cudaError_t e;
+    if ((e = set_pass_attr<D, 64>()) != cudaSuccess) return e;
+    if ((e = set_pass_attr<D, 128>()) != cudaSuccess) return e;
+    return set_pass_attr<D, 256>();
 }
 
 template <int D>
@@ -420,28 +648,42 @@ cudaError_t launch_cert_D(const DevProblem& P, const int32_t* cls, int32_t count
 
 cudaError_t prepare_kernels() {
     cudaError_t e;
-    if ((e = set_pass_attr<4>()) != cudaSuccess) return e;
-    if ((e = set_pass_attr<8>()) != cudaSuccess) return e;
-    if ((e = set_pass_attr<16>()) != cudaSuccess) return e;
-    if ((e = set_pass_attr<32>()) != cudaSuccess) return e;
+    if ((e = set_pass_attrs<4>()) != cudaSuccess) return e;
+    if ((e = set_pass_attrs<8>()) != cudaSuccess) return e;
+    if ((e = set_pass_attrs<16>()) != cudaSuccess) return e;
+    if ((e = set_pass_attrs<32>()) != cudaSuccess) return e;
     return prepare_cta_kernels();
 }
 
-cudaError_t launch_region_pass(const DevProblem& P, int k, const int32_t* cls, int32_t count, int par,
-                               cudaStream_t s) {
+cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, const int32_t* cls, int32_t count,
+                               cudaStream_t s, int block) {
     if (count <= 0) return cudaSuccess;
+    if (block > 0 && block != 64 && block != 256) block = 128;
+    if (block < 0 && k != 2) block = 128;   // the one-thread-per-region layout exists for 4 x 4 only
+    if (k == 1 && block < 0) block = 128;
     switch (k) {
         case 1: {
             const int64_t units = (int64_t)P.n_inst * count;
-            region_pass_d2_kernel<<<(unsigned)((units + kBlock - 1) / kBlock), kBlock, 0, s>>>(P, cls, count, par);
+            region_pass_d2_kernel<<<(unsigned)((units + block - 1) / block), block, 0, s>>>(P, io, cls, count);
             return cudaGetLastError();
         }
-        case 2: return launch_pass_D<4>(P, cls, count, par, k, s);
-        case 3: return launch_pass_D<8>(P, cls, count, par, k, s);
-        case 4: return launch_pass_D<16>(P, cls, count, par, k, s);
-        case 5: return launch_pass_D<32>(P, cls, count, par, k, s);
+        case 2: {
+            if (block < 0) {
+                const int tb = -block;
+                const int64_t units = (int64_t)P.n_inst * count;
+                const unsigned grid = (unsigned)((units + tb - 1) / tb);
+                if (tb == 64) region_pass_t4_kernel<64><<<grid, 64, 0, s>>>(P, io, cls, count, k);
+                else if (tb == 256) region_pass_t4_kernel<256><<<grid, 256, 0, s>>>(P, io, cls, count, k);
+                else region_pass_t4_kernel<128><<<grid, 128, 0, s>>>(P, io, cls, count, k);
+                return cudaGetLastError();
+            }
+            return launch_pass_D<4>(P, io, cls, count, k, s, block);
+        }
+        case 3: return launch_pass_D<8>(P, io, cls, count, k, s, block);
+        case 4: return launch_pass_D<16>(P, io, cls, count, k, s, block);
+        case 5: return launch_pass_D<32>(P, io, cls, count, k, s, block);
         case 6:
-        case 7: return launch_region_pass_cta(P, k, cls, count, par, s);
+        case 7: return launch_region_pass_cta(P, io, k, cls, count, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -469,6 +711,18 @@ cudaError_t launch_update(const DevProblem& P, int par, int mode, cudaStream_t s
     const int64_t n = (int64_t)P.n_inst * (P.msg_elems >> 1);
     const int64_t blocks = (n + 255) / 256;
     update_kernel<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(P, par, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DevProblem& P, const PassIO& io, cudaStream_t s) {
+    const int64_t n = (int64_t)P.n_inst * (P.msg_elems >> 1);
+    if (n <= 0) return cudaSuccess;
+    finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, io);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const DevProblem& P, int n, cudaStream_t s) {
+    advance_kernel<<<1, 1, 0, s>>>(P.st, n);
     return cudaGetLastError();
 }
 

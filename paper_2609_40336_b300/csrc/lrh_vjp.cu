@@ -45,7 +45,7 @@ __device__ __forceinline__ float kdd(float lk, float ll, float pk, float pl, flo
 
 template <int D>
 __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, const int32_t* __restrict__ cls,
-                                                         const int32_t count, const int par) {
+                                                         const int32_t count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = kVB / D;
     const int g = threadIdx.x / D;
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
     const bool valid = unit < (int64_t)P.n_inst * count;
     const int inst = valid ? (int)(unit / count) : 0;
     const int r = valid ? cls[unit % count] : 0;
-    const float th = (float)P.st->theta[par];
+    const float th = (float)P.st->th3[P.st->t0 % 3];
     const float beta = (float)P.st->beta;
 
     float ar[D], ai[D], vr[D], vi[D];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
         for (int c = 0; c < D; ++c) dst[c] = Yb[s * D + c];
         float2* trb = P.tr + (int64_t)inst * P.msg_elems;
         for (int q = R.child_begin; q < R.child_end; ++q) {
-            const PairInfo pi = P.pair[P.child_pairs[q]];
+            const PairInfo pi = P.child_info[q];
             const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
             for (int idx = s; idx < Df * Df; idx += D) {
                 const int ra = pdep_bits(idx >> kf, M), rb = pdep_bits(idx & (Df - 1), M);
@@ -242,10 +242,10 @@ __global__ void vjp_termbar_kernel(const DevProblem P, float2* __restrict__ term
 }
 
 template <int D>
-cudaError_t vjp_D(const DevProblem& P, const int32_t* cls, int32_t count, int par, cudaStream_t s) {
+cudaError_t vjp_D(const DevProblem& P, const int32_t* cls, int32_t count, cudaStream_t s) {
     constexpr int G = kVB / D;
     const int64_t units = (int64_t)P.n_inst * count;
-    vjp_region_kernel<D><<<(unsigned)((units + G - 1) / G), kVB, VjpSmem<D>::bytes, s>>>(P, cls, count, par);
+    vjp_region_kernel<D><<<(unsigned)((units + G - 1) / G), kVB, VjpSmem<D>::bytes, s>>>(P, cls, count);
     return cudaGetLastError();
 }
 
@@ -266,14 +266,14 @@ cudaError_t prepare_vjp_kernels() {
     return vjp_attr<32>();
 }
 
-cudaError_t launch_vjp_region(const DevProblem& P, int k, const int32_t* cls, int32_t count, int par, cudaStream_t s) {
+cudaError_t launch_vjp_region(const DevProblem& P, int k, const int32_t* cls, int32_t count, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     switch (k) {
-        case 1: return vjp_D<2>(P, cls, count, par, s);
-        case 2: return vjp_D<4>(P, cls, count, par, s);
-        case 3: return vjp_D<8>(P, cls, count, par, s);
-        case 4: return vjp_D<16>(P, cls, count, par, s);
-        case 5: return vjp_D<32>(P, cls, count, par, s);
+        case 1: return vjp_D<2>(P, cls, count, s);
+        case 2: return vjp_D<4>(P, cls, count, s);
+        case 3: return vjp_D<8>(P, cls, count, s);
+        case 4: return vjp_D<16>(P, cls, count, s);
+        case 5: return vjp_D<32>(P, cls, count, s);
         default: return cudaErrorInvalidValue;
     }
 }

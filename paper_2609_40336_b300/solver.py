@@ -120,7 +120,8 @@ class Solver:
                     max_region_sites=inf.max_region_sites, msg_elems=inf.msg_elems,
                     lambda_G=inf.lambda_G, gamma_G=inf.gamma_G, iteration=inf.iteration,
                     class_sites=list(inf.class_sites[:nc]), class_regions=list(inf.class_regions[:nc]),
-                    sweeps=[int(x) for x in inf.sweeps[:nc]])
+                    sweeps=[int(x) for x in inf.sweeps[:nc]], class_block=list(inf.class_block[:nc]),
+                    concurrent_classes=bool(inf.concurrent_classes))
 
     def pairs(self):
         par = np.zeros(self.n_pairs, np.int32)
@@ -144,6 +145,17 @@ class Solver:
             raise TypeError(f"unknown options {sorted(kw)}")
         L.check(self._lib.lrh_set_options(self._h, C.byref(o)), "lrh_set_options")
 
+    def autotune(self, cache_path: Optional[str] = None, force: bool = False) -> dict:
+        """Pick launch shapes on this problem (see lrh_autotune); returns the chosen shapes."""
+        path = cache_path.encode() if cache_path else None
+        L.check(self._lib.lrh_autotune(self._h, path, 1 if force else 0), "lrh_autotune")
+        inf = self.info()
+        return dict(class_sites=inf["class_sites"], class_block=inf["class_block"],
+                    concurrent_classes=inf["concurrent_classes"])
+
+    def set_launch_shape(self, k_sites: int, block: int) -> None:
+        L.check(self._lib.lrh_set_launch_shape(self._h, int(k_sites), int(block)), "lrh_set_launch_shape")
+
     def restart(self) -> None:
         L.check(self._lib.lrh_restart(self._h), "lrh_restart")
 
@@ -159,6 +171,33 @@ class Solver:
 
     def synchronize(self) -> None:
         L.check(self._lib.lrh_synchronize(self._h), "lrh_synchronize")
+
+    def kappa(self) -> int:
+        """kappa_G = max over sites i of the number of pairs e->f with i in f (Thm 6); at
+        level 1 this is Delta_G, the maximum node degree (Thm 4)."""
+        par, chi, _ = self.pairs()
+        regions = self._keep["region_sites"], self._keep["region_ptr"]
+        sites, ptr = regions
+        count = {}
+        for f in chi:
+            for sidx in sites[ptr[f]:ptr[f + 1]]:
+                count[int(sidx)] = count.get(int(sidx), 0) + 1
+        return max(count.values()) if count else 0
+
+    def theorem_parameters(self, eps: float, n_sites: int, R: Optional[float] = None, c_frac: float = 0.5) -> dict:
+        """Parameter rules of the convergence theorems for a target error density eps:
+        Alg. 2 (Thm 5, Thm 7): beta = 2 Gamma_G / (n eps), L_hat = beta Lambda_G / 2 and, given
+        R = dist(nu0, argmax Q_beta), T >= 2 R sqrt(Gamma_G Lambda_G) / (n eps) - 1;
+        Alg. 1 (Thm 4, Thm 6): alpha = c eps with c = c_frac / kappa_G < 1 / kappa_G and, given R,
+        T >= R^2 / (2 c (1 - c kappa_G) n eps^2)."""
+        beta = 2.0 * self.gamma_G / (n_sites * eps)
+        kap = self.kappa()
+        c = c_frac / kap
+        out = dict(beta=beta, lhat=beta * self.lambda_G / 2.0, alpha=c * eps, kappa_G=kap)
+        if R is not None:
+            out["T_nesterov"] = int(np.ceil(2.0 * R * np.sqrt(self.gamma_G * self.lambda_G) / (n_sites * eps) - 1))
+            out["T_subgradient"] = int(np.ceil(R ** 2 / (2.0 * c * (1.0 - c * kap) * n_sites * eps ** 2)))
+        return out
 
     def run_schedule(self, betas: Sequence[float], iters_per_stage: int) -> None:
         """Alg. 2 under beta continuation: per beta, L_hat = beta Lambda_G / 2,
@@ -190,6 +229,17 @@ class Solver:
         arr = np.zeros((self.n_instances, self.msg_elems), np.complex64)
         L.check(self._lib.lrh_get_messages(self._h, _MSGS[which], arr.ctypes.data, nbytes, 0), "lrh_get_messages")
         return arr
+
+    def get_state(self) -> bytes:
+        """Checkpoint of the iteration (see lrh_get_state)."""
+        n = int(self._lib.lrh_state_bytes(self._h))
+        buf = np.zeros(n, np.uint8)
+        L.check(self._lib.lrh_get_state(self._h, buf.ctypes.data, n), "lrh_get_state")
+        return buf.tobytes()
+
+    def set_state(self, state: bytes) -> None:
+        buf = np.frombuffer(state, np.uint8).copy()
+        L.check(self._lib.lrh_set_state(self._h, buf.ctypes.data, buf.size), "lrh_set_state")
 
     def set_terms(self, term_mats) -> None:
         """Replace the term matrices (same supports as at creation); list of

@@ -33,3 +33,21 @@ def test_comparator_matches_oracle():
         blk = st.nu[0, P.msg_off[q]:P.msg_off[q] + 4].reshape(2, 2)
         assert np.abs(nu_c[eidx, which] - blk).max() < 1e-10
     assert abs(comp.bound() - dual.dual_value(P, h, st.nu)[0]) < 1e-10
+
+
+def test_poset_comparator_matches_oracle_on_clusters():
+    """The general-poset comparator (plaquettes, intervals) against the oracle at 1e-10."""
+    for p in (g.lattices.j1j2_square(3, J2s=(0.5,)), g.lattices.perturbed_chain(8, L=3, delta=0.4, seed=2)):
+        comp = bench.TorchFP64Poset(p, torch.device("cpu"))
+        P = Poset(p.regions)
+        h = dual.local_terms(p, P)
+        assert comp.lam == P.lipschitz_lambda()
+        st = dual.NesterovState(nu=dual.zeros_messages(P, 1), zeta=dual.zeros_messages(P, 1))
+        th = 1.0
+        for beta in (1.0, 4.0):
+            for _ in range(3):
+                q_c = float(comp.iterate(th, beta, beta * comp.lam / 2))
+                res = dual.nesterov_step(P, h, st, beta, beta * comp.lam / 2)
+                th = bench.next_theta(th)
+                assert abs(q_c - res.value.sum()) < 1e-10 * abs(q_c)
+        assert abs(comp.bound() - dual.dual_value(P, h, st.nu)[0]) < 1e-10 * abs(comp.bound())

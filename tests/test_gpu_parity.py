@@ -196,3 +196,87 @@ def test_messages_stay_traceless_on_gpu():
         Df = int(P.D[P.pair_child[q]])
         M = nu[P.msg_off[q]:P.msg_off[q] + Df * Df].reshape(Df, Df)
         assert abs(np.trace(M)) < 1e-5 * max(1.0, np.abs(M).max())
+
+
+@pytest.mark.parametrize("variant", ["nesterov", "subgradient"])
+def test_checkpoint_resume_is_bitwise_identical(variant):
+    p, _, _ = setup("xxz_tri4_plaq")
+    kw = dict(beta=4.0) if variant == "nesterov" else dict(alpha=0.3, step_rule="inv_sqrt")
+    a = Solver(p, variant=variant, **kw)
+    a.step(13)
+    state = a.get_state()
+    a.step(21)
+    b = Solver(p, variant=variant, **kw)
+    b.set_state(state)
+    b.step(21)
+    for w in ("nu", "zeta", "nu_best"):
+        assert np.array_equal(a.messages(w), b.messages(w)), w
+    if variant == "subgradient":
+        assert np.array_equal(a.bound("best"), b.bound("best"))
+
+
+def test_autotune_chooses_valid_shapes_and_uses_cache(tmp_path):
+    """Lane layouts change only which CTA runs a region (bit-identical results); the
+    one-thread 4x4 layout agrees to rounding.  The second call reads the cache."""
+    p, P, h = setup("xxz_tri4_plaq")
+    s = Solver(p, beta=4.0)
+    s.step(5)
+    s.evaluate()
+    g0, v0 = s.messages("grad"), s.region_values("last")
+    cache = tmp_path / "tune.jsonl"
+    shapes = s.autotune(str(cache), force=True)
+    assert all(b in (64, 128, 256) or (k == 2 and b in (-64, -128, -256))
+               for k, b in zip(shapes["class_sites"], shapes["class_block"]))
+    lines = cache.read_text().splitlines()
+    assert len(lines) >= 1 and all(l.startswith("{") for l in lines)
+    s.evaluate()
+    g1, v1 = s.messages("grad"), s.region_values("last")
+    if all(b > 0 for b in shapes["class_block"]):
+        assert np.array_equal(g1, g0) and np.array_equal(v1, v0)
+    else:
+        assert np.max(np.abs(v1 - v0)) <= 1e-5 and grad_rel_err(g1, g0.astype(np.complex128), P.n_pairs) <= 1e-5
+    s2 = Solver(p, beta=4.0)
+    shapes2 = s2.autotune(str(cache))
+    assert shapes2 == shapes and cache.read_text().splitlines() == lines
+
+
+@pytest.mark.parametrize("block", [64, 256, -128])
+def test_launch_shapes_of_the_4x4_class_match_the_oracle(block):
+    p, P, h = setup("heis8x8_level1")
+    nu = random_traceless_messages(P, 1, seed=17, scale=0.7)
+    s = Solver(p, variant="nesterov", beta=4.0)
+    s.set_launch_shape(2, block)
+    s.set_messages("nu", nu)
+    s.restart()
+    s.evaluate()
+    ref = dual.region_pass(P, h, nu.astype(np.complex128), "smooth", beta=4.0)
+    tn = theta_norms(P, h, nu)
+    assert np.max(np.abs(s.region_values("last") - ref.value)) <= 1e-5 * max(1.0, tn)
+    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= grad_tol(4.0, tn)
+    s.step(12)
+    ref_s = Solver(p, variant="nesterov", beta=4.0)
+    ref_s.set_messages("nu", nu)
+    ref_s.restart()
+    ref_s.step(12)
+    a, b = s.messages("nu"), ref_s.messages("nu")
+    if block > 0:
+        assert np.array_equal(a, b)
+    else:
+        assert np.linalg.norm(a - b) <= 1e-5 * max(1.0, np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["heis8x8_level1", "xxz_tri4_plaq", "chain_L6_D64", "chain_L7_D128"])
+def test_fused_iterations_equal_single_iterations(name):
+    """Alg. 2 runs n iterations as n region passes that apply the previous update on the fly
+    (ping-pong buffers) plus one final update; n single-iteration calls apply every update
+    in the final-update kernel.  Both must give bit-identical messages."""
+    p, _, _ = setup(name)
+    a = Solver(p, beta=2.0, use_graph=False)
+    b = Solver(p, beta=2.0, use_graph=True)
+    a.step(7)
+    for _ in range(7):
+        b.step(1)
+    b.step(6)
+    a.step(6)
+    for w in ("nu", "zeta"):
+        assert np.array_equal(a.messages(w), b.messages(w)), w
