@@ -587,6 +587,31 @@ def run_lrh(args, ws, rank, dev, stream):
     s.close()
 
 
+KERNEL_SOURCES = ["lrh_kernels.cu", "lrh_device.cuh", "lrh_internal.cuh", "lrh_cta.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2609_40336_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/traffic.json),
+    only while the kernel sources are the ones that capture measured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(WL_KEY)
+    if not rec or rec.get("kernel_sources_sha256_16") != kernel_source_hash():
+        return None
+    return rec
+
+
 def roofline(s, dev, stream, k):
     """Dominant kernel: the region pass of class k, timed with CUDA events around a CUDA graph
     of back-to-back launches on the library's stream (no host launch gaps)."""
@@ -625,8 +650,11 @@ def roofline(s, dev, stream, k):
     sweeps = (inf1["sweeps"][ci] - inf0["sweeps"][ci]) / (reps * n_reg)
     fpr = 20 * sweeps * D * D * (D - 1) + 8 * D ** 3
     achieved = n_reg * fpr / dur / 1e12
+    tr = recorded_traffic()
     return {"bound": "alu", "kernel": f"region pass, {n_reg} regions of {D}x{D}", "achieved": achieved,
-            "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+            "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "traffic_note": tr.get("note") if tr else "no ncu capture of the current kernel sources",
             "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)",
             "launch_us": dur * 1e6, "sweeps_per_region": sweeps, "flops_per_region": fpr,
             "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger"}
@@ -684,7 +712,13 @@ def measure_extras(s, p, dev, stream, args, fstar, zero, value):
     if True:
         try:
             per_it = time_fp64_comparator(p, dev)
+            ttt = None
+            if out.get("iters_to_1e-4"):
+                ttt = per_it * out["iters_to_1e-4"]
             out["fp64_torch_comparator"] = {"ms_per_iteration": per_it * 1e3,
+                                            "time_to_1e-4_per_site_s_estimate": ttt,
+                                            "time_to_1e-4_speedup": (ttt / out["time_to_1e-4_per_site_s"])
+                                            if ttt and out.get("time_to_1e-4_per_site_s") else None,
                                             "region_eigensolves_per_s": s.n_regions / per_it,
                                             "speedup_per_region_eigensolve": value / (s.n_regions / per_it),
                                             "note": "single instance, same Alg. 2 iteration in complex128"}

@@ -78,9 +78,11 @@ __device__ __forceinline__ void rot_params_c(T app, T aqq, T br, T bi, RotC<T>& 
 
 __device__ __forceinline__ int tri(int i, int j, int D) { return i * D - ((i * (i - 1)) >> 1) + (j - i); }
 
+// Hermitian matrix in shared memory as a packed upper triangle (FP64 certification).
 template <typename T>
 struct Packed {
     using C2 = typename V2<T>::t;
+    using Real = T;
     C2* a;
     int D;
     __device__ __forceinline__ C2 get(int i, int j) const {
@@ -91,6 +93,41 @@ struct Packed {
     }
     __device__ __forceinline__ void set(int i, int j, C2 v) const {
         if (i <= j) { a[tri(i, j, D)] = v; } else { v.y = -v.y; a[tri(j, i, D)] = v; }
+    }
+    __device__ __forceinline__ C2 dget(int i) const { return a[tri(i, i, D)]; }
+    __device__ __forceinline__ void dset(int i, C2 v) const { a[tri(i, i, D)] = v; }
+    // sums of |a_ij|^2 over the upper triangle (diagonal included) and over the diagonal
+    template <int NT>
+    __device__ __forceinline__ void sums(T& upper, T& diag) const {
+        upper = T(0); diag = T(0);
+        for (int e = threadIdx.x; e < D * (D + 1) / 2; e += NT) { const C2 v = a[e]; upper += v.x * v.x + v.y * v.y; }
+        for (int i = threadIdx.x; i < D; i += NT) { const C2 v = a[tri(i, i, D)]; diag += v.x * v.x + v.y * v.y; }
+    }
+};
+
+// Hermitian matrix in shared memory, both triangles stored row-major (FP32 pass): one
+// multiply-add per address; every write of an off-diagonal entry also writes its mirror.
+template <typename T>
+struct Full {
+    using C2 = typename V2<T>::t;
+    using Real = T;
+    C2* a;
+    int D;
+    __device__ __forceinline__ C2 get(int i, int j) const { return a[i * D + j]; }
+    __device__ __forceinline__ void set(int i, int j, C2 v) const {
+        a[i * D + j] = v;
+        v.y = -v.y;
+        a[j * D + i] = v;
+    }
+    __device__ __forceinline__ C2 dget(int i) const { return a[i * (D + 1)]; }
+    __device__ __forceinline__ void dset(int i, C2 v) const { a[i * (D + 1)] = v; }
+    template <int NT>
+    __device__ __forceinline__ void sums(T& upper, T& diag) const {
+        upper = T(0); diag = T(0);
+        for (int e = threadIdx.x; e < D * D; e += NT) {
+            const int i = e / D, j = e - (e / D) * D;
+            if (i <= j) { const C2 v = a[e]; upper += v.x * v.x + v.y * v.y; if (i == j) diag += v.x * v.x; }
+        }
     }
 };
 
@@ -154,10 +191,12 @@ struct CtaSmem {
     static constexpr size_t bytes = off_red + sizeof(double) * (NT / 32) + 16;
 };
 
-// Cyclic Jacobi on the packed matrix; V (if WANT_V) holds row `row`, columns
-// [chunk * W, chunk * W + W) in slot order.  Returns the sweeps run.
-template <int D, typename T, bool WANT_V>
-__device__ int jacobi_cta(Packed<T> A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
+// Cyclic Jacobi on the Hermitian matrix behind accessor A; V (if WANT_V) holds row `row`,
+// columns [chunk * W, chunk * W + W) in slot order.  Two barriers per round: after the rotation
+// parameters, and after the block updates (the slot map is double-buffered and its next
+// state written during the update phase).  Returns the sweeps run.
+template <int D, typename T, bool WANT_V, typename Acc>
+__device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
                           T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out) {
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
@@ -166,43 +205,27 @@ __device__ int jacobi_cta(Packed<T> A, RotC<T>* prm, int* idx0, int* idx1, const
     constexpr int W = D / CH;
     const int t = threadIdx.x;
     const int chunk = t % CH;
-    T n2 = T(0);
-    for (int e = t; e < (int)(D * (D + 1) / 2); e += NT) {
-        const auto v = A.a[e];
-        n2 += v.x * v.x + v.y * v.y;   // diagonal counted once, off-diagonal below
-    }
-    // off-diagonal entries appear once in the triangle but twice in ||A||_F^2
-    T offd = T(0);
-    for (int i = t; i < D; i += NT) {
-        const auto v = A.a[tri(i, i, D)];
-        offd += v.x * v.x + v.y * v.y;
-    }
-    const T norm2 = T(2) * block_sum<NT>(n2, red) - block_sum<NT>(offd, red);
+    T up, dg;
+    A.template sums<NT>(up, dg);
+    const T norm2 = T(2) * block_sum<NT>(up, red) - block_sum<NT>(dg, red);
     norm2_out = norm2;
     const T thresh = tol2 * norm2;
     int* ix = idx0;
     int* ixn = idx1;
     int sweeps = 0;
     for (;;) {
-        T diag = T(0), tot = T(0);
-        for (int e = t; e < (int)(D * (D + 1) / 2); e += NT) {
-            const auto v = A.a[e];
-            tot += v.x * v.x + v.y * v.y;
-        }
-        for (int i = t; i < D; i += NT) {
-            const auto v = A.a[tri(i, i, D)];
-            diag += v.x * v.x + v.y * v.y;
-        }
-        const T off = T(2) * (block_sum<NT>(tot, red) - block_sum<NT>(diag, red));
+        A.template sums<NT>(up, dg);
+        const T off = T(2) * (block_sum<NT>(up, red) - block_sum<NT>(dg, red));
         if (off <= thresh || sweeps >= max_sweeps) break;
         ++sweeps;
         for (int r = 0; r < D - 1; ++r) {
             if (t < n) {
                 const int p = ix[2 * t], q = ix[2 * t + 1];
                 const auto b = A.get(p, q);
-                rot_params_c<T>(A.a[tri(p, p, D)].x, A.a[tri(q, q, D)].x, b.x, b.y, prm[t]);
+                rot_params_c<T>(A.dget(p).x, A.dget(q).x, b.x, b.y, prm[t]);
             }
             __syncthreads();
+            if (t < D) ixn[t] = ix[rr_src_c(t, D)];
             if (WANT_V) {
 #pragma unroll
                 for (int m = 0; m < W / 2; ++m) {
@@ -221,15 +244,15 @@ __device__ int jacobi_cta(Packed<T> A, RotC<T>* prm, int* idx0, int* idx1, const
                 const RotC<T> K = prm[kk];
                 const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
                 if (kk == ll) {
-                    auto b00 = A.a[tri(pk, pk, D)];
-                    auto b11 = A.a[tri(qk, qk, D)];
+                    auto b00 = A.dget(pk);
+                    auto b11 = A.dget(qk);
                     auto b01 = A.get(pk, qk);
                     auto b10 = b01; b10.y = -b10.y;
                     b00.y = T(0); b11.y = T(0);
                     two_sided<T>(b00, b01, b10, b11, K, K);
                     b00.y = T(0); b11.y = T(0);
-                    A.a[tri(pk, pk, D)] = b00;
-                    A.a[tri(qk, qk, D)] = b11;
+                    A.dset(pk, b00);
+                    A.dset(qk, b11);
                     auto z = b01; z.x = T(0); z.y = T(0);
                     A.set(pk, qk, z);
                 } else {
@@ -240,8 +263,6 @@ __device__ int jacobi_cta(Packed<T> A, RotC<T>* prm, int* idx0, int* idx1, const
                     A.set(pk, pl, b00); A.set(pk, ql, b01); A.set(qk, pl, b10); A.set(qk, ql, b11);
                 }
             }
-            __syncthreads();
-            if (t < D) ixn[t] = ix[rr_src_c(t, D)];
             if (WANT_V) {
                 // new[c] = old[rr_src(c)] over global slots; chunk boundaries move one value each way
                 const T flr = __shfl_up_sync(kFull, vr[W - 2], 1);
@@ -315,7 +336,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
 // FP32 pass version: message entries from pass_entry (pending Alg. 2 update applied); the
 // region owns its parent messages and also stores the conjugate (lower-triangle) entries.
 template <int D>
-__device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Packed<float> A, const PassIO& io,
+__device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Full<float> A, const PassIO& io,
                                    const dev::Thetas& T) {
     constexpr int NT = CtaCfg<D>::NT;
     const int64_t mbase = (int64_t)inst * P.msg_elems;
@@ -349,7 +370,7 @@ __device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int
             re += m.x; im += m.y;
         }
         if (i == j) im = 0.f;
-        A.a[tri(i, j, D)] = make_float2(re, im);
+        A.set(i, j, make_float2(re, im));
     }
 }
 
@@ -389,7 +410,7 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     if (io.writer && blockIdx.x == 0 && t == 0) dev::advance_theta(P, io);
     build_table<D, float>(tab);
     if (t < D) idx0[t] = t;
-    Packed<float> A{buf, D};
+    Full<float> A{buf, D};
     assemble_packed_io<D>(P, R, inst, A, io, Th);
     __syncthreads();
     const int row = t / 4, chunk = t % 4;
@@ -399,7 +420,7 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     float norm2;
     const int sweeps = jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2);
     // the slot maps are back to the identity after whole sweeps: diag = eigenvalues
-    if (t < D) lam[t] = buf[tri(t, t, D)].x;
+    if (t < D) lam[t] = buf[t * (D + 1)].x;
     __syncthreads();
     float lmin = lam[0];
     for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
@@ -424,9 +445,12 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
         buf[c * D + row] = make_float2(vr[m] * q, vi[m] * q);
     }
     __syncthreads();
-    // rho = W W^dagger in TR x TC register tiles: rho[i][c] = sum_k W[i][k] conj(W[c][k])
+    // rho = W W^dagger in TR x TC register tiles: rho[i][c] = sum_k W[i][k] conj(W[c][k]); a thread
+    // owns rows i0 .. i0+TR-1 and the strided columns cb + (D/TC) b, so that consecutive threads
+    // read and write consecutive columns (no shared-memory bank conflicts)
     const int rb = t / (D / TC), cb = t % (D / TC);
-    const int i0 = rb * TR, c0 = cb * TC;
+    const int i0 = rb * TR;
+    constexpr int CS = D / TC;
     float accr[TR][TC], acci[TR][TC];
 #pragma unroll
     for (int a = 0; a < TR; ++a)
@@ -438,7 +462,7 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
 #pragma unroll
         for (int a = 0; a < TR; ++a) wi[a] = wk[i0 + a];
 #pragma unroll
-        for (int b = 0; b < TC; ++b) wc[b] = wk[c0 + b];
+        for (int b = 0; b < TC; ++b) wc[b] = wk[cb + CS * b];
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
@@ -451,7 +475,7 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
 #pragma unroll
     for (int a = 0; a < TR; ++a)
 #pragma unroll
-        for (int b = 0; b < TC; ++b) buf[(i0 + a) * D + c0 + b] = make_float2(accr[a][b], acci[a][b]);
+        for (int b = 0; b < TC; ++b) buf[(i0 + a) * D + cb + CS * b] = make_float2(accr[a][b], acci[a][b]);
     __syncthreads();
     // exact Hermitian symmetry: lower triangle := conj(upper), real diagonal
     for (int e = t; e < D * D; e += NT) {

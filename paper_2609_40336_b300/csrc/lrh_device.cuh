@@ -316,6 +316,31 @@ __device__ __forceinline__ float2 pass_entry(const PassIO& io, const Thetas& T, 
     return extrapolate(n, z, T.cur);
 }
 
+// Two consecutive entries (mi, ri even: 16-byte aligned) with float4 loads and stores; the same
+// per-entry arithmetic as pass_entry.
+__device__ __forceinline__ float4 pass_entry2(const PassIO& io, const Thetas& T, int64_t mi, int64_t ri, bool owner) {
+    float4 n = *reinterpret_cast<const float4*>(io.nu_in + mi);
+    if (!io.zeta_in) return n;
+    float4 z = *reinterpret_cast<const float4*>(io.zeta_in + mi);
+    if (io.pending) {
+        const float4 r = *reinterpret_cast<const float4*>(io.rho_in + ri);
+        const float4 t = *reinterpret_cast<const float4*>(io.tr_in + mi);
+        float2 n0 = make_float2(n.x, n.y), n1 = make_float2(n.z, n.w);
+        float2 z0 = make_float2(z.x, z.y), z1 = make_float2(z.z, z.w);
+        nesterov_update(n0, z0, r.x - t.x, r.y - t.y, T.prev, T.kz);
+        nesterov_update(n1, z1, r.z - t.z, r.w - t.w, T.prev, T.kz);
+        n = make_float4(n0.x, n0.y, n1.x, n1.y);
+        z = make_float4(z0.x, z0.y, z1.x, z1.y);
+        if (owner) {
+            *reinterpret_cast<float4*>(io.nu_out + mi) = n;
+            *reinterpret_cast<float4*>(io.zeta_out + mi) = z;
+        }
+    }
+    const float2 e0 = extrapolate(make_float2(n.x, n.y), make_float2(z.x, z.y), T.cur);
+    const float2 e1 = extrapolate(make_float2(n.z, n.w), make_float2(z.z, z.w), T.cur);
+    return make_float4(e0.x, e0.y, e1.x, e1.y);
+}
+
 // Row s of theta_e for an FP32 pass: h_e - sum_children 1 (x) m + sum_parents m with the
 // message entries of pass_entry.
 template <int D>
@@ -352,12 +377,24 @@ __device__ __forceinline__ void assemble_row_io(const DevProblem& P, const Regio
     }
     for (int q = R.parent_begin; q < R.parent_end; ++q) {
         const PairInfo pi = P.parent_info[q];
+        if constexpr (D <= 8) {   // float4 gathers; at larger D the unrolled loads would crowd the registers
 #pragma unroll
-        for (int c = 0; c < D; ++c) {
-            const int64_t x = (int64_t)s * D + c;
-            const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
-            ar[c] += m.x;
-            ai[c] += m.y;
+            for (int c = 0; c < D; c += 2) {
+                const int64_t x = (int64_t)s * D + c;
+                const float4 m = pass_entry2(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                ar[c] += m.x;
+                ai[c] += m.y;
+                ar[c + 1] += m.z;
+                ai[c + 1] += m.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int64_t x = (int64_t)s * D + c;
+                const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                ar[c] += m.x;
+                ai[c] += m.y;
+            }
         }
     }
 }

@@ -37,24 +37,29 @@ using namespace dev;
 template <int D, int BLOCK>
 struct PassSmem {
     static constexpr int kGroups = BLOCK / D;
-    static constexpr size_t per_group = (D / 2) * sizeof(Rot<float>) + D * sizeof(float) + 2 * D * D * sizeof(float2);
+    static constexpr int LD = D + 2;   // padded row stride (float2) of the W / rho staging: rows of
+                                       // different lanes start in different banks, float4 stays aligned
+    static constexpr size_t per_group = (D / 2) * sizeof(Rot<float>) + D * sizeof(float) + 2 * D * LD * sizeof(float2);
     static constexpr size_t bytes = kGroups * per_group + 16;
 };
 
+// Register budget per lane of the lane-row pass (A and V rows plus the round's temporaries).
+template <int D> struct RegCap { static constexpr int v = D == 32 ? 232 : (D == 16 ? 128 : (D == 8 ? 96 : 80)); };
+
 // FP32 region pass for 4 <= D <= 32; BLOCK threads = BLOCK / D regions per CTA (autotuned).
 template <int D, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, const PassIO io,
-                                                            const int32_t* __restrict__ cls, const int32_t count,
-                                                            const int k) {
+__device__ __forceinline__ void region_pass_impl(const DevProblem& P, const PassIO& io, const int32_t* __restrict__ cls,
+                                                 const int32_t count, const int k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = BLOCK / D;
     const int g = threadIdx.x / D;
     const int s = threadIdx.x % D;
     unsigned char* base = smem_raw + g * PassSmem<D, BLOCK>::per_group;
     Rot<float>* prm = reinterpret_cast<Rot<float>*>(base);
+    constexpr int LD = PassSmem<D, BLOCK>::LD;
     float2* Wb = reinterpret_cast<float2*>(base + (D / 2) * sizeof(Rot<float>));
-    float2* Rb = Wb + D * D;
-    float* pw = reinterpret_cast<float*>(Rb + D * D);
+    float2* Rb = Wb + D * LD;
+    float* pw = reinterpret_cast<float*>(Rb + D * LD);
     __shared__ unsigned long long blk_sweeps;
     if (threadIdx.x == 0) blk_sweeps = 0ull;
 
@@ -108,13 +113,13 @@ __global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, 
 #pragma unroll
     for (int c = 0; c < D; ++c) { const float q = pw[c]; ar[c] = vr[c] * q; ai[c] = vi[c] * q; }
     {
-        float4* wrow = reinterpret_cast<float4*>(Wb + s * D);
+        float4* wrow = reinterpret_cast<float4*>(Wb + s * LD);
 #pragma unroll
         for (int c = 0; c < D / 2; ++c) wrow[c] = make_float4(ar[2 * c], ai[2 * c], ar[2 * c + 1], ai[2 * c + 1]);
     }
     __syncwarp();
     for (int j = 0; j < D; ++j) {
-        const float4* wj = reinterpret_cast<const float4*>(Wb + j * D);
+        const float4* wj = reinterpret_cast<const float4*>(Wb + j * LD);
         float accr = 0.f, acci = 0.f;
 #pragma unroll
         for (int c = 0; c < D / 2; ++c) {
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, 
             accr += ar[2 * c + 1] * x.z + ai[2 * c + 1] * x.w;
             acci += ai[2 * c + 1] * x.z - ar[2 * c + 1] * x.w;
         }
-        Rb[s * D + j] = make_float2(accr, acci);
+        Rb[s * LD + j] = make_float2(accr, acci);
     }
     __syncwarp();
     // Make rho exactly Hermitian (the two triangles come from differently rounded sums):
@@ -134,21 +139,21 @@ __global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, 
         float2 fix[D];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const float2 up = Rb[j * D + s];
+            const float2 up = Rb[j * LD + s];
             fix[j] = make_float2(up.x, -up.y);
         }
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            if (j < s) Rb[s * D + j] = fix[j];
-            if (j == s) Rb[s * D + j].y = 0.f;
+            if (j < s) Rb[s * LD + j] = fix[j];
+            if (j == s) Rb[s * LD + j].y = 0.f;
         }
     }
     __syncwarp();
     if (valid) {
         if (R.rho_off >= 0) {
             float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off + (int64_t)s * D);
-            const float4* srcr = reinterpret_cast<const float4*>(Rb + s * D);
+            const float4* srcr = reinterpret_cast<const float4*>(Rb + s * LD);
 #pragma unroll
             for (int c = 0; c < D / 2; ++c) dst[c] = srcr[c];
         }
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, 
                 float accr = 0.f, acci = 0.f;
                 for (int c = 0; c < nrest; ++c) {
                     const int x = pdep_bits(c, Mc);
-                    const float2 v = Rb[(ra | x) * D + (rb | x)];
+                    const float2 v = Rb[(ra | x) * LD + (rb | x)];
                     accr += v.x;
                     acci += v.y;
                 }
@@ -183,6 +188,21 @@ __global__ void __launch_bounds__(BLOCK) region_pass_kernel(const DevProblem P, 
     if (valid && s == 0) atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
     __syncthreads();
     if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
+}
+
+template <int D, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) __maxnreg__(RegCap<D>::v) region_pass_kernel(const DevProblem P, const PassIO io,
+                                                                                       const int32_t* __restrict__ cls,
+                                                                                       const int32_t count, const int k) {
+    region_pass_impl<D, BLOCK>(P, io, cls, count, k);
+}
+
+// D = 32 keeps ptxas's own register heuristic (explicit caps made it spill).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) region_pass_kernel32(const DevProblem P, const PassIO io,
+                                                              const int32_t* __restrict__ cls, const int32_t count,
+                                                              const int k) {
+    region_pass_impl<32, BLOCK>(P, io, cls, count, k);
 }
 
 // D = 2 closed form, one thread per region.  theta = m I + K, K = [[hh, b], [conj(b), -hh]],
@@ -208,10 +228,9 @@ __global__ void __launch_bounds__(256) region_pass_d2_kernel(const DevProblem P,
     const int64_t rbase = (int64_t)inst * P.rho_elems;
     for (int q = R.parent_begin; q < R.parent_end; ++q) {
         const PairInfo pi = P.parent_info[q];
-        float2 m[4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x) m[x] = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
-        a += m[0].x; br += m[1].x; bi += m[1].y; d += m[3].x;
+        const float4 m01 = pass_entry2(io, T, mbase + pi.off, rbase + R.rho_off, true);
+        const float4 m23 = pass_entry2(io, T, mbase + pi.off + 2, rbase + R.rho_off + 2, true);
+        a += m01.x; br += m01.z; bi += m01.w; d += m23.z;
     }
     // children of a one-site region do not exist (no proper non-empty subset)
     const float m = 0.5f * (a + d);
@@ -327,11 +346,10 @@ __global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem 
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 4; j += 2) {
                     const int x = 4 * i + j;
-                    const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
-                    ar[i][j] += m.x;
-                    ai[i][j] += m.y;
+                    const float4 m = pass_entry2(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                    ar[i][j] += m.x; ai[i][j] += m.y; ar[i][j + 1] += m.z; ai[i][j + 1] += m.w;
                 }
         }
 #pragma unroll
@@ -605,8 +623,12 @@ __global__ void set_state_kernel(IterState* st, int par, double theta, double t,
 
 template <int D, int BLOCK>
 cudaError_t set_pass_attr() {
-    return cudaFuncSetAttribute(region_pass_kernel<D, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)PassSmem<D, BLOCK>::bytes);
+    if constexpr (D == 32)
+        return cudaFuncSetAttribute(region_pass_kernel32<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PassSmem<D, BLOCK>::bytes);
+    else
+        return cudaFuncSetAttribute(region_pass_kernel<D, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PassSmem<D, BLOCK>::bytes);
 }
 
 template <int D, int BLOCK>
@@ -615,7 +637,10 @@ cudaError_t launch_pass_DB(const DevProblem& P, const PassIO& io, const int32_t*
     constexpr int G = BLOCK / D;
     const int64_t units = (int64_t)P.n_inst * count;
     const int64_t blocks = (units + G - 1) / G;
-    region_pass_kernel<D, BLOCK><<<(unsigned)blocks, BLOCK, PassSmem<D, BLOCK>::bytes, s>>>(P, io, cls, count, k);
+    if constexpr (D == 32)
+        region_pass_kernel32<BLOCK><<<(unsigned)blocks, BLOCK, PassSmem<D, BLOCK>::bytes, s>>>(P, io, cls, count, k);
+    else
+        region_pass_kernel<D, BLOCK><<<(unsigned)blocks, BLOCK, PassSmem<D, BLOCK>::bytes, s>>>(P, io, cls, count, k);
     return cudaGetLastError();
 }
 

@@ -28,8 +28,9 @@ constexpr int kVB = 128;
 template <int D>
 struct VjpSmem {
     static constexpr int G = kVB / D;
+    static constexpr int LD = D + 2;   // padded row stride (float2) of the staged matrices
     static constexpr size_t per_group = (D / 2 > 0 ? D / 2 : 1) * sizeof(Rot<float>) + 2 * D * sizeof(float) +
-                                        2 * (size_t)D * D * sizeof(float2);
+                                        2 * (size_t)D * LD * sizeof(float2);
     static constexpr size_t bytes = G * ((per_group + 15) / 16 * 16) + 16;
 };
 
@@ -54,8 +55,9 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
     Rot<float>* prm = reinterpret_cast<Rot<float>*>(base);
     float* lam = reinterpret_cast<float*>(base + (D / 2 > 0 ? D / 2 : 1) * sizeof(Rot<float>));
     float* pp = lam + D;
+    constexpr int LD = VjpSmem<D>::LD;
     float2* Vb = reinterpret_cast<float2*>(pp + D);
-    float2* Yb = Vb + D * D;
+    float2* Yb = Vb + D * LD;
 
     const int64_t unit = (int64_t)blockIdx.x * G + g;
     const bool valid = unit < (int64_t)P.n_inst * count;
@@ -93,32 +95,32 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
         assemble_row<D, float>(P, R0, inst, s, P.gbar, nullptr, 0.0f, false, ar, ai);
     }
 #pragma unroll
-    for (int c = 0; c < D; ++c) { Vb[s * D + c] = make_float2(vr[c], vi[c]); Yb[s * D + c] = make_float2(ar[c], ai[c]); }
+    for (int c = 0; c < D; ++c) { Vb[s * LD + c] = make_float2(vr[c], vi[c]); Yb[s * LD + c] = make_float2(ar[c], ai[c]); }
     __syncwarp();
     // (1) Y = rho_bar V  (row s; own row of rho_bar from smem, rows of V broadcast)
     float yr[D], yi[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) { yr[c] = 0.f; yi[c] = 0.f; }
     for (int j = 0; j < D; ++j) {
-        const float2 a = Yb[s * D + j];
+        const float2 a = Yb[s * LD + j];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const float2 v = Vb[j * D + c];
+            const float2 v = Vb[j * LD + c];
             yr[c] += a.x * v.x - a.y * v.y;
             yi[c] += a.x * v.y + a.y * v.x;
         }
     }
 #pragma unroll
-    for (int c = 0; c < D; ++c) Yb[s * D + c] = make_float2(yr[c], yi[c]);   // own row only
+    for (int c = 0; c < D; ++c) Yb[s * LD + c] = make_float2(yr[c], yi[c]);   // own row only
     __syncwarp();
     // (2) M = V^dagger Y  (row k = s): M[k][c] = sum_i conj(V[i][k]) Y[i][c]
 #pragma unroll
     for (int c = 0; c < D; ++c) { yr[c] = 0.f; yi[c] = 0.f; }
     for (int i = 0; i < D; ++i) {
-        const float2 v = Vb[i * D + s];
+        const float2 v = Vb[i * LD + s];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const float2 y = Yb[i * D + c];
+            const float2 y = Yb[i * LD + c];
             yr[c] += v.x * y.x + v.y * y.y;
             yi[c] += v.x * y.y - v.y * y.x;
         }
@@ -135,17 +137,17 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
         const float kv = kdd(lam[s], lam[c], pp[s], pp[c], beta);
         float xr = yr[c] * kv, xi = yi[c] * kv;
         if (c == s) xr += coef * pp[s];
-        Yb[s * D + c] = make_float2(xr, xi);
+        Yb[s * LD + c] = make_float2(xr, xi);
     }
     __syncwarp();
     // (3) Zr = V X  (row s; own row of V from smem, rows of X broadcast)
 #pragma unroll
     for (int c = 0; c < D; ++c) { yr[c] = 0.f; yi[c] = 0.f; }
     for (int j = 0; j < D; ++j) {
-        const float2 a = Vb[s * D + j];
+        const float2 a = Vb[s * LD + j];
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const float2 x = Yb[j * D + c];
+            const float2 x = Yb[j * LD + c];
             yr[c] += a.x * x.x - a.y * x.y;
             yi[c] += a.x * x.y + a.y * x.x;
         }
@@ -156,29 +158,29 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
         float tr_ = 0.f, ti_ = 0.f;
 #pragma unroll
         for (int c = 0; c < D; ++c) {
-            const float2 v = Vb[j * D + c];
+            const float2 v = Vb[j * LD + c];
             tr_ += yr[c] * v.x + yi[c] * v.y;
             ti_ += yi[c] * v.x - yr[c] * v.y;
         }
-        Yb[s * D + j] = make_float2(tr_, ti_);
+        Yb[s * LD + j] = make_float2(tr_, ti_);
     }
     __syncwarp();
     {
         float2 fix[D];
 #pragma unroll
-        for (int j = 0; j < D; ++j) { const float2 up = Yb[j * D + s]; fix[j] = make_float2(up.x, -up.y); }
+        for (int j = 0; j < D; ++j) { const float2 up = Yb[j * LD + s]; fix[j] = make_float2(up.x, -up.y); }
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            if (j < s) Yb[s * D + j] = fix[j];
-            if (j == s) Yb[s * D + j].y = 0.f;
+            if (j < s) Yb[s * LD + j] = fix[j];
+            if (j == s) Yb[s * LD + j].y = 0.f;
         }
     }
     __syncwarp();
     if (valid) {
         float2* dst = P.thb + (int64_t)inst * P.all_elems + R.all_off + (int64_t)s * D;
 #pragma unroll
-        for (int c = 0; c < D; ++c) dst[c] = Yb[s * D + c];
+        for (int c = 0; c < D; ++c) dst[c] = Yb[s * LD + c];
         float2* trb = P.tr + (int64_t)inst * P.msg_elems;
         for (int q = R.child_begin; q < R.child_end; ++q) {
             const PairInfo pi = P.child_info[q];
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
                 float sr = 0.f, si = 0.f;
                 for (int c = 0; c < nrest; ++c) {
                     const int x = pdep_bits(c, Mc);
-                    const float2 v = Yb[(ra | x) * D + (rb | x)];
+                    const float2 v = Yb[(ra | x) * LD + (rb | x)];
                     sr += v.x; si += v.y;
                 }
                 trb[pi.off + idx] = make_float2(sr, si);
