@@ -496,8 +496,8 @@ def job_throughput(units_per_rank, iters, steps, total_ms_max, world):
 def make_solver(p, stream):
     from paper_2609_40336_b300 import Solver
     if WL.variant == "nesterov":
-        return Solver(p, variant="nesterov", beta=WL.betas[0], use_graph=True, stream=stream.cuda_stream)
-    return Solver(p, variant="subgradient", alpha=WL.alpha, step_rule=WL.step_rule, use_graph=True,
+        return Solver(p, variant="nesterov", beta=WL.betas[0], loop="auto", stream=stream.cuda_stream)
+    return Solver(p, variant="subgradient", alpha=WL.alpha, step_rule=WL.step_rule, loop="auto",
                   stream=stream.cuda_stream)
 
 
@@ -513,13 +513,17 @@ def solve(s, zero):
     return s.bound("certified")
 
 
-def launches_per_step(n_classes):
+def launches_per_step(n_classes, loop):
     """Kernels of the library per step: Alg. 2 stage = 2 state kernels (options, restart) +
-    one pass (n_classes kernels) per iteration + final update + advance; Alg. 1 iteration =
-    n_classes passes + reduce + update; then n_classes certification kernels + 1 reduction."""
+    one pass (n_classes kernels) per iteration + final update + advance, or with the persistent
+    driver one cooperative kernel + final update + advance; Alg. 1 = restart kernel + per
+    iteration n_classes passes + reduce + update, or one cooperative kernel; then n_classes
+    certification kernels + 1 reduction."""
     if WL.variant == "nesterov":
-        return len(WL.betas) * (2 + WL.iters_per_stage * n_classes + 2) + n_classes + 1
-    return 1 + WL.n_iterations() * (n_classes + 2) + n_classes + 1
+        per_stage = 1 + 2 if loop == "persistent" else WL.iters_per_stage * n_classes + 2
+        return len(WL.betas) * (2 + per_stage) + n_classes + 1
+    body = 1 if loop == "persistent" else WL.n_iterations() * (n_classes + 2)
+    return 1 + body + n_classes + 1
 
 
 def run_lrh(args, ws, rank, dev, stream):
@@ -575,13 +579,13 @@ def run_lrh(args, ws, rank, dev, stream):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 bound reduction and certification)",
                 "data": "synthetic", "config": config({"parallelism": f"independent problem per GPU x{ws}",
-                                                       "launch_shapes": tuned}),
+                                                       "launch_shapes": tuned, "loop_driver": s.info()["loop"]}),
                 "certified_bound_per_site": [float(b) / p.n_sites for b in bounds][:8],
                 "gap_per_site_vs_converged": (float(np.max(np.atleast_1d(fstar["fstar"]) - np.asarray(bounds))) / p.n_sites)
                 if fstar else None,
                 "us_per_iteration": 1e3 * total_ms / args.steps / iters,
                 "wall_s_timed_region": wall, "clocks": clocks.summary(),
-                "gpu_launches": launches_per_step(len(inf["class_sites"])) * args.steps}
+                "gpu_launches": launches_per_step(len(inf["class_sites"]), s.info()["loop"]) * args.steps}
         line.update(extras)
         print(json.dumps(line), flush=True)
     s.close()
@@ -660,6 +664,52 @@ def roofline(s, dev, stream, k):
             "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger"}
 
 
+def roofline_persistent(s, dev, stream, n_iter):
+    """Dominant kernel under the persistent driver: one cooperative launch running n_iter
+    iterations of every class (timed with CUDA events on the library's stream around the
+    lrh_step call, which adds the small final-update and advance kernels)."""
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    s.restart()
+    s.step(n_iter)                      # warm
+    s.restart()
+    torch.cuda.synchronize()
+    inf0 = s.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(n_iter)
+    e1.record(stream)
+    e1.synchronize()
+    dur = e0.elapsed_time(e1) * 1e-3
+    inf1 = s.info()
+    flops, parts = 0.0, []
+    for ci, k in enumerate(inf1["class_sites"]):
+        D = 2 ** k
+        regions = inf1["class_regions"][ci] * s.n_instances
+        if D == 2:
+            parts.append(f"{regions} regions of 2x2 (closed form, not counted)")
+            continue
+        sweeps = inf1["sweeps"][ci] - inf0["sweeps"][ci]
+        flops += 20.0 * sweeps * D * D * (D - 1) + 8.0 * D ** 3 * regions * n_iter
+        parts.append(f"{regions} regions of {D}x{D} ({sweeps / (regions * n_iter):.2f} sweeps)")
+    achieved = flops / dur / 1e12
+    return {"bound": "alu", "kernel": f"persist_kernel: {n_iter} iterations of " + ", ".join(parts),
+            "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+            "traffic": None, "traffic_note": "cooperative launch not captured with ncu (multi-pass replay of a grid barrier)",
+            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)",
+            "launch_us": dur * 1e6, "us_per_iteration": dur * 1e6 / n_iter,
+            "flop_model": "sum over classes of 20*S*D^2*(D-1) + 8*D^3 per region and iteration"}
+
+
 def time_to_target(s, p, zero, fstar):
     """Wall time until the FP64-certified bound is within 1e-3 / 1e-4 per site of the
     converged reference (worst instance), certifying every CERT_EVERY iterations."""
@@ -704,7 +754,11 @@ def measure_extras(s, p, dev, stream, args, fstar, zero, value):
     out = {}
     n_units = s.n_regions * s.n_instances
     iters = WL.n_iterations()
-    out["roofline"] = roofline(s, dev, stream, WL.dominant_k)
+    if s.info()["loop"] == "persistent":
+        out["roofline"] = roofline_persistent(s, dev, stream, WL.iters_per_stage if WL.variant == "nesterov" else 200)
+        out["roofline_region_pass"] = roofline(s, dev, stream, WL.dominant_k)
+    else:
+        out["roofline"] = roofline(s, dev, stream, WL.dominant_k)
     # ---- time to 1e-4/site (certify every CERT_EVERY iterations, certification time included)
     if fstar:
         out.update(time_to_target(s, p, zero, fstar))

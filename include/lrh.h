@@ -65,7 +65,7 @@ extern "C" {
 #define LRH_EPOSET       (-3)  /* duplicate region, or a term fits in no region */
 #define LRH_ENOMEM       (-4)  /* host or device allocation failed */
 #define LRH_ECUDA        (-5)  /* a CUDA runtime call failed */
-#define LRH_ETIMEOUT     (-6)  /* reserved: a bounded device wait gave up */
+#define LRH_ETIMEOUT     (-6)  /* a bounded device wait gave up (grid barrier of the persistent launch) */
 #define LRH_ENUMERIC     (-7)  /* a non-finite eigenvalue, value or message was produced */
 #define LRH_EUNSUPPORTED (-8)  /* region size beyond the kernels built into this library */
 
@@ -75,6 +75,11 @@ extern "C" {
 
 #define LRH_STEP_CONST    0    /* alpha_t = alpha                        (Thm 4 choice)  */
 #define LRH_STEP_INV_SQRT 1    /* alpha_t = alpha / sqrt(t + 1)                           */
+
+#define LRH_LOOP_EAGER      0  /* lrh_options.loop: one launch per kernel per iteration        */
+#define LRH_LOOP_GRAPH      1  /* replay of a captured CUDA graph of iterations               */
+#define LRH_LOOP_PERSISTENT 2  /* one cooperative launch for all iterations of an lrh_step    */
+#define LRH_LOOP_AUTO       3  /* chosen by lrh_autotune (graph or persistent)                */
 
 #define LRH_MSG_NU        0    /* current multipliers nu                                  */
 #define LRH_MSG_ZETA      1    /* Nesterov auxiliary sequence zeta                        */
@@ -111,7 +116,15 @@ typedef struct {
     double  degen_tol;    /* ground space = eigenvalues within degen_tol * max(1,||theta||_F)
                              of lambda_min (subgradient); <= 0 selects 1e-5                   */
     int32_t max_sweeps;   /* Jacobi sweep cap of the FP32 eigensolver; <= 0 selects 15        */
-    int32_t use_graph;    /* nonzero: lrh_step replays a captured CUDA graph of iterations    */
+    int32_t loop;         /* iteration driver of lrh_step: LRH_LOOP_EAGER (kernel launches),
+                             LRH_LOOP_GRAPH (a captured CUDA graph of iterations),
+                             LRH_LOOP_PERSISTENT (one cooperative launch running all the
+                             iterations, grid-wide barriers between passes; problems whose
+                             classes all have <= 4 sites, else GRAPH), LRH_LOOP_AUTO (the
+                             choice of lrh_autotune; before it: PERSISTENT when the problem
+                             fits one wave of resident CTAs, else GRAPH).  All drivers give
+                             bit-identical messages for the same launch shapes; the
+                             persistent one runs every class in the lane layout.             */
 } lrh_options;
 
 typedef struct lrh_problem lrh_problem;
@@ -133,6 +146,9 @@ typedef struct {
     int32_t class_block[8];       /* threads per CTA of each class's region pass (autotuned);
                                      negative: one thread per region (4 x 4 regions)            */
     int32_t concurrent_classes;   /* 1: region classes run on forked streams within an iteration */
+    int32_t loop;                 /* driver lrh_step uses now (LRH_LOOP_EAGER/GRAPH/PERSISTENT)  */
+    int32_t persistent_grid;      /* CTAs of the persistent launch (0: not available)             */
+    int64_t persistent_tiles;     /* region tiles per pass in the persistent launch               */
 } lrh_info;
 
 /* ---------------------------------------------------------------- entry points */
@@ -216,11 +232,13 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
 
 /* Autotuner.  Times, on this problem's own data and stream, the launch shapes of every region
  * class with at most 5 sites (64, 128 or 256 threads per CTA, i.e. 64/D .. 256/D regions per
- * CTA) and whether the classes of one iteration run concurrently on forked streams, then
- * keeps the fastest.  Choices are read from / appended to `cache_path` (JSON lines keyed by
- * class size, region count and SM count; NULL = no cache); flags bit 0 forces re-measuring.
- * Runs region passes at the current point (their outputs are recomputed by the next
- * iteration), must not be called during stream capture, and synchronises. */
+ * CTA), whether the classes of one iteration run concurrently on forked streams, and, when
+ * the problem allows a persistent launch, the graph against the persistent iteration driver
+ * (used when lrh_options.loop is LRH_LOOP_AUTO); then keeps the fastest.  Choices are read
+ * from / appended to `cache_path` (JSON lines keyed by class size, region count and SM count;
+ * NULL = no cache); flags bit 0 forces re-measuring.  Runs region passes at the current point
+ * (their outputs are recomputed by the next iteration) and iterations on a saved copy of the
+ * multipliers, which it restores; must not be called during stream capture; synchronises. */
 int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
 
 /* Set the launch shape of one region class by hand (what lrh_autotune chooses): 64, 128 or
@@ -228,6 +246,14 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
  * one thread per region.  The lane layouts give bit-identical results; the one-thread layout
  * rotates in another order and agrees to rounding. */
 int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block);
+
+/* Self-test of the bounded grid-barrier wait of the persistent driver: one persistent launch
+ * whose first barrier is never released (it waits for one CTA more than the grid), so every CTA gives
+ * up after the wait limit (one second) and raises the timeout status.  Returns LRH_ETIMEOUT
+ * when the wait ended as designed (the status is then cleared and the problem stays usable;
+ * the pass before the barrier only rewrites states and values that the next iteration
+ * recomputes), LRH_EUNSUPPORTED when the problem has no persistent launch.  Synchronises. */
+int lrh_selftest_barrier_timeout(lrh_problem* p);
 
 /* Checkpoint / resume.  The state is the iteration scalars (theta_k, step counter, beta,
  * L_hat, alpha, iteration parity), nu, zeta, nu_best and q_best, packed into one host buffer

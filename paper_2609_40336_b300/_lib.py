@@ -45,7 +45,7 @@ class Options(C.Structure):
         ("lhat", C.c_double),
         ("degen_tol", C.c_double),
         ("max_sweeps", C.c_int32),
-        ("use_graph", C.c_int32),
+        ("loop", C.c_int32),
     ]
 
 
@@ -65,6 +65,9 @@ class Info(C.Structure):
         ("sweeps", C.c_uint64 * 8),
         ("class_block", C.c_int32 * 8),
         ("concurrent_classes", C.c_int32),
+        ("loop", C.c_int32),
+        ("persistent_grid", C.c_int32),
+        ("persistent_tiles", C.c_int64),
     ]
 
 
@@ -89,6 +92,7 @@ SIGNATURES = {
     "lrh_get_region_values": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "lrh_get_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrh_set_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
+    "lrh_selftest_barrier_timeout": (C.c_int, [C.c_void_p]),
     "lrh_synchronize": (C.c_int, [C.c_void_p]),
     "lrh_set_terms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lrh_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32]),

@@ -100,6 +100,13 @@ struct lrh_problem {
     // chosen by lrh_autotune (defaults: 128 threads, concurrent classes)
     std::vector<int> class_block;
     bool concurrent = true;
+    // persistent driver: plan of the cooperative launch (classes with k <= 4 only), its grid,
+    // the resident-CTA capacity and the autotuned driver for LRH_LOOP_AUTO (-1: not tuned)
+    PersistPlan plan{};
+    int persist_kmax = 0;
+    int persist_grid = 0;
+    int64_t persist_cap = 0;
+    int loop_auto = -1;
 
     template <typename T>
     int dalloc(T** ptr, int64_t count) {
@@ -134,6 +141,7 @@ int validate_options(const lrh_options* o) {
     if (o->variant == LRH_SUBGRADIENT && !(o->alpha > 0.0)) return fail(LRH_EINVAL, "alpha must be > 0");
     if (o->variant == LRH_NESTEROV && !(o->beta > 0.0)) return fail(LRH_EINVAL, "beta must be > 0");
     if (!std::isfinite(o->beta) || !std::isfinite(o->alpha) || !std::isfinite(o->lhat)) return fail(LRH_EINVAL, "non-finite option");
+    if (o->loop < LRH_LOOP_EAGER || o->loop > LRH_LOOP_AUTO) return fail(LRH_EINVAL, "unknown iteration driver (loop)");
     return LRH_OK;
 }
 
@@ -238,6 +246,93 @@ int launch_all_classes(lrh_problem* p, const PassIO& io0) {
     return LRH_OK;
 }
 
+// After n fused Alg. 2 passes: apply the pending update of the last pass (its multipliers in
+// A when n = 1 or n - 1 is even, else B; its states in X when n - 1 is even, else Y) into the
+// canonical A, and advance t0 by n.
+int enqueue_nesterov_tail(lrh_problem* p, int n) {
+    DevProblem& P = p->P;
+    PassIO fin{};
+    fin.rel = n - 1;
+    fin.nu_in = (n == 1) ? P.nu : ((n - 1) % 2 == 1 ? P.nu_b : P.nu);
+    fin.zeta_in = (n == 1) ? P.zeta : ((n - 1) % 2 == 1 ? P.zeta_b : P.zeta);
+    fin.rho_in = ((n - 1) % 2 == 0) ? P.rho : P.rho_b;
+    fin.tr_in = ((n - 1) % 2 == 0) ? P.tr : P.tr_b;
+    fin.nu_out = P.nu;
+    fin.zeta_out = P.zeta;
+    LRH_CK(launch_finalize(P, fin, p->stream));
+    LRH_CK(launch_advance(P, n, p->stream));
+    return LRH_OK;
+}
+
+// Driver lrh_step uses now (LRH_LOOP_EAGER / GRAPH / PERSISTENT).
+int effective_loop(const lrh_problem* p) {
+    int m = p->opt.loop;
+    if (m == LRH_LOOP_AUTO)
+        m = p->loop_auto >= 0 ? p->loop_auto
+                              : ((p->persist_grid > 0 && p->plan.tiles <= p->persist_cap) ? LRH_LOOP_PERSISTENT : LRH_LOOP_GRAPH);
+    if (m == LRH_LOOP_PERSISTENT && p->persist_grid <= 0) m = LRH_LOOP_GRAPH;
+    return m;
+}
+
+// n iterations in one cooperative launch (plus, for Alg. 2, the finalisation of the last pass).
+// Launches are split so that one launch's barrier arrivals (grid x barriers) stay below 2^30:
+// the 32-bit arrival counter never wraps.  Split Alg. 2 steps are bit-identical to one step.
+int run_persistent(lrh_problem* p, int n) {
+    PersistPlan L = p->plan;
+    L.nesterov = p->opt.variant == LRH_NESTEROV ? 1 : 0;
+    const int64_t per_iter = L.nesterov ? 1 : 3;
+    const int64_t max_n = std::max<int64_t>(1, ((int64_t)1 << 30) / ((int64_t)p->persist_grid * per_iter));
+    for (int done = 0; done < n;) {
+        const int c = (int)std::min<int64_t>(max_n, n - done);
+        L.n = c;
+        L.par0 = (int)((p->iteration + done) & 1);
+        LRH_CK(launch_persistent(p->P, L, p->persist_kmax, p->persist_grid, p->stream));
+        if (L.nesterov) {
+            const int rc = enqueue_nesterov_tail(p, c);
+            if (rc) return rc;
+        }
+        done += c;
+    }
+    return LRH_OK;
+}
+
+// Plan of the persistent launch: classes in cost order (heaviest first), tiles of
+// persistent_tile_regions(k) regions, grid = min(tiles, resident CTAs).  Not available when a
+// class has more than 4 sites or the device lacks cooperative launches.
+int plan_persistent(lrh_problem* p) {
+    p->persist_grid = 0;
+    const size_t nc = p->class_k.size();
+    if (nc == 0 || nc > (size_t)kPersistClasses) return LRH_OK;
+    int kmax = 2;
+    for (int k : p->class_k) { if (k > 4) return LRH_OK; kmax = std::max(kmax, k); }
+    int coop = 0, sms = 0, nb = 0;
+    LRH_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device));
+    LRH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (!coop) return LRH_OK;
+    LRH_CK(persistent_prepare(kmax, &nb));
+    if (nb <= 0) return LRH_OK;
+    PersistPlan L{};
+    int64_t tiles = 0;
+    for (size_t c = 0; c < nc; ++c) {
+        const int64_t per = persistent_tile_regions(p->class_k[c]);
+        L.cls[c] = p->class_list[c];
+        L.count[c] = p->class_count[c];
+        L.k[c] = p->class_k[c];
+        L.tile0[c] = tiles;
+        tiles += ((int64_t)p->n_inst * p->class_count[c] + per - 1) / per;
+    }
+    L.tiles = tiles;
+    L.n_classes = (int32_t)nc;
+    int rc;
+    if ((rc = p->dalloc(&L.bar, 2))) return rc;
+    LRH_CK(cudaMemset(L.bar, 0, 2 * sizeof(unsigned)));
+    p->plan = L;
+    p->persist_kmax = kmax;
+    p->persist_cap = (int64_t)nb * sms;
+    p->persist_grid = (int)std::min<int64_t>(tiles, p->persist_cap);
+    return LRH_OK;
+}
+
 // Alg. 2, n iterations as n region passes: pass 0 reads the canonical nu, zeta; pass j >= 1
 // first applies iteration j-1's pending update (owners write it to the other buffer:
 // odd j -> B, even j -> A) and writes its states to X (even j) or Y (odd j); then the
@@ -265,17 +360,7 @@ int enqueue_nesterov(lrh_problem* p, int n) {
         int rc = launch_all_classes(p, io);
         if (rc) return rc;
     }
-    PassIO fin{};
-    fin.rel = n - 1;
-    fin.nu_in = (n == 1) ? nuA : ((n - 1) % 2 == 1 ? nuB : nuA);
-    fin.zeta_in = (n == 1) ? zA : ((n - 1) % 2 == 1 ? zB : zA);
-    fin.rho_in = ((n - 1) % 2 == 0) ? rX : rY;
-    fin.tr_in = ((n - 1) % 2 == 0) ? tX : tY;
-    fin.nu_out = nuA;
-    fin.zeta_out = zA;
-    LRH_CK(launch_finalize(P, fin, p->stream));
-    LRH_CK(launch_advance(P, n, p->stream));
-    return LRH_OK;
+    return enqueue_nesterov_tail(p, n);
 }
 
 void drop_graphs(lrh_problem* p) {
@@ -287,7 +372,9 @@ void drop_graphs(lrh_problem* p) {
 
 int step_nesterov(lrh_problem* p, int n) {
     if (n <= 0) return LRH_OK;
-    if (!p->opt.use_graph || n < 2) return enqueue_nesterov(p, n);
+    const int mode = effective_loop(p);
+    if (mode == LRH_LOOP_PERSISTENT) return run_persistent(p, n);
+    if (mode == LRH_LOOP_EAGER || n < 2) return enqueue_nesterov(p, n);
     cudaGraphExec_t ge = nullptr;
     for (auto& g : p->nest_graphs) if (g.first == n) ge = g.second;
     if (!ge) {
@@ -332,6 +419,12 @@ int read_err(lrh_problem* p) {
     int32_t h = 0;
     LRH_CK(cudaMemcpyAsync(&h, p->P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
+    if (h & DEV_ERR_TIMEOUT) {
+        LRH_CK(cudaMemsetAsync(p->P.err, 0, sizeof(int32_t), p->stream));
+        LRH_CK(cudaStreamSynchronize(p->stream));
+        return fail(LRH_ETIMEOUT, "a grid barrier of the persistent iteration waited longer than its limit; "
+                                  "the launch stopped (messages are those of an unfinished step)");
+    }
     if (h & DEV_ERR_NUMERIC) return fail(LRH_ENUMERIC, "a non-finite eigenvalue, value or message was produced");
     return LRH_OK;
 }
@@ -647,6 +740,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         p->class_k = k2; p->class_count = c2; p->class_list = l2;
     }
     p->class_block.assign(p->class_k.size(), 128);
+    if ((rc = plan_persistent(p))) return rc;
     LRH_CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     for (size_t c = 1; c < p->class_k.size(); ++c) {
         cudaStream_t a;
@@ -694,6 +788,9 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
         info->class_block[c] = p->class_block[c];
     }
     info->concurrent_classes = p->concurrent ? 1 : 0;
+    info->loop = effective_loop(p);
+    info->persistent_grid = p->persist_grid;
+    info->persistent_tiles = p->persist_grid > 0 ? p->plan.tiles : 0;
     return LRH_OK;
 }
 
@@ -738,8 +835,14 @@ int lrh_step(lrh_problem* p, int32_t n_iters) {
         p->iteration += n_iters;
         return LRH_OK;
     }
+    const int mode = effective_loop(p);
+    if (mode == LRH_LOOP_PERSISTENT) {
+        if ((rc = run_persistent(p, n_iters))) return rc;
+        p->iteration += n_iters;
+        return LRH_OK;
+    }
     while (n_iters > 0) {
-        if (p->opt.use_graph && (p->iteration & 1) == 0 && n_iters >= kGraphChunk) {
+        if (mode == LRH_LOOP_GRAPH && (p->iteration & 1) == 0 && n_iters >= kGraphChunk) {
             if (!p->graph_exec && (rc = build_graph(p))) return rc;
             LRH_CK(cudaGraphLaunch(p->graph_exec, p->stream));
             p->iteration += kGraphChunk;
@@ -1072,6 +1175,66 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         }
         p->concurrent = conc != 0;
     }
+    if (p->persist_grid > 0) {
+        drop_graphs(p);   // the graph driver is timed with the shapes chosen above
+        std::string key = std::string("loop variant=") + (p->opt.variant == LRH_NESTEROV ? "nesterov" : "subgradient");
+        for (size_t c = 0; c < p->class_k.size(); ++c)
+            key += " k" + std::to_string(p->class_k[c]) + "=" + std::to_string((int64_t)p->class_count[c] * p->n_inst) +
+                   "/" + std::to_string(p->class_block[c]);
+        key += " sms=" + std::to_string(sms);
+        int choice = LRH_LOOP_GRAPH;
+        if (!cache_lookup(cache, key, &choice)) {
+            // iterate on a saved copy of the multipliers and iteration scalars, restored afterwards
+            const int64_t nm = p->n_inst * p->msg_elems;
+            const size_t b_msg = sizeof(float2) * (size_t)std::max<int64_t>(nm, 1);
+            const size_t b_inst = sizeof(double) * (size_t)p->n_inst;
+            struct Scratch {
+                void* ptr = nullptr;
+                ~Scratch() { if (ptr) cudaFree(ptr); }
+            } scratch;
+            LRH_CK(cudaStreamSynchronize(p->stream));
+            if (cudaMalloc(&scratch.ptr, 3 * b_msg + 2 * b_inst + sizeof(IterState) + 64) != cudaSuccess)
+                return fail(LRH_ENOMEM, "cudaMalloc of the autotuner's saved multipliers failed");
+            char* base = static_cast<char*>(scratch.ptr);
+            float2* s_nu = reinterpret_cast<float2*>(base);
+            float2* s_zeta = reinterpret_cast<float2*>(base + b_msg);
+            float2* s_best = reinterpret_cast<float2*>(base + 2 * b_msg);
+            double* s_q = reinterpret_cast<double*>(base + 3 * b_msg);
+            int32_t* s_flag = reinterpret_cast<int32_t*>(base + 3 * b_msg + b_inst);
+            IterState* s_st = reinterpret_cast<IterState*>(base + 3 * b_msg + 2 * b_inst);
+            int rc;
+            auto copy_all = [&](bool save) -> int {
+                auto cp = [&](void* a, void* b, size_t bytes) {
+                    return cudaMemcpyAsync(save ? a : b, save ? b : a, bytes, cudaMemcpyDeviceToDevice, p->stream);
+                };
+                LRH_CK(cp(s_nu, p->P.nu, sizeof(float2) * nm));
+                LRH_CK(cp(s_zeta, p->P.zeta, sizeof(float2) * nm));
+                LRH_CK(cp(s_best, p->P.nu_best, sizeof(float2) * nm));
+                LRH_CK(cp(s_q, p->P.q_best, sizeof(double) * p->n_inst));
+                LRH_CK(cp(s_flag, p->P.best_flag, sizeof(int32_t) * p->n_inst));
+                LRH_CK(cp(s_st, p->P.st, sizeof(IterState)));
+                return LRH_OK;
+            };
+            const int saved_loop = p->opt.loop;
+            const int64_t saved_it = p->iteration;
+            constexpr int kTuneIters = 16;
+            float ms[2] = {0.f, 0.f};
+            const int modes[2] = {LRH_LOOP_GRAPH, LRH_LOOP_PERSISTENT};
+            if ((rc = copy_all(true))) return rc;
+            for (int m = 0; m < 2; ++m) {
+                p->opt.loop = modes[m];
+                rc = time_ms(p, 3, [&]() { return lrh_step(p, kTuneIters); }, &ms[m]);
+                const int rc2 = copy_all(false);
+                p->iteration = saved_it;
+                if (rc || rc2) { p->opt.loop = saved_loop; return rc ? rc : rc2; }
+            }
+            p->opt.loop = saved_loop;
+            LRH_CK(cudaStreamSynchronize(p->stream));
+            choice = ms[1] < ms[0] ? LRH_LOOP_PERSISTENT : LRH_LOOP_GRAPH;
+            new_lines.push_back("{\"key\": \"" + key + "\", \"loop\": " + std::to_string(choice) + "}");
+        }
+        p->loop_auto = choice;
+    }
     if (cache_path && !new_lines.empty()) {
         FILE* f = std::fopen(cache_path, "a");
         if (!f) return fail(LRH_EINVAL, std::string("cannot write the autotune cache ") + cache_path);
@@ -1093,6 +1256,20 @@ int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
             return LRH_OK;
         }
     return fail(LRH_EINVAL, "no region class with " + std::to_string(k_sites) + " sites");
+}
+
+int lrh_selftest_barrier_timeout(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (p->persist_grid <= 0) return fail(LRH_EUNSUPPORTED, "this problem has no persistent launch");
+    DeviceGuard dg(p->device);
+    int rc = read_err(p);
+    if (rc) return rc;
+    PersistPlan L = p->plan;
+    L.n = 1;
+    L.nesterov = p->opt.variant == LRH_NESTEROV ? 1 : 0;
+    L.par0 = (int)(p->iteration & 1);
+    LRH_CK(launch_persistent(p->P, L, p->persist_kmax, p->persist_grid, p->stream, true));
+    return read_err(p);
 }
 
 int lrh_synchronize(lrh_problem* p) {

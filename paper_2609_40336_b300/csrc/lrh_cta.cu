@@ -1,17 +1,18 @@
 // CTA-level region pass for D = 64 and D = 128 (regions of 6 and 7 sites), sm_103a.
 //
-// One CTA owns one region.  theta is kept as a packed Hermitian upper triangle in shared
-// memory (D(D+1)/2 complex entries: 66 KB in FP32, 132 KB in FP64 at D = 128).  A sweep of
-// the cyclic two-sided Jacobi method runs D-1 rounds of the round-robin tournament; instead
-// of moving matrix entries, a slot -> index map (two small arrays in shared memory) is
-// rotated each round.  Every round:
+// One CTA owns one region.  theta lives in shared memory: in the FP32 pass as the upper triangle
+// of a row-padded D x (D+1) array with permuted indices, so that a warp's accesses fall on
+// distinct banks (130 KB at D = 128), in the FP64 certification as a packed upper triangle
+// (D(D+1)/2 complex entries: 132 KB at D = 128).  A sweep of the cyclic two-sided Jacobi
+// method runs D-1 rounds of the round-robin tournament; instead of moving matrix entries, a
+// slot -> index map (two small arrays in shared memory) is rotated each round.  Every round:
 //   1. D/2 threads compute the rotation (c, w) of the pair in slots (2k, 2k+1);
 //   2. the 2x2 blocks (k <= l) of the D/2 x D/2 block grid are updated in ONE pass,
 //      B' = J_k^H B J_l: the blocks partition the unordered index pairs, so no two threads
-//      touch the same packed entry and no second pass (row vs column) is needed;
+//      touch the same entry and no second pass (row vs column) is needed;
 //   3. V (in registers, 4 threads per row, columns in slot order) gets the column rotation
 //      and then the tournament's column permutation, which moves one complex value across
-//      each chunk boundary (two neighbour shuffles).
+//      each chunk boundary (two shuffles between the lanes holding neighbouring chunks).
 // The Gibbs / ground state rho = W W^dagger, W = V diag(sqrt p), is formed from W^T staged
 // in the same shared-memory buffer, with register tiles; then made exactly Hermitian, traced
 // onto the children and written out.  The FP64 certification kernel reuses the Jacobi part
@@ -85,6 +86,7 @@ struct Packed {
     using Real = T;
     C2* a;
     int D;
+    __device__ __forceinline__ int sig(int j) const { return j; }
     __device__ __forceinline__ C2 get(int i, int j) const {
         if (i <= j) return a[tri(i, j, D)];
         C2 v = a[tri(j, i, D)];
@@ -105,28 +107,46 @@ struct Packed {
     }
 };
 
-// Hermitian matrix in shared memory, both triangles stored row-major (FP32 pass): one
-// multiply-add per address; every write of an off-diagonal entry also writes its mirror.
+// Hermitian matrix in shared memory for the FP32 pass: the upper triangle of a D x (D+1)
+// row-padded array.  Logical index j is stored at position sig(j) = (j >> 1) + (j & 1) D/2 (rows
+// and columns alike) and the Jacobi slot map holds positions; entry (i, j) of positions lives
+// at (min, max), so its word address is congruent to 2 (i + j) modulo 32 banks whichever triangle
+// it belongs to.  The tournament's slots hold positions that step by 1 from one slot pair to the
+// next, so a warp's accesses fall on consecutive banks; no mirror writes are needed.
+// get/set/dget/dset take positions.
 template <typename T>
 struct Full {
     using C2 = typename V2<T>::t;
     using Real = T;
     C2* a;
     int D;
-    __device__ __forceinline__ C2 get(int i, int j) const { return a[i * D + j]; }
-    __device__ __forceinline__ void set(int i, int j, C2 v) const {
-        a[i * D + j] = v;
-        v.y = -v.y;
-        a[j * D + i] = v;
+    __device__ __forceinline__ int sig(int j) const { return (j >> 1) + (j & 1) * (D >> 1); }
+    __device__ __forceinline__ C2 get(int i, int j) const {
+        const bool up = i <= j;
+        C2 v = a[up ? i * (D + 1) + j : j * (D + 1) + i];
+        if (!up) v.y = -v.y;
+        return v;
     }
-    __device__ __forceinline__ C2 dget(int i) const { return a[i * (D + 1)]; }
-    __device__ __forceinline__ void dset(int i, C2 v) const { a[i * (D + 1)] = v; }
+    __device__ __forceinline__ void set(int i, int j, C2 v) const {
+        const bool up = i <= j;
+        if (!up) v.y = -v.y;
+        a[up ? i * (D + 1) + j : j * (D + 1) + i] = v;
+    }
+    __device__ __forceinline__ C2 dget(int i) const { return a[i * (D + 2)]; }
+    __device__ __forceinline__ void dset(int i, C2 v) const { a[i * (D + 2)] = v; }
+    // sums of |a_ij|^2 over the upper triangle (diagonal included) and over the diagonal
     template <int NT>
     __device__ __forceinline__ void sums(T& upper, T& diag) const {
-        upper = T(0); diag = T(0);
+        upper = T(0);
+        diag = T(0);
         for (int e = threadIdx.x; e < D * D; e += NT) {
             const int i = e / D, j = e - (e / D) * D;
-            if (i <= j) { const C2 v = a[e]; upper += v.x * v.x + v.y * v.y; if (i == j) diag += v.x * v.x; }
+            if (i <= j) {
+                const C2 v = a[i * (D + 1) + j];
+                const T m = v.x * v.x + v.y * v.y;
+                upper += m;
+                if (i == j) diag += m;
+            }
         }
     }
 };
@@ -156,6 +176,12 @@ __device__ __forceinline__ void two_sided(C2& b00, C2& b01, C2& b10, C2& b11, co
     rowmix(b01, b11);
 }
 
+// V rows in registers: a warp holds 8 rows x 4 column chunks, lane = 8 chunk + (row mod 8).
+// The 8 lanes of a quarter-warp share one chunk, so the rotation parameters they read are one
+// shared-memory address (a broadcast), and the neighbour chunk of the same row is 8 lanes away.
+__device__ __forceinline__ int vrow_of(int t) { return (t >> 5) * 8 + (t & 7); }
+__device__ __forceinline__ int vchunk_of(int t) { return (t >> 3) & 3; }
+
 template <int NT, typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
 #pragma unroll
@@ -180,7 +206,7 @@ struct CtaSmem {
     static constexpr int NT = CtaCfg<D>::NT;
     static constexpr size_t tri_elems = (size_t)D * (D + 1) / 2;
     // FP32 kernel also stages W^T and rho (D x D) in the same buffer
-    static constexpr size_t buf_bytes_f = ((sizeof(float2) * (size_t)D * D) + 15) / 16 * 16;
+    static constexpr size_t buf_bytes_f = ((sizeof(float2) * (size_t)D * (D + 1)) + 15) / 16 * 16;
     static constexpr size_t buf_bytes_d = ((sizeof(double2) * tri_elems) + 15) / 16 * 16;
     static constexpr size_t buf_bytes = sizeof(T) == 4 ? buf_bytes_f : buf_bytes_d;
     static constexpr size_t off_prm = buf_bytes;
@@ -200,11 +226,19 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
                           T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out) {
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
-    constexpr int NB = n * (n + 1) / 2;
+    // off-diagonal blocks (k < l) first, spread over all threads; the diagonal blocks (k = l,
+    // about half the work each) go to the threads left idle by the last off-diagonal iteration
+    constexpr int NOFF = n * (n - 1) / 2;
+    constexpr int ITER = (NOFF + NT - 1) / NT;
+    constexpr int IDLE = ITER * NT - NOFF;
+    constexpr int DGT = IDLE > 0 ? IDLE : NT;         // threads that take diagonal blocks
+    constexpr int DG0 = NT - DGT;                     // the first of them
+    constexpr int JD0 = IDLE > 0 ? ITER - 1 : ITER;   // their first iteration without an off-diagonal block
+    constexpr int NIT = JD0 + (n + DGT - 1) / DGT;
     constexpr int CH = 4;
     constexpr int W = D / CH;
     const int t = threadIdx.x;
-    const int chunk = t % CH;
+    const int chunk = vchunk_of(t);
     T up, dg;
     A.template sums<NT>(up, dg);
     const T norm2 = T(2) * block_sum<NT>(up, red) - block_sum<NT>(dg, red);
@@ -238,37 +272,44 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
                     pr = npr; pi = npi; qr = nqr; qi = nqi;
                 }
             }
-            for (int bidx = t; bidx < NB; bidx += NT) {
-                const int kl = tab[bidx];
-                const int kk = kl >> 8, ll = kl & 255;
-                const RotC<T> K = prm[kk];
-                const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
-                if (kk == ll) {
-                    auto b00 = A.dget(pk);
-                    auto b11 = A.dget(qk);
-                    auto b01 = A.get(pk, qk);
-                    auto b10 = b01; b10.y = -b10.y;
-                    b00.y = T(0); b11.y = T(0);
-                    two_sided<T>(b00, b01, b10, b11, K, K);
-                    b00.y = T(0); b11.y = T(0);
-                    A.dset(pk, b00);
-                    A.dset(qk, b11);
-                    auto z = b01; z.x = T(0); z.y = T(0);
-                    A.set(pk, qk, z);
-                } else {
-                    const RotC<T> Lr = prm[ll];
+#pragma unroll 1
+            for (int j = 0; j < NIT; ++j) {
+                const int v = t + NT * j;
+                if (v < NOFF) {
+                    const int kl = tab[v];
+                    const int kk = kl >> 8, ll = kl & 255;
+                    const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
                     const int pl = ix[2 * ll], ql = ix[2 * ll + 1];
                     auto b00 = A.get(pk, pl), b01 = A.get(pk, ql), b10 = A.get(qk, pl), b11 = A.get(qk, ql);
+                    const RotC<T> K = prm[kk];
+                    const RotC<T> Lr = prm[ll];
                     two_sided<T>(b00, b01, b10, b11, K, Lr);
                     A.set(pk, pl, b00); A.set(pk, ql, b01); A.set(qk, pl, b10); A.set(qk, ql, b11);
+                } else {
+                    const int kk = (t - DG0) + DGT * (j - JD0);
+                    if (t >= DG0 && kk < n) {
+                        const RotC<T> K = prm[kk];
+                        const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
+                        auto b00 = A.dget(pk);
+                        auto b11 = A.dget(qk);
+                        auto b01 = A.get(pk, qk);
+                        auto b10 = b01; b10.y = -b10.y;
+                        b00.y = T(0); b11.y = T(0);
+                        two_sided<T>(b00, b01, b10, b11, K, K);
+                        b00.y = T(0); b11.y = T(0);
+                        A.dset(pk, b00);
+                        A.dset(qk, b11);
+                        auto z = b01; z.x = T(0); z.y = T(0);
+                        A.set(pk, qk, z);
+                    }
                 }
             }
             if (WANT_V) {
                 // new[c] = old[rr_src(c)] over global slots; chunk boundaries move one value each way
-                const T flr = __shfl_up_sync(kFull, vr[W - 2], 1);
-                const T fli = __shfl_up_sync(kFull, vi[W - 2], 1);
-                const T frr = __shfl_down_sync(kFull, vr[1], 1);
-                const T fri = __shfl_down_sync(kFull, vi[1], 1);
+                const T flr = __shfl_up_sync(kFull, vr[W - 2], 8);
+                const T fli = __shfl_up_sync(kFull, vi[W - 2], 8);
+                const T frr = __shfl_down_sync(kFull, vr[1], 8);
+                const T fri = __shfl_down_sync(kFull, vi[1], 8);
                 T nr[W], ni[W];
                 nr[0] = chunk == 0 ? vr[0] : flr;
                 ni[0] = chunk == 0 ? vi[0] : fli;
@@ -334,7 +375,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
 }
 
 // FP32 pass version: message entries from pass_entry (pending Alg. 2 update applied); the
-// region owns its parent messages and also stores the conjugate (lower-triangle) entries.
+// region owns its parent messages and also stores their conjugate (lower-triangle) entries.
 template <int D>
 __device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Full<float> A, const PassIO& io,
                                    const dev::Thetas& T) {
@@ -370,17 +411,18 @@ __device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int
             re += m.x; im += m.y;
         }
         if (i == j) im = 0.f;
-        A.set(i, j, make_float2(re, im));
+        A.set(A.sig(i), A.sig(j), make_float2(re, im));
     }
 }
 
+// off-diagonal block pairs (k < l) in row order
 template <int D, typename T>
 __device__ void build_table(unsigned short* tab) {
     constexpr int n = D / 2;
     const int t = threadIdx.x;
     if (t < n) {
-        const int off = t * n - ((t * (t - 1)) >> 1);
-        for (int l = t; l < n; ++l) tab[off + (l - t)] = (unsigned short)((t << 8) | l);
+        const int off = t * (n - 1) - ((t * (t - 1)) >> 1);
+        for (int l = t + 1; l < n; ++l) tab[off + (l - t - 1)] = (unsigned short)((t << 8) | l);
     }
 }
 
@@ -409,18 +451,18 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     const dev::Thetas Th = dev::pass_thetas(P, io);
     if (io.writer && blockIdx.x == 0 && t == 0) dev::advance_theta(P, io);
     build_table<D, float>(tab);
-    if (t < D) idx0[t] = t;
     Full<float> A{buf, D};
+    if (t < D) idx0[t] = A.sig(t);
     assemble_packed_io<D>(P, R, inst, A, io, Th);
     __syncthreads();
-    const int row = t / 4, chunk = t % 4;
+    const int row = vrow_of(t), chunk = vchunk_of(t);
     float vr[W], vi[W];
 #pragma unroll
     for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
     float norm2;
     const int sweeps = jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2);
     // the slot maps are back to the identity after whole sweeps: diag = eigenvalues
-    if (t < D) lam[t] = buf[t * (D + 1)].x;
+    if (t < D) lam[t] = A.dget(A.sig(t)).x;
     __syncthreads();
     float lmin = lam[0];
     for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
@@ -528,8 +570,8 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
     const int r = cls[blockIdx.x % count];
     const RegionInfo R = P.reg[r];
     build_table<D, double>(tab);
-    if (t < D) idx0[t] = t;
     Packed<double> A{buf, D};
+    if (t < D) idx0[t] = A.sig(t);
     assemble_packed<D, double>(P, R, inst, A, msg, nullptr, 0.0f, true);
     __syncthreads();
     double vr[W], vi[W];

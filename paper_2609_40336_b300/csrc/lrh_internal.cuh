@@ -73,7 +73,7 @@ struct PassIO {
 };
 
 // Error bits raised by kernels.
-enum : int32_t { DEV_ERR_NUMERIC = 1 };
+enum : int32_t { DEV_ERR_NUMERIC = 1, DEV_ERR_TIMEOUT = 2 };
 
 struct DevProblem {
     int32_t n_inst;
@@ -158,5 +158,30 @@ cudaError_t launch_vjp_outputs(const DevProblem& P, float2* nu_bar, float2* term
 
 // update modes
 enum : int { UPD_STEP = 0, UPD_GRAD_ONLY = 1 };
+
+// Persistent iteration (lrh_kernels.cu): one cooperative launch for n iterations over up to
+// kPersistClasses size classes with k <= 4 (kmax = the largest k, at least 2).  Tiles of class
+// c are [tile0[c], tile0[c + 1]); a tile holds persistent_tile_regions(k) regions.
+constexpr int kPersistClasses = 4;
+struct PersistPlan {
+    const int32_t* cls[kPersistClasses];
+    int32_t count[kPersistClasses];
+    int32_t k[kPersistClasses];
+    int64_t tile0[kPersistClasses];
+    int64_t tiles;
+    int32_t n_classes;
+    int32_t n;            // iterations
+    int32_t nesterov;     // 1: fused Alg. 2 passes; 0: Alg. 1 iterations
+    int32_t par0;         // Alg. 1: parity of the first iteration
+    unsigned* bar;        // device arrival counter of the grid barrier (zeroed by launch_persistent)
+    unsigned expect;      // arrivals per barrier (the grid; set by launch_persistent)
+};
+int persistent_tile_regions(int k);
+cudaError_t persistent_prepare(int kmax, int* blocks_per_sm);
+// unreleased = true (self-test of the bounded wait): every barrier expects one CTA more than the
+// grid, so the first barrier never opens and every CTA returns after its wait limit with
+// DEV_ERR_TIMEOUT.
+cudaError_t launch_persistent(const DevProblem& P, const PersistPlan& L, int kmax, int grid, cudaStream_t s,
+                              bool unreleased = false);
 
 }  // namespace lrh

@@ -49,7 +49,7 @@ template <int D> struct RegCap { static constexpr int v = D == 32 ? 232 : (D == 
 // FP32 region pass for 4 <= D <= 32; BLOCK threads = BLOCK / D regions per CTA (autotuned).
 template <int D, int BLOCK>
 __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const PassIO& io, const int32_t* __restrict__ cls,
-                                                 const int32_t count, const int k) {
+                                                 const int32_t count, const int k, const int64_t tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int G = BLOCK / D;
     const int g = threadIdx.x / D;
@@ -63,14 +63,13 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
     __shared__ unsigned long long blk_sweeps;
     if (threadIdx.x == 0) blk_sweeps = 0ull;
 
-    const int64_t unit = (int64_t)blockIdx.x * G + g;
+    const int64_t unit = tile * G + g;
     const bool valid = unit < (int64_t)P.n_inst * count;
     const int inst = valid ? (int)(unit / count) : 0;
     const int r = valid ? cls[unit % count] : 0;
     const bool nest = P.st->variant == 1;
     const int max_sweeps = P.st->max_sweeps;
     const Thetas T = pass_thetas(P, io);
-    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
 
     float ar[D], ai[D], vr[D], vi[D];
     RegionInfo R;
@@ -194,7 +193,8 @@ template <int D, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) __maxnreg__(RegCap<D>::v) region_pass_kernel(const DevProblem P, const PassIO io,
                                                                                        const int32_t* __restrict__ cls,
                                                                                        const int32_t count, const int k) {
-    region_pass_impl<D, BLOCK>(P, io, cls, count, k);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+    region_pass_impl<D, BLOCK>(P, io, cls, count, k, blockIdx.x);
 }
 
 // D = 32 keeps ptxas's own register heuristic (explicit caps made it spill).
@@ -202,18 +202,16 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) region_pass_kernel32(const DevProblem P, const PassIO io,
                                                               const int32_t* __restrict__ cls, const int32_t count,
                                                               const int k) {
-    region_pass_impl<32, BLOCK>(P, io, cls, count, k);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+    region_pass_impl<32, BLOCK>(P, io, cls, count, k, blockIdx.x);
 }
 
 // D = 2 closed form, one thread per region.  theta = m I + K, K = [[hh, b], [conj(b), -hh]],
 // K^2 = r^2 I with r = sqrt(hh^2 + |b|^2): lambda = m -+ r,
 // Gibbs state (1/2)(I - tanh(beta r) K / r), F_beta = m - r - log(1 + e^{-2 beta r}) / beta,
 // ground projector (1/2)(I - K / r), or I/2 when 2r is within the degeneracy tolerance.
-__global__ void __launch_bounds__(256) region_pass_d2_kernel(const DevProblem P, const PassIO io,
-                                                            const int32_t* __restrict__ cls, const int32_t count) {
-    const Thetas T = pass_thetas(P, io);
-    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
-    const int64_t unit = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void region_d2_unit(const DevProblem& P, const PassIO& io, const Thetas& T,
+                                               const int32_t* __restrict__ cls, const int32_t count, const int64_t unit) {
     if (unit >= (int64_t)P.n_inst * count) return;
     const int inst = (int)(unit / count);
     const int r = cls[unit % count];
@@ -255,6 +253,13 @@ __global__ void __launch_bounds__(256) region_pass_d2_kernel(const DevProblem P,
     }
     P.val[(int64_t)inst * P.n_regions + r] = (double)F;
     if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+}
+
+__global__ void __launch_bounds__(256) region_pass_d2_kernel(const DevProblem P, const PassIO io,
+                                                            const int32_t* __restrict__ cls, const int32_t count) {
+    const Thetas T = pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+    region_d2_unit(P, io, T, cls, count, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // 4 x 4 regions, one thread per region: the whole cyclic Jacobi runs in registers with
@@ -523,9 +528,8 @@ __global__ void certify_d2_kernel(const DevProblem P, const int32_t* __restrict_
 // complex entries of one instance's message array (every block holds D_f^2 >= 4 entries, so
 // the two never straddle pairs): g = rho_f - Tr_{e\f} rho_e; nu += alpha_t g, with nu_best
 // copied first when the previous pass set a new best q.
-__global__ void update_kernel(const DevProblem P, const int par, const int mode) {
+__device__ __forceinline__ void update_elem(const DevProblem& P, const int par, const int mode, const int64_t tid) {
     const int64_t halfm = P.msg_elems >> 1;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double td = P.st->t[par];
     if (tid == 0 && mode == UPD_STEP) P.st->t[par ^ 1] = td + 1.0;
     if (tid >= (int64_t)P.n_inst * halfm) return;
@@ -547,6 +551,10 @@ __global__ void update_kernel(const DevProblem P, const int par, const int mode)
     nv.z = fmaf(alpha, gv.z, nv.z); nv.w = fmaf(alpha, gv.w, nv.w);
     if (!(isfinite(nv.x) && isfinite(nv.y) && isfinite(nv.z) && isfinite(nv.w))) atomicOr(P.err, DEV_ERR_NUMERIC);
     *reinterpret_cast<float4*>(P.nu + mi) = nv;
+}
+
+__global__ void update_kernel(const DevProblem P, const int par, const int mode) {
+    update_elem(P, par, mode, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Alg. 2: the pending update of iteration t = t0 + io.rel (its states in io.rho_in / tr_in, its
@@ -579,17 +587,21 @@ __global__ void advance_kernel(IterState* st, int n) { st->t0 += n; }
 // Deterministic per-instance FP64 sum of per-region values (fixed strided partial sums and a
 // fixed tree), with optional Alg. 1 best-so-far tracking.
 constexpr int kReduce = 256;
-__global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, const double* __restrict__ vals,
-                                                        const int track_best) {
-    __shared__ double sh[kReduce];
-    const int inst = blockIdx.x;
+// kReduce fixed strided partial sums and a fixed tree, computed by NT <= kReduce threads (each
+// thread takes the partial-sum slots vt = threadIdx.x + NT j): the same additions in the same
+// order for any NT.  The caller synchronises before reusing sh.
+template <int NT>
+__device__ __forceinline__ void reduce_instance(const DevProblem& P, const double* __restrict__ vals, const int track_best,
+                                                const int inst, double* sh) {
     const double* v = vals + (int64_t)inst * P.n_regions;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < P.n_regions; i += kReduce) acc += v[i];
-    sh[threadIdx.x] = acc;
+    for (int vt = threadIdx.x; vt < kReduce; vt += NT) {
+        double acc = 0.0;
+        for (int i = vt; i < P.n_regions; i += kReduce) acc += v[i];
+        sh[vt] = acc;
+    }
     __syncthreads();
     for (int w = kReduce / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        for (int vt = threadIdx.x; vt < w; vt += NT) sh[vt] += sh[vt + w];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -601,6 +613,12 @@ __global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, con
             if (better) P.q_best[inst] = q;
         }
     }
+}
+
+__global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, const double* __restrict__ vals,
+                                                        const int track_best) {
+    __shared__ double sh[kReduce];
+    reduce_instance<kReduce>(P, vals, track_best, blockIdx.x, sh);
 }
 
 __global__ void set_state_kernel(IterState* st, int par, double theta, double t, int set_theta_t, double beta,
@@ -619,6 +637,165 @@ __global__ void set_state_kernel(IterState* st, int par, double theta, double t,
     st->variant = variant;
     st->step_rule = step_rule;
     st->max_sweeps = max_sweeps;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent iteration: one cooperative launch (every block resident) runs n iterations over
+// all size classes k <= KMAX, with a grid-wide barrier where the graph path has a launch
+// boundary.  Per pass, the tiles of all classes (kBlock / D regions of one class per tile;
+// kBlock regions for D = 2) are dealt to the blocks round-robin; the per-region code is the
+// same as in the per-class kernels, so the results are bit-identical to the graph path.
+//   Alg. 2: n fused passes (the PassIO sequence of the graph path), one barrier after each;
+//           the caller finalises the last pending update.
+//   Alg. 1: pass, barrier, per-instance reduction with best tracking, barrier, message update,
+//           barrier.
+// ---------------------------------------------------------------------------------------------
+constexpr unsigned long long kBarrierLimitNs = 1000000000ull;   // one second per wait
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Grid-wide barrier on one monotonic arrival counter (zeroed before the launch): a CTA adds 1
+// with release semantics and waits, with acquire loads, until the counter reaches the end of
+// its group of `expect` arrivals.  No reset and no second word, so the last arrival needs no
+// extra round trip.  A wait longer than kBarrierLimitNs, or one that sees another CTA's timeout
+// (checked every 256 polls), raises DEV_ERR_TIMEOUT and returns false; the caller then returns.
+__device__ __forceinline__ bool grid_sync(int32_t* err, unsigned* bar, unsigned expect) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned old = atom_add_release(bar, 1u);
+        const unsigned target = (old / expect + 1u) * expect;
+        const unsigned long long t0 = global_ns();
+        for (unsigned poll = 1; (int)(ld_acquire_u32(bar) - target) < 0; ++poll) {
+            if ((poll & 255u) == 0 &&
+                ((ld_acquire_u32(reinterpret_cast<const unsigned*>(err)) & DEV_ERR_TIMEOUT) ||
+                 global_ns() - t0 > kBarrierLimitNs)) {
+                atomicOr(err, DEV_ERR_TIMEOUT);
+                good = 0;
+                break;
+            }
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// PassIO of fused pass j of an n-pass Alg. 2 step: buffers A (nu, zeta), B (nu_b, zeta_b),
+// X (rho, tr), Y (rho_b, tr_b); pass j reads A when j is 0 or odd, else B, applies the pending
+// update of pass j - 1 (states from X when j is odd, Y when even) into B (odd j) or A (even j),
+// and writes its states to X (even j) or Y (odd j).
+__device__ __forceinline__ PassIO nesterov_io(const DevProblem& P, const int j) {
+    PassIO io{};
+    io.rel = j;
+    io.writer = 1;
+    io.pending = j > 0;
+    const bool odd = (j & 1) != 0;
+    io.nu_in = (odd || j == 0) ? P.nu : P.nu_b;
+    io.zeta_in = (odd || j == 0) ? P.zeta : P.zeta_b;
+    if (j > 0) {
+        io.rho_in = odd ? P.rho : P.rho_b;
+        io.tr_in = odd ? P.tr : P.tr_b;
+        io.nu_out = odd ? P.nu_b : P.nu;
+        io.zeta_out = odd ? P.zeta_b : P.zeta;
+    }
+    io.rho_out = odd ? P.rho_b : P.rho;
+    io.tr_out = odd ? P.tr_b : P.tr;
+    return io;
+}
+
+// Register budget of the persistent kernel (its tile loop keeps the pass's PassIO and the plan
+// live around the per-region code): no spills up to k = 3; a small one at k = 4.
+template <int KMAX> struct PersistCap { static constexpr int v = KMAX == 2 ? 96 : (KMAX == 3 ? 128 : 168); };
+
+template <int KMAX>
+__global__ void __launch_bounds__(kBlock) __maxnreg__(PersistCap<KMAX>::v)
+    persist_kernel(const DevProblem P, const PersistPlan L) {
+    __shared__ double red[kReduce];
+    for (int j = 0; j < L.n; ++j) {
+        PassIO io{};
+        if (L.nesterov) {
+            io = nesterov_io(P, j);
+            if (blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+        } else {
+            io.nu_in = P.nu;
+            io.rho_out = P.rho;
+            io.tr_out = P.tr;
+        }
+        const Thetas T = pass_thetas(P, io);
+        for (int64_t tile = blockIdx.x; tile < L.tiles; tile += gridDim.x) {
+            // class of this tile, with compile-time indices into the plan (no local copy of it)
+            int k = L.k[0];
+            const int32_t* cls = L.cls[0];
+            int32_t count = L.count[0];
+            int64_t first = L.tile0[0];
+#pragma unroll
+            for (int q = 1; q < kPersistClasses; ++q)
+                if (q < L.n_classes && tile >= L.tile0[q]) { k = L.k[q]; cls = L.cls[q]; count = L.count[q]; first = L.tile0[q]; }
+            const int64_t lt = tile - first;
+            if (k == 1) {
+                region_d2_unit(P, io, T, cls, count, lt * kBlock + threadIdx.x);
+            } else if (k == 2) {
+                region_pass_impl<4, kBlock>(P, io, cls, count, 2, lt);
+            } else if (k == 3) {
+                if constexpr (KMAX >= 3) region_pass_impl<8, kBlock>(P, io, cls, count, 3, lt);
+            } else {
+                if constexpr (KMAX >= 4) region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
+            }
+        }
+        if (!grid_sync(P.err, L.bar, L.expect)) return;
+        if (!L.nesterov) {
+            const int par = (L.par0 + j) & 1;
+            for (int inst = blockIdx.x; inst < P.n_inst; inst += gridDim.x) {
+                reduce_instance<kBlock>(P, P.val, 1, inst, red);
+                __syncthreads();
+            }
+            if (!grid_sync(P.err, L.bar, L.expect)) return;
+            int64_t nel = (int64_t)P.n_inst * (P.msg_elems >> 1);
+            if (nel < 1) nel = 1;   // element 0 also advances the iteration counter
+            for (int64_t tid = (int64_t)blockIdx.x * kBlock + threadIdx.x; tid < nel; tid += (int64_t)gridDim.x * kBlock)
+                update_elem(P, par, UPD_STEP, tid);
+            if (!grid_sync(P.err, L.bar, L.expect)) return;
+        }
+    }
+}
+
+template <int KMAX>
+size_t persist_smem() {
+    constexpr int D = 1 << KMAX;
+    return PassSmem<(D < 4 ? 4 : D), kBlock>::bytes;
+}
+
+template <int KMAX>
+cudaError_t persist_prepare(int* blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(persist_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)persist_smem<KMAX>());
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persist_kernel<KMAX>, kBlock, persist_smem<KMAX>());
+}
+
+template <int KMAX>
+cudaError_t persist_launch(const DevProblem& P, const PersistPlan& L, int grid, cudaStream_t s) {
+    void* args[] = {const_cast<DevProblem*>(&P), const_cast<PersistPlan*>(&L)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(persist_kernel<KMAX>), dim3(grid), dim3(kBlock), args,
+                                       persist_smem<KMAX>(), s);
 }
 
 template <int D, int BLOCK>
@@ -749,6 +926,32 @@ cudaError_t launch_finalize(const DevProblem& P, const PassIO& io, cudaStream_t 
 cudaError_t launch_advance(const DevProblem& P, int n, cudaStream_t s) {
     advance_kernel<<<1, 1, 0, s>>>(P.st, n);
     return cudaGetLastError();
+}
+
+int persistent_tile_regions(int k) { return k == 1 ? kBlock : kBlock >> k; }
+
+cudaError_t persistent_prepare(int kmax, int* blocks_per_sm) {
+    switch (kmax) {
+        case 2: return persist_prepare<2>(blocks_per_sm);
+        case 3: return persist_prepare<3>(blocks_per_sm);
+        case 4: return persist_prepare<4>(blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_persistent(const DevProblem& P, const PersistPlan& Lin, int kmax, int grid, cudaStream_t s,
+                              bool unreleased) {
+    PersistPlan L = Lin;
+    // self-test: a barrier that expects one CTA more than the grid never opens
+    L.expect = (unsigned)grid + (unreleased ? 1u : 0u);
+    cudaError_t e = cudaMemsetAsync(L.bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    switch (kmax) {
+        case 2: return persist_launch<2>(P, L, grid, s);
+        case 3: return persist_launch<3>(P, L, grid, s);
+        case 4: return persist_launch<4>(P, L, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_best, cudaStream_t s) {

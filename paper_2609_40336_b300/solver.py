@@ -67,22 +67,38 @@ def _current_stream():
     return C.c_void_p(0)
 
 
+_LOOPS = {"eager": 0, "graph": 1, "persistent": 2, "auto": 3}
+_LOOP_NAMES = {v: k for k, v in _LOOPS.items()}
+
+
+def _loop_code(loop: str, use_graph: Optional[bool]) -> int:
+    """Iteration driver code (lrh_options.loop); use_graph True / False means graph / eager."""
+    if use_graph is not None:
+        return _LOOPS["graph"] if use_graph else _LOOPS["eager"]
+    if loop not in _LOOPS:
+        raise ValueError(f"unknown loop driver {loop!r}")
+    return _LOOPS[loop]
+
+
 class Solver:
     """One (batched) relaxation problem on the GPU.
 
     ``problem`` is any object with ``n_sites``, ``regions``, ``term_sites`` and
-    ``term_mats`` (see include/lrh.h for the conventions).
+    ``term_mats`` (see include/lrh.h for the conventions).  ``loop`` selects the iteration
+    driver of ``step``: "eager" (kernel launches), "graph" (captured CUDA graph), "persistent"
+    (one cooperative launch per call, classes of <= 4 sites) or "auto" (the autotuner's choice);
+    ``use_graph`` True / False is shorthand for "graph" / "eager".
     """
 
     def __init__(self, problem, variant: str = "nesterov", beta: float = 1.0, lhat: Optional[float] = None,
                  alpha: float = 1.0, step_rule: str = "inv_sqrt", degen_tol: float = 1e-5,
-                 max_sweeps: int = 15, use_graph: bool = True, stream=None):
+                 max_sweeps: int = 15, use_graph: Optional[bool] = None, loop: str = "auto", stream=None):
         self._lib = L.load()
         self._h = C.c_void_p(0)
         desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats)
         self._opt = L.Options(variant=_VARIANTS[variant], step_rule=_RULES[step_rule], alpha=float(alpha),
                               beta=float(beta), lhat=float(lhat) if lhat else 0.0, degen_tol=float(degen_tol),
-                              max_sweeps=int(max_sweeps), use_graph=int(bool(use_graph)))
+                              max_sweeps=int(max_sweeps), loop=_loop_code(loop, use_graph))
         st = _current_stream() if stream is None else C.c_void_p(int(stream))
         L.check(self._lib.lrh_create(C.byref(desc), C.byref(self._opt), st, C.byref(self._h)), "lrh_create")
         inf = self.info()
@@ -121,7 +137,8 @@ class Solver:
                     lambda_G=inf.lambda_G, gamma_G=inf.gamma_G, iteration=inf.iteration,
                     class_sites=list(inf.class_sites[:nc]), class_regions=list(inf.class_regions[:nc]),
                     sweeps=[int(x) for x in inf.sweeps[:nc]], class_block=list(inf.class_block[:nc]),
-                    concurrent_classes=bool(inf.concurrent_classes))
+                    concurrent_classes=bool(inf.concurrent_classes), loop=_LOOP_NAMES[inf.loop],
+                    persistent_grid=inf.persistent_grid, persistent_tiles=inf.persistent_tiles)
 
     def pairs(self):
         par = np.zeros(self.n_pairs, np.int32)
@@ -140,7 +157,8 @@ class Solver:
         for k in ("alpha", "beta", "degen_tol"):
             if k in kw: setattr(o, k, float(kw.pop(k)))
         if "max_sweeps" in kw: o.max_sweeps = int(kw.pop("max_sweeps"))
-        if "use_graph" in kw: o.use_graph = int(bool(kw.pop("use_graph")))
+        if "use_graph" in kw: o.loop = _loop_code("auto", kw.pop("use_graph"))
+        if "loop" in kw: o.loop = _loop_code(kw.pop("loop"), None)
         if kw:
             raise TypeError(f"unknown options {sorted(kw)}")
         L.check(self._lib.lrh_set_options(self._h, C.byref(o)), "lrh_set_options")
@@ -151,7 +169,7 @@ class Solver:
         L.check(self._lib.lrh_autotune(self._h, path, 1 if force else 0), "lrh_autotune")
         inf = self.info()
         return dict(class_sites=inf["class_sites"], class_block=inf["class_block"],
-                    concurrent_classes=inf["concurrent_classes"])
+                    concurrent_classes=inf["concurrent_classes"], loop=inf["loop"])
 
     def set_launch_shape(self, k_sites: int, block: int) -> None:
         L.check(self._lib.lrh_set_launch_shape(self._h, int(k_sites), int(block)), "lrh_set_launch_shape")
@@ -168,6 +186,14 @@ class Solver:
     def launch_region_pass(self, k_sites: int) -> None:
         """Region pass of one size class only (no update); used to time the dominant kernel."""
         L.check(self._lib.lrh_launch_region_pass(self._h, int(k_sites)), "lrh_launch_region_pass")
+
+    def selftest_barrier_timeout(self) -> int:
+        """Run the persistent driver's bounded-wait self-test (see lrh_selftest_barrier_timeout);
+        returns LRH_ETIMEOUT (-6) when the never-released barrier timed out as designed."""
+        rc = self._lib.lrh_selftest_barrier_timeout(self._h)
+        if rc not in (0, -6):
+            L.check(rc, "lrh_selftest_barrier_timeout")
+        return rc
 
     def synchronize(self) -> None:
         L.check(self._lib.lrh_synchronize(self._h), "lrh_synchronize")
