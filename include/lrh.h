@@ -81,6 +81,10 @@ extern "C" {
 #define LRH_LOOP_PERSISTENT 2  /* one cooperative launch for all iterations of an lrh_step    */
 #define LRH_LOOP_AUTO       3  /* chosen by lrh_autotune (graph or persistent)                */
 
+#define LRH_SHAPE_CTA_FP32   1  /* lrh_set_launch_shape, classes of 6-7 sites: rho = W W^dagger on the FP32 cores */
+#define LRH_SHAPE_CTA_TENSOR 2  /* ... on the tensor cores (tcgen05, three TF32 products per term, FP32
+                                   accumulate); 7-site (128 x 128) regions only */
+
 #define LRH_MSG_NU        0    /* current multipliers nu                                  */
 #define LRH_MSG_ZETA      1    /* Nesterov auxiliary sequence zeta                        */
 #define LRH_MSG_NU_BEST   2    /* subgradient: nu at the best q seen so far               */
@@ -121,8 +125,7 @@ typedef struct {
                              LRH_LOOP_PERSISTENT (one cooperative launch running all the
                              iterations, grid-wide barriers between passes; problems whose
                              classes all have <= 4 sites, else GRAPH), LRH_LOOP_AUTO (the
-                             choice of lrh_autotune; before it: PERSISTENT when the problem
-                             fits one wave of resident CTAs, else GRAPH).  All drivers give
+                             choice of lrh_autotune; GRAPH before it).  All drivers give
                              bit-identical messages for the same launch shapes; the
                              persistent one runs every class in the lane layout.             */
 } lrh_options;
@@ -144,8 +147,10 @@ typedef struct {
     int32_t class_regions[8];     /* regions per instance of each class                        */
     uint64_t sweeps[8];           /* cumulative FP32 Jacobi sweeps x regions, per class        */
     int32_t class_block[8];       /* threads per CTA of each class's region pass (autotuned);
-                                     negative: one thread per region (4 x 4 regions)            */
-    int32_t concurrent_classes;   /* 1: region classes run on forked streams within an iteration */
+                                     negative: one thread per region (4 x 4 regions); classes of
+                                     6-7 sites: LRH_SHAPE_CTA_FP32 / LRH_SHAPE_CTA_TENSOR        */
+    int32_t concurrent_classes;   /* region classes of one pass: 0 one after another, 1 on forked
+                                     streams, 2 in one launch (classes of <= 4 sites; autotuned) */
     int32_t loop;                 /* driver lrh_step uses now (LRH_LOOP_EAGER/GRAPH/PERSISTENT)  */
     int32_t persistent_grid;      /* CTAs of the persistent launch (0: not available)             */
     int64_t persistent_tiles;     /* region tiles per pass in the persistent launch               */
@@ -232,7 +237,8 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
 
 /* Autotuner.  Times, on this problem's own data and stream, the launch shapes of every region
  * class with at most 5 sites (64, 128 or 256 threads per CTA, i.e. 64/D .. 256/D regions per
- * CTA), whether the classes of one iteration run concurrently on forked streams, and, when
+ * CTA), whether the classes of one pass run one after another, on forked streams or in one
+ * launch, and, when
  * the problem allows a persistent launch, the graph against the persistent iteration driver
  * (used when lrh_options.loop is LRH_LOOP_AUTO); then keeps the fastest.  Choices are read
  * from / appended to `cache_path` (JSON lines keyed by class size, region count and SM count;
@@ -244,8 +250,16 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
 /* Set the launch shape of one region class by hand (what lrh_autotune chooses): 64, 128 or
  * 256 threads per CTA with 2^k_sites lanes per region, or for 4 x 4 regions -64, -128, -256 for
  * one thread per region.  The lane layouts give bit-identical results; the one-thread layout
- * rotates in another order and agrees to rounding. */
+ * rotates in another order and agrees to rounding.  For classes of 6 or 7 sites (one CTA per
+ * region) the shape selects the back-transform: LRH_SHAPE_CTA_FP32, or for 7 sites also
+ * LRH_SHAPE_CTA_TENSOR (results agree to FP32 rounding). */
 int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block);
+
+/* How the region classes of one pass are launched (what lrh_autotune chooses): 0 one class
+ * after another on the problem's stream, 1 on forked streams (the default), 2 all classes in
+ * one launch (problems whose classes all have <= 4 sites; LRH_EUNSUPPORTED otherwise).  All
+ * three give bit-identical results for lane launch shapes. */
+int lrh_set_class_mode(lrh_problem* p, int32_t mode);
 
 /* Self-test of the bounded grid-barrier wait of the persistent driver: one persistent launch
  * whose first barrier is never released (it waits for one CTA more than the grid), so every CTA gives

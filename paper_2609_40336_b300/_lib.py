@@ -93,6 +93,7 @@ SIGNATURES = {
     "lrh_get_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrh_set_messages": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]),
     "lrh_selftest_barrier_timeout": (C.c_int, [C.c_void_p]),
+    "lrh_set_class_mode": (C.c_int, [C.c_void_p, C.c_int32]),
     "lrh_synchronize": (C.c_int, [C.c_void_p]),
     "lrh_set_terms": (C.c_int, [C.c_void_p, C.c_void_p]),
     "lrh_autotune": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int32]),

@@ -100,6 +100,7 @@ struct lrh_problem {
     // chosen by lrh_autotune (defaults: 128 threads, concurrent classes)
     std::vector<int> class_block;
     bool concurrent = true;
+    bool fused = false;   // all classes (<= 4 sites) in one launch per pass (autotuned)
     // persistent driver: plan of the cooperative launch (classes with k <= 4 only), its grid,
     // the resident-CTA capacity and the autotuned driver for LRH_LOOP_AUTO (-1: not tuned)
     PersistPlan plan{};
@@ -221,11 +222,16 @@ PassIO plain_io(const lrh_problem* p) {
     return io;
 }
 
-// Region pass of every size class: class 0 on the problem's stream, the others on forked
-// streams (independent work: disjoint outputs, read-only inputs; in a pending pass every
-// updated message has exactly one owner), joined afterwards.  Only class 0 may be `writer`.
+// Region pass of every size class: one launch for all classes (when chosen and possible), or
+// class 0 on the problem's stream and the others on forked streams (independent work: disjoint
+// outputs, read-only inputs; in a pending pass every updated message has exactly one owner),
+// joined afterwards.  Only class 0 may be `writer`.
 int launch_all_classes(lrh_problem* p, const PassIO& io0) {
     const size_t nc = p->class_k.size();
+    if (p->fused && p->persist_grid > 0) {
+        LRH_CK(launch_class_pass(p->P, p->plan, p->persist_kmax, io0, p->stream));
+        return LRH_OK;
+    }
     PassIO io = io0;
     io.writer = 0;
     if (!p->concurrent || nc < 2) {
@@ -267,9 +273,7 @@ int enqueue_nesterov_tail(lrh_problem* p, int n) {
 // Driver lrh_step uses now (LRH_LOOP_EAGER / GRAPH / PERSISTENT).
 int effective_loop(const lrh_problem* p) {
     int m = p->opt.loop;
-    if (m == LRH_LOOP_AUTO)
-        m = p->loop_auto >= 0 ? p->loop_auto
-                              : ((p->persist_grid > 0 && p->plan.tiles <= p->persist_cap) ? LRH_LOOP_PERSISTENT : LRH_LOOP_GRAPH);
+    if (m == LRH_LOOP_AUTO) m = p->loop_auto >= 0 ? p->loop_auto : LRH_LOOP_GRAPH;
     if (m == LRH_LOOP_PERSISTENT && p->persist_grid <= 0) m = LRH_LOOP_GRAPH;
     return m;
 }
@@ -715,6 +719,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         LRH_CK(cudaMemcpy(P.q_best, ninf.data(), sizeof(double) * NI, cudaMemcpyHostToDevice));
     }
     // size classes
+    for (int k = 0; k < 8; ++k) P.class_base[k] = -1;
     for (int k = 1; k <= kMaxSites; ++k) {
         std::vector<int32_t> lst;
         for (int e = 0; e < R; ++e) if ((int)regs[e].size() == k) lst.push_back(e);
@@ -725,6 +730,9 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         p->class_k.push_back(k);
         p->class_count.push_back((int32_t)lst.size());
         p->class_list.push_back(dl);
+        bool contiguous = true;
+        for (size_t i = 1; i < lst.size(); ++i) contiguous = contiguous && lst[i] == lst[0] + (int32_t)i;
+        P.class_base[k] = contiguous ? lst[0] : -1;
     }
     // most expensive class first (it stays on the problem's stream)
     {
@@ -740,6 +748,9 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         p->class_k = k2; p->class_count = c2; p->class_list = l2;
     }
     p->class_block.assign(p->class_k.size(), 128);
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        if (p->class_k[c] >= 6) p->class_block[c] = LRH_SHAPE_CTA_FP32;   // CTA classes: FP32 back-transform
+    p->P.tc_backtransform = 0;
     if ((rc = plan_persistent(p))) return rc;
     LRH_CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     for (size_t c = 1; c < p->class_k.size(); ++c) {
@@ -787,7 +798,7 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
         info->sweeps[c] = sw[p->class_k[c]];
         info->class_block[c] = p->class_block[c];
     }
-    info->concurrent_classes = p->concurrent ? 1 : 0;
+    info->concurrent_classes = (p->fused && p->persist_grid > 0) ? 2 : (p->concurrent ? 1 : 0);
     info->loop = effective_loop(p);
     info->persistent_grid = p->persist_grid;
     info->persistent_tiles = p->persist_grid > 0 ? p->plan.tiles : 0;
@@ -1136,7 +1147,29 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
     std::vector<std::string> new_lines;
     for (size_t c = 0; c < p->class_k.size(); ++c) {
         const int k = p->class_k[c];
-        if (k > 5) continue;   // CTA classes: one region per CTA, nothing to choose
+        if (k > 5) {   // CTA classes: one region per CTA; choose the back-transform (CUDA cores or tcgen05)
+            const std::string key = "region_pass_backtransform k=" + std::to_string(k) + " units=" +
+                                    std::to_string((int64_t)p->class_count[c] * p->n_inst) + " sms=" + std::to_string(sms);
+            int mode = 0;
+            if (!cache_lookup(cache, key, &mode)) {
+                float best = 1e30f;
+                for (int cand : {LRH_SHAPE_CTA_FP32, LRH_SHAPE_CTA_TENSOR}) {
+                    if (cand == LRH_SHAPE_CTA_TENSOR && k != 7) continue;   // built for 7-site regions only
+                    int rc = lrh_set_launch_shape(p, k, cand);
+                    if (rc) return rc;
+                    float ms = 0;
+                    rc = time_ms(p, 2, [&]() -> int {
+                        LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, 0));
+                        return LRH_OK; }, &ms);
+                    if (rc) return rc;
+                    if (ms < best) { best = ms; mode = cand; }
+                }
+                new_lines.push_back("{\"key\": \"" + key + "\", \"block\": " + std::to_string(mode) + "}");
+            }
+            int rc = lrh_set_launch_shape(p, k, mode);
+            if (rc) return rc;
+            continue;
+        }
         const std::string key = "region_pass k=" + std::to_string(k) + " units=" +
                                 std::to_string((int64_t)p->class_count[c] * p->n_inst) + " sms=" + std::to_string(sms);
         int blk = 0;
@@ -1156,35 +1189,19 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         }
         p->class_block[c] = blk;
     }
-    if (p->class_k.size() > 1) {
-        std::string key = "concurrent classes";
-        for (size_t c = 0; c < p->class_k.size(); ++c)
-            key += " k" + std::to_string(p->class_k[c]) + "=" + std::to_string((int64_t)p->class_count[c] * p->n_inst);
-        key += " sms=" + std::to_string(sms);
-        int conc = 1;
-        if (!cache_lookup(cache, key, &conc)) {
-            float ms_seq = 0, ms_con = 0;
-            p->concurrent = false;
-            int rc = time_ms(p, 3, [&]() { return launch_all_classes(p, plain_io(p)); }, &ms_seq);
-            if (rc) return rc;
-            p->concurrent = true;
-            rc = time_ms(p, 3, [&]() { return launch_all_classes(p, plain_io(p)); }, &ms_con);
-            if (rc) return rc;
-            conc = ms_con <= ms_seq ? 1 : 0;
-            new_lines.push_back("{\"key\": \"" + key + "\", \"concurrent\": " + std::to_string(conc) + "}");
-        }
-        p->concurrent = conc != 0;
-    }
-    if (p->persist_grid > 0) {
-        drop_graphs(p);   // the graph driver is timed with the shapes chosen above
-        std::string key = std::string("loop variant=") + (p->opt.variant == LRH_NESTEROV ? "nesterov" : "subgradient");
+    // Iteration driver: how the classes of a pass are launched (one after another, forked
+    // streams, one launch) under the graph driver, and the persistent driver; each timed over
+    // whole iterations on a saved copy of the multipliers and iteration scalars.
+    const bool several = p->class_k.size() > 1;
+    if (several || p->persist_grid > 0) {
+        drop_graphs(p);
+        std::string key = std::string("driver variant=") + (p->opt.variant == LRH_NESTEROV ? "nesterov" : "subgradient");
         for (size_t c = 0; c < p->class_k.size(); ++c)
             key += " k" + std::to_string(p->class_k[c]) + "=" + std::to_string((int64_t)p->class_count[c] * p->n_inst) +
                    "/" + std::to_string(p->class_block[c]);
         key += " sms=" + std::to_string(sms);
-        int choice = LRH_LOOP_GRAPH;
+        int choice = 10 * LRH_LOOP_GRAPH + 1;   // 10 * loop + class mode
         if (!cache_lookup(cache, key, &choice)) {
-            // iterate on a saved copy of the multipliers and iteration scalars, restored afterwards
             const int64_t nm = p->n_inst * p->msg_elems;
             const size_t b_msg = sizeof(float2) * (size_t)std::max<int64_t>(nm, 1);
             const size_t b_inst = sizeof(double) * (size_t)p->n_inst;
@@ -1202,10 +1219,9 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
             double* s_q = reinterpret_cast<double*>(base + 3 * b_msg);
             int32_t* s_flag = reinterpret_cast<int32_t*>(base + 3 * b_msg + b_inst);
             IterState* s_st = reinterpret_cast<IterState*>(base + 3 * b_msg + 2 * b_inst);
-            int rc;
             auto copy_all = [&](bool save) -> int {
-                auto cp = [&](void* a, void* b, size_t bytes) {
-                    return cudaMemcpyAsync(save ? a : b, save ? b : a, bytes, cudaMemcpyDeviceToDevice, p->stream);
+                auto cp = [&](void* x, void* y, size_t bytes) {
+                    return cudaMemcpyAsync(save ? x : y, save ? y : x, bytes, cudaMemcpyDeviceToDevice, p->stream);
                 };
                 LRH_CK(cp(s_nu, p->P.nu, sizeof(float2) * nm));
                 LRH_CK(cp(s_zeta, p->P.zeta, sizeof(float2) * nm));
@@ -1216,24 +1232,41 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
                 return LRH_OK;
             };
             const int saved_loop = p->opt.loop;
+            const bool saved_conc = p->concurrent, saved_fused = p->fused;
             const int64_t saved_it = p->iteration;
-            constexpr int kTuneIters = 16;
-            float ms[2] = {0.f, 0.f};
-            const int modes[2] = {LRH_LOOP_GRAPH, LRH_LOOP_PERSISTENT};
+            constexpr int kTuneIters = 8;
+            int rc;
             if ((rc = copy_all(true))) return rc;
-            for (int m = 0; m < 2; ++m) {
-                p->opt.loop = modes[m];
-                rc = time_ms(p, 3, [&]() { return lrh_step(p, kTuneIters); }, &ms[m]);
+            float best = 1e30f;
+            for (int cand = 0; cand < 4; ++cand) {   // graph x {0, 1, 2}, then persistent
+                const int loop = cand < 3 ? LRH_LOOP_GRAPH : LRH_LOOP_PERSISTENT;
+                const int mode = cand < 3 ? cand : 1;
+                if (cand < 3 && !several && mode != 1) continue;
+                if (cand == 2 && p->persist_grid <= 0) continue;
+                if (cand == 3 && p->persist_grid <= 0) continue;
+                p->opt.loop = loop;
+                p->concurrent = mode == 1;
+                p->fused = mode == 2;
+                drop_graphs(p);
+                float ms = 0;
+                rc = time_ms(p, 2, [&]() { return lrh_step(p, kTuneIters); }, &ms);
                 const int rc2 = copy_all(false);
                 p->iteration = saved_it;
-                if (rc || rc2) { p->opt.loop = saved_loop; return rc ? rc : rc2; }
+                if (rc || rc2) {
+                    p->opt.loop = saved_loop; p->concurrent = saved_conc; p->fused = saved_fused;
+                    return rc ? rc : rc2;
+                }
+                if (ms < best) { best = ms; choice = 10 * loop + mode; }
             }
             p->opt.loop = saved_loop;
             LRH_CK(cudaStreamSynchronize(p->stream));
-            choice = ms[1] < ms[0] ? LRH_LOOP_PERSISTENT : LRH_LOOP_GRAPH;
-            new_lines.push_back("{\"key\": \"" + key + "\", \"loop\": " + std::to_string(choice) + "}");
+            new_lines.push_back("{\"key\": \"" + key + "\", \"driver\": " + std::to_string(choice) + "}");
         }
-        p->loop_auto = choice;
+        const int loop = choice / 10, mode = choice % 10;
+        p->concurrent = mode == 1;
+        p->fused = mode == 2 && p->persist_grid > 0;
+        p->loop_auto = (loop == LRH_LOOP_PERSISTENT && p->persist_grid > 0) ? LRH_LOOP_PERSISTENT : LRH_LOOP_GRAPH;
+        drop_graphs(p);
     }
     if (cache_path && !new_lines.empty()) {
         FILE* f = std::fopen(cache_path, "a");
@@ -1247,15 +1280,32 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
 
 int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
-    const bool ok = block == 64 || block == 128 || block == 256 || (k_sites == 2 && (block == -64 || block == -128 || block == -256));
-    if (!ok || (block > 0 && block < (1 << k_sites))) return fail(LRH_EINVAL, "unsupported launch shape for this region size");
+    bool ok;
+    if (k_sites >= 6) ok = block == LRH_SHAPE_CTA_FP32 || (block == LRH_SHAPE_CTA_TENSOR && k_sites == 7);
+    else ok = (block == 64 || block == 128 || block == 256 || (k_sites == 2 && (block == -64 || block == -128 || block == -256))) &&
+              !(block > 0 && block < (1 << k_sites));
+    if (!ok) return fail(LRH_EINVAL, "unsupported launch shape for this region size");
     for (size_t c = 0; c < p->class_k.size(); ++c)
         if (p->class_k[c] == k_sites) {
             p->class_block[c] = block;
+            if (k_sites >= 6) {
+                const int bit = 1 << (k_sites - 6);
+                p->P.tc_backtransform = block == LRH_SHAPE_CTA_TENSOR ? (p->P.tc_backtransform | bit) : (p->P.tc_backtransform & ~bit);
+            }
             drop_graphs(p);
             return LRH_OK;
         }
     return fail(LRH_EINVAL, "no region class with " + std::to_string(k_sites) + " sites");
+}
+
+int lrh_set_class_mode(lrh_problem* p, int32_t mode) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (mode < 0 || mode > 2) return fail(LRH_EINVAL, "class mode must be 0, 1 or 2");
+    if (mode == 2 && p->persist_grid <= 0) return fail(LRH_EUNSUPPORTED, "one-launch passes need classes of <= 4 sites");
+    p->concurrent = mode == 1;
+    p->fused = mode == 2;
+    drop_graphs(p);
+    return LRH_OK;
 }
 
 int lrh_selftest_barrier_timeout(lrh_problem* p) {

@@ -13,9 +13,9 @@
 //   3. V (in registers, 4 threads per row, columns in slot order) gets the column rotation
 //      and then the tournament's column permutation, which moves one complex value across
 //      each chunk boundary (two shuffles between the lanes holding neighbouring chunks).
-// The Gibbs / ground state rho = W W^dagger, W = V diag(sqrt p), is formed from W^T staged
-// in the same shared-memory buffer, with register tiles; then made exactly Hermitian, traced
-// onto the children and written out.  The FP64 certification kernel reuses the Jacobi part
+// The Gibbs / ground state rho = W W^dagger, W = V diag(sqrt p), is formed either on the FP32
+// cores from W^T staged in the same shared-memory buffer, with register tiles, or on the tensor
+// cores (tcgen05, below); then made exactly Hermitian, traced onto the children and written out.  The FP64 certification kernel reuses the Jacobi part
 // (no V) to return lambda_min.
 #include "lrh_device.cuh"
 #include "lrh_internal.cuh"
@@ -59,23 +59,6 @@ template <typename T>
 __device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
-
-template <typename T>
-__device__ __forceinline__ void rot_params_c(T app, T aqq, T br, T bi, RotC<T>& R) {
-    const T h = aqq - app;
-    const T b2 = br * br + bi * bi;
-    const T r = sqrt_t<T>(h * h + T(4) * b2);
-    const T den = fabs(h) + r;
-    const T sg = h >= T(0) ? T(1) : T(-1);
-    T t = T(0), sig = T(0);
-    if (den > T(0)) t = -sg * T(2) * sqrt_t<T>(b2) / den;
-    const T c = T(1) / sqrt_t<T>(T(1) + t * t);
-    if (den > T(0)) sig = -sg * T(2) * c / den;
-    R.c = c;
-    R.wr = sig * br;
-    R.wi = sig * bi;
-    R.pad = T(0);
-}
 
 __device__ __forceinline__ int tri(int i, int j, int D) { return i * D - ((i * (i - 1)) >> 1) + (j - i); }
 
@@ -195,6 +178,11 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     return s;
 }
 
+// Rotation record of pair k: one pad record after every D/8 pairs (one V column chunk), so the
+// four chunks' records that a warp reads in the same instruction fall on different banks.
+template <int D>
+__device__ __forceinline__ int prm_at(int k) { return k + k / (D / 8); }
+
 template <int D> struct CtaCfg;
 template <> struct CtaCfg<64> { static constexpr int NT = 256; static constexpr int TR = 4, TC = 4; };
 template <> struct CtaCfg<128> { static constexpr int NT = 512; static constexpr int TR = 4, TC = 8; };
@@ -206,24 +194,56 @@ struct CtaSmem {
     static constexpr int NT = CtaCfg<D>::NT;
     static constexpr size_t tri_elems = (size_t)D * (D + 1) / 2;
     // FP32 kernel also stages W^T and rho (D x D) in the same buffer
-    static constexpr size_t buf_bytes_f = ((sizeof(float2) * (size_t)D * (D + 1)) + 15) / 16 * 16;
+    // FP32 pass: the Jacobi matrix (D x (D+1) complex), later the tensor-core operand chunks
+    // (2 buffers x hi/lo x 2D rows x KC tf32) or the W^T / rho staging
+    static constexpr size_t jac_bytes = sizeof(float2) * (size_t)D * (D + 1);
+    static constexpr size_t tc_bytes = D == 128 ? (size_t)4 * (2 * D) * 32 * 4 : 0;   // 2 buffers x hi/lo
+    static constexpr size_t buf_bytes_f = ((jac_bytes > tc_bytes ? jac_bytes : tc_bytes) + 127) / 128 * 128;
     static constexpr size_t buf_bytes_d = ((sizeof(double2) * tri_elems) + 15) / 16 * 16;
     static constexpr size_t buf_bytes = sizeof(T) == 4 ? buf_bytes_f : buf_bytes_d;
     static constexpr size_t off_prm = buf_bytes;
-    static constexpr size_t off_idx = off_prm + sizeof(RotC<T>) * n;
+    static constexpr size_t off_idx = off_prm + sizeof(RotC<T>) * (n + 4);   // + one pad record per V chunk
     static constexpr size_t off_tab = off_idx + sizeof(int) * 2 * D;
     static constexpr size_t off_lam = off_tab + ((sizeof(unsigned short) * NB + 15) / 16 * 16);
     static constexpr size_t off_red = off_lam + sizeof(float) * 2 * D;
-    static constexpr size_t bytes = off_red + sizeof(double) * (NT / 32) + 16;
+    static constexpr size_t off_mbar = (off_red + sizeof(double) * (NT / 32) + 15) / 16 * 16;   // 2 mbarriers + TMEM slot
+    static constexpr size_t bytes = off_mbar + 32;
 };
+
+// Rotation J = [[c, -w], [conj(w), c]], w = sigma a_pq, of pair (p, q) from a_pp, a_qq, a_pq
+// (h = a_qq - a_pp, r = sqrt(h^2 + 4|a_pq|^2), t = -sgn(h) 2|a_pq| / (|h| + r), c = 1 / sqrt(1 + t^2),
+// sigma = -sgn(h) 2 c / (|h| + r)), and the diagonal after it, a_pp + t |a_pq| and a_qq - t |a_pq|.
+template <typename T>
+__device__ __forceinline__ void rot_params_d(T app, T aqq, T br, T bi, RotC<T>& R, typename V2<T>::t& dnew) {
+    const T h = aqq - app;
+    const T b2 = br * br + bi * bi;
+    const T r = sqrt_t<T>(h * h + T(4) * b2);
+    const T den = fabs(h) + r;
+    const T sg = h >= T(0) ? T(1) : T(-1);
+    const T bn = sqrt_t<T>(b2);
+    T t = T(0), sig = T(0);
+    if (den > T(0)) t = -sg * T(2) * bn / den;
+    const T c = T(1) / sqrt_t<T>(T(1) + t * t);
+    if (den > T(0)) sig = -sg * T(2) * c / den;
+    R.c = c;
+    R.wr = sig * br;
+    R.wi = sig * bi;
+    R.pad = T(0);
+    dnew.x = app + t * bn;
+    dnew.y = aqq - t * bn;
+}
 
 // Cyclic Jacobi on the Hermitian matrix behind accessor A; V (if WANT_V) holds row `row`,
 // columns [chunk * W, chunk * W + W) in slot order.  Two barriers per round: after the rotation
 // parameters, and after the block updates (the slot map is double-buffered and its next
 // state written during the update phase).  Returns the sweeps run.
+// (Computing the next round's rotations inside the block updates, to save the first barrier,
+// measured slower: the 64 parameter computations then fall on many warps, each of which runs
+// the divisions and square roots for one lane, instead of two warps running them for all.)
 template <int D, typename T, bool WANT_V, typename Acc>
 __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
                           T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out) {
+    using C2 = typename V2<T>::t;
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
     // off-diagonal blocks (k < l) first, spread over all threads; the diagonal blocks (k = l,
@@ -254,16 +274,17 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
         ++sweeps;
         for (int r = 0; r < D - 1; ++r) {
             if (t < n) {
-                const int p = ix[2 * t], q = ix[2 * t + 1];
-                const auto b = A.get(p, q);
-                rot_params_c<T>(A.dget(p).x, A.dget(q).x, b.x, b.y, prm[t]);
+                const int2 pq = reinterpret_cast<const int2*>(ix)[t];
+                const auto b = A.get(pq.x, pq.y);
+                C2 unused;
+                rot_params_d<T>(A.dget(pq.x).x, A.dget(pq.y).x, b.x, b.y, prm[prm_at<D>(t)], unused);
             }
             __syncthreads();
             if (t < D) ixn[t] = ix[rr_src_c(t, D)];
             if (WANT_V) {
 #pragma unroll
                 for (int m = 0; m < W / 2; ++m) {
-                    const RotC<T> Rk = prm[(chunk * W) / 2 + m];
+                    const RotC<T> Rk = prm[prm_at<D>((chunk * W) / 2 + m)];
                     T& pr = vr[2 * m]; T& pi = vi[2 * m]; T& qr = vr[2 * m + 1]; T& qi = vi[2 * m + 1];
                     const T npr = Rk.c * pr + (Rk.wr * qr + Rk.wi * qi);
                     const T npi = Rk.c * pi + (Rk.wr * qi - Rk.wi * qr);
@@ -278,18 +299,20 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
                 if (v < NOFF) {
                     const int kl = tab[v];
                     const int kk = kl >> 8, ll = kl & 255;
-                    const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
-                    const int pl = ix[2 * ll], ql = ix[2 * ll + 1];
+                    const int2 pqk = reinterpret_cast<const int2*>(ix)[kk];
+                    const int2 pql = reinterpret_cast<const int2*>(ix)[ll];
+                    const int pk = pqk.x, qk = pqk.y, pl = pql.x, ql = pql.y;
                     auto b00 = A.get(pk, pl), b01 = A.get(pk, ql), b10 = A.get(qk, pl), b11 = A.get(qk, ql);
-                    const RotC<T> K = prm[kk];
-                    const RotC<T> Lr = prm[ll];
+                    const RotC<T> K = prm[prm_at<D>(kk)];
+                    const RotC<T> Lr = prm[prm_at<D>(ll)];
                     two_sided<T>(b00, b01, b10, b11, K, Lr);
                     A.set(pk, pl, b00); A.set(pk, ql, b01); A.set(qk, pl, b10); A.set(qk, ql, b11);
                 } else {
                     const int kk = (t - DG0) + DGT * (j - JD0);
                     if (t >= DG0 && kk < n) {
-                        const RotC<T> K = prm[kk];
-                        const int pk = ix[2 * kk], qk = ix[2 * kk + 1];
+                        const RotC<T> K = prm[prm_at<D>(kk)];
+                        const int2 pq = reinterpret_cast<const int2*>(ix)[kk];
+                        const int pk = pq.x, qk = pq.y;
                         auto b00 = A.dget(pk);
                         auto b11 = A.dget(qk);
                         auto b01 = A.get(pk, qk);
@@ -426,6 +449,231 @@ __device__ void build_table(unsigned short* tab) {
     }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Tensor-core back-transform for the FP32 CTA pass (D = 128): rho = W W^dagger with
+// W = V diag(sqrt p), as one real GEMM  [rho_r; rho_i] = A B^T  with
+//   A = [[W_r, W_i], [W_i, -W_r]]  (2D x 2D),   B = [W_r, W_i]  (D x 2D, = the first D rows of A),
+// on tcgen05.mma kind::tf32 with FP32 accumulators in tensor memory.  FP32 accuracy from three
+// TF32 products per term (x = hi + lo, hi = x with the low 13 mantissa bits cleared, lo = x - hi
+// exact; A B^T ~ A_hi B_hi + A_hi B_lo + A_lo B_hi, the dropped lo*lo term is below 2^-21
+// relative).  K = 2D is staged in chunks of KC columns (KC / 2 values of c, real then imaginary
+// part; KC = 32) into two alternating shared-memory buffers while the previous chunk's MMAs run.
+// Operands use the K-major layout without swizzle: core matrices of 8 rows x 16 bytes, K-adjacent
+// core matrices 128 bytes apart (leading byte offset), 8-row groups KC * 32 bytes apart (stride
+// byte offset).  One elected thread issues the MMAs and commits them to an mbarrier; all waits
+// are bounded and report DEV_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------------------------
+namespace tc {
+
+// K columns per chunk
+template <int D> struct TcKC { static constexpr int v = 32; };
+constexpr uint32_t kLBO = 128;         // bytes between K-adjacent core matrices
+template <int KC> struct TcSBO { static constexpr uint32_t v = (KC / 4) * 128; };   // bytes between 8-row groups
+constexpr unsigned long long kWaitNs = 500000000ull;
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// instruction descriptor of kind::tf32: F32 accumulator, TF32 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// shared-memory matrix descriptor: start address, leading / stride byte offsets, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+                 :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait for the phase with the given parity; false after kWaitNs
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}\n" : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (now_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// byte offset of element (row m, K column kk) of one operand buffer
+template <int KC>
+__device__ __forceinline__ uint32_t off(int m, int kk) {
+    return (uint32_t)((m >> 3) * TcSBO<KC>::v + (kk >> 2) * kLBO + (m & 7) * 16 + (kk & 3) * 4);
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+                 "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Stage K chunk j (c in [16 j, 16 j + 16)) of A = [[W_r, W_i], [W_i, -W_r]] as hi and lo parts.
+// The thread holding row `row`, columns [vc W, vc W + W) of V writes when the chunk is in them;
+// OFF is the chunk's first column inside the thread's W columns (compile-time).
+template <int D, int OFF>
+__device__ __forceinline__ void stage_rows(unsigned char* hi, unsigned char* lo, int row, const float* q,
+                                           const float (&vr)[D / 4], const float (&vi)[D / 4], int c0) {
+#pragma unroll
+    constexpr int KC = TcKC<D>::v;
+    for (int g = 0; g < KC / 8; ++g) {   // K groups of 4: real parts of c0 + 4g .. c0 + 4g + 3
+        float wr[4], wi[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float s = q[c0 + 4 * g + e];
+            wr[e] = vr[OFF + 4 * g + e] * s;
+            wi[e] = vi[OFF + 4 * g + e] * s;
+        }
+        // row: [W_r | W_i]; row + D: [W_i | -W_r]
+        const float4 a0 = make_float4(wr[0], wr[1], wr[2], wr[3]);
+        const float4 a1 = make_float4(wi[0], wi[1], wi[2], wi[3]);
+        const float4 b0 = a1;
+        const float4 b1 = make_float4(-wr[0], -wr[1], -wr[2], -wr[3]);
+        const float4 parts[4] = {a0, a1, b0, b1};
+        const int rows[4] = {row, row, row + D, row + D};
+        const int cols[4] = {4 * g, KC / 2 + 4 * g, 4 * g, KC / 2 + 4 * g};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 x = parts[u];
+            const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+            const float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+            const uint32_t o = off<KC>(rows[u], cols[u]);
+            *reinterpret_cast<float4*>(hi + o) = h;
+            *reinterpret_cast<float4*>(lo + o) = l;
+        }
+    }
+}
+
+}  // namespace tc
+
+// rho = W W^dagger on the tensor cores into two padded planes Rr, Ri (D x (D+1) floats each, the
+// upper triangle of rho is read from them).  Returns false if a wait timed out (DEV_ERR_TIMEOUT).
+template <int D>
+__device__ bool backtransform_tc(const DevProblem& P, unsigned char* sm, float* pw, uint64_t* mbar, uint32_t* tslot,
+                                 const float (&vr)[D / 4], const float (&vi)[D / 4], int row, int chunk) {
+    using S = CtaSmem<D, float>;
+    constexpr int W = D / 4;
+    constexpr int M = 128;                    // MMA rows per tile
+    constexpr int MT = (2 * D) / M;           // A tiles: 1 (D = 64) or 2 (D = 128)
+    constexpr int KC = tc::TcKC<D>::v;
+    constexpr uint32_t SBO = tc::TcSBO<KC>::v;
+    constexpr int NCH = (2 * D) / KC;         // K chunks
+    constexpr uint32_t NCOL = D == 64 ? 64u : 256u;   // TMEM columns (power of two >= 32)
+    constexpr uint32_t PART = (uint32_t)(2 * D) * KC * 4;   // bytes of one operand part (2D rows x KC)
+    static_assert(4 * PART <= S::buf_bytes, "tensor-core operands do not fit the buffer");
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t base = tc::saddr(sm);
+    const uint32_t mb0 = tc::saddr(mbar), mb1 = tc::saddr(mbar + 1);
+    const uint32_t idesc = tc::idesc_tf32(M, D);
+    bool ok = true;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(tc::saddr(tslot)), "r"(NCOL) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    for (int j = 0; j < NCH; ++j) {
+        const int b = j & 1;
+        unsigned char* hi = sm + (size_t)(2 * b) * PART;
+        unsigned char* lo = hi + PART;
+        if (j >= 2 && !tc::wait_parity(b ? mb1 : mb0, (uint32_t)((j / 2 - 1) & 1))) ok = false;
+        const int c0 = KC / 2 * j;            // first c of the chunk
+        if (chunk == c0 / W) {   // the chunk's KC / 2 columns start at 0 or at W / 2 of the thread's W
+            if (c0 % W == 0) tc::stage_rows<D, 0>(hi, lo, row, pw, vr, vi, c0);
+            else tc::stage_rows<D, W / 2>(hi, lo, row, pw, vr, vi, c0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = base + (uint32_t)(2 * b) * PART, alo = ahi + PART;
+#pragma unroll
+            for (int s = 0; s < KC / 8; ++s) {
+                const uint32_t ko = (uint32_t)(2 * s) * tc::kLBO;   // 8 K columns = 2 core matrices
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const uint32_t mo = (uint32_t)mt * (M / 8) * SBO;
+                    const uint32_t d = tmem + (uint32_t)(mt * D);
+                    const uint32_t acc0 = (j > 0 || s > 0) ? 1u : 0u;
+                    tc::mma(d, tc::sdesc(ahi + mo + ko, tc::kLBO, SBO), tc::sdesc(ahi + ko, tc::kLBO, SBO), idesc, acc0);
+                    tc::mma(d, tc::sdesc(ahi + mo + ko, tc::kLBO, SBO), tc::sdesc(alo + ko, tc::kLBO, SBO), idesc, 1u);
+                    tc::mma(d, tc::sdesc(alo + mo + ko, tc::kLBO, SBO), tc::sdesc(ahi + ko, tc::kLBO, SBO), idesc, 1u);
+                }
+            }
+            tc::commit(b ? mb1 : mb0);
+        }
+    }
+    // the last commit covers every MMA issued before it
+    if (!tc::wait_parity(((NCH - 1) & 1) ? mb1 : mb0, (uint32_t)(((NCH - 1) / 2) & 1))) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // accumulators -> padded planes (the operand buffers are free now)
+    float* Rr = reinterpret_cast<float*>(sm);
+    float* Ri = Rr + D * (D + 1);
+    {
+        const int q = warp & 3, g = warp >> 2, lane = t & 31;
+        float v[32];
+        if constexpr (D == 128) {
+            const int i = 32 * q + lane;
+            tc::ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * g), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) Rr[i * (D + 1) + 32 * g + e] = v[e];
+            tc::ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(D + 32 * g), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) Ri[i * (D + 1) + 32 * g + e] = v[e];
+        } else {
+            const int lanei = 32 * q + lane;
+            tc::ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * g), v);
+            float* dst = lanei < D ? Rr + lanei * (D + 1) : Ri + (lanei - D) * (D + 1);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) dst[32 * g + e] = v[e];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(NCOL) : "memory");
+    }
+    if (!ok && t == 0) atomicOr(P.err, DEV_ERR_TIMEOUT);
+    return ok;
+}
+
 template <int D>
 __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const DevProblem P, const PassIO io,
                                                                         const int32_t* __restrict__ cls,
@@ -479,71 +727,110 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
         if (t < D) pw[t] = (lam[t] - lmin <= tau) ? sqrtf(1.0f / Z) : 0.f;
     }
     __syncthreads();
-    // W^T[c][row] = V[row][c] sqrt(p_c)   (overwrites the triangle, no longer needed)
+    // the tensor-core back-transform is built for D = 128 only: at D = 64 a kernel containing it
+    // ran with half the resident CTAs per SM (one instead of two) and was slower overall
+    bool use_tc = false;
+    if constexpr (D == 128) use_tc = ((P.tc_backtransform >> (k - 6)) & 1) != 0;
+    if (use_tc) {
+        if constexpr (D == 128) {
+            uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + S::off_mbar);
+            uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + S::off_mbar + 16);
+            backtransform_tc<D>(P, sm, pw, mbar, tslot, vr, vi, row, chunk);
+            // rho from the planes: upper triangle as computed, lower = its conjugate, real diagonal
+            const float* Rr = reinterpret_cast<const float*>(sm);
+            const float* Ri = Rr + D * (D + 1);
+            auto rho_at = [&](int i, int j) -> float2 {
+                if (i < j) return make_float2(Rr[i * (D + 1) + j], Ri[i * (D + 1) + j]);
+                if (i > j) return make_float2(Rr[j * (D + 1) + i], -Ri[j * (D + 1) + i]);
+                return make_float2(Rr[i * (D + 1) + i], 0.f);
+            };
+            if (R.rho_off >= 0) {
+                float2* dst = io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off;
+                for (int e = t; e < D * D; e += NT) dst[e] = rho_at(e / D, e % D);
+            }
+            float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
+            for (int q = R.child_begin; q < R.child_end; ++q) {
+                const PairInfo pi = P.child_info[q];
+                const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
+                for (int o = t; o < Df * Df; o += NT) {
+                    const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
+                    float sr = 0.f, si = 0.f;
+                    for (int c = 0; c < nrest; ++c) {
+                        const int x = pdep7(c, Mc);
+                        const float2 v = rho_at(ra | x, rbb | x);
+                        sr += v.x; si += v.y;
+                    }
+                    trb[pi.off + o] = make_float2(sr, si);
+                }
+            }
+        }
+    } else {
+        // W^T[c][row] = V[row][c] sqrt(p_c)   (overwrites the triangle, no longer needed)
 #pragma unroll
-    for (int m = 0; m < W; ++m) {
-        const int c = chunk * W + m;
-        const float q = pw[c];
-        buf[c * D + row] = make_float2(vr[m] * q, vi[m] * q);
-    }
-    __syncthreads();
-    // rho = W W^dagger in TR x TC register tiles: rho[i][c] = sum_k W[i][k] conj(W[c][k]); a thread
-    // owns rows i0 .. i0+TR-1 and the strided columns cb + (D/TC) b, so that consecutive threads
-    // read and write consecutive columns (no shared-memory bank conflicts)
-    const int rb = t / (D / TC), cb = t % (D / TC);
-    const int i0 = rb * TR;
-    constexpr int CS = D / TC;
-    float accr[TR][TC], acci[TR][TC];
-#pragma unroll
-    for (int a = 0; a < TR; ++a)
-#pragma unroll
-        for (int b = 0; b < TC; ++b) { accr[a][b] = 0.f; acci[a][b] = 0.f; }
-    for (int kk = 0; kk < D; ++kk) {
-        const float2* wk = buf + kk * D;
-        float2 wi[TR], wc[TC];
-#pragma unroll
-        for (int a = 0; a < TR; ++a) wi[a] = wk[i0 + a];
-#pragma unroll
-        for (int b = 0; b < TC; ++b) wc[b] = wk[cb + CS * b];
+        for (int m = 0; m < W; ++m) {
+            const int c = chunk * W + m;
+            const float q = pw[c];
+            buf[c * D + row] = make_float2(vr[m] * q, vi[m] * q);
+        }
+        __syncthreads();
+        // rho = W W^dagger in TR x TC register tiles: rho[i][c] = sum_k W[i][k] conj(W[c][k]); a thread
+        // owns rows i0 .. i0+TR-1 and the strided columns cb + (D/TC) b, so that consecutive threads
+        // read and write consecutive columns (no shared-memory bank conflicts)
+        const int rb = t / (D / TC), cb = t % (D / TC);
+        const int i0 = rb * TR;
+        constexpr int CS = D / TC;
+        float accr[TR][TC], acci[TR][TC];
 #pragma unroll
         for (int a = 0; a < TR; ++a)
 #pragma unroll
-            for (int b = 0; b < TC; ++b) {
-                accr[a][b] += wi[a].x * wc[b].x + wi[a].y * wc[b].y;
-                acci[a][b] += wi[a].y * wc[b].x - wi[a].x * wc[b].y;
-            }
-    }
-    __syncthreads();
+            for (int b = 0; b < TC; ++b) { accr[a][b] = 0.f; acci[a][b] = 0.f; }
+        for (int kk = 0; kk < D; ++kk) {
+            const float2* wk = buf + kk * D;
+            float2 wi[TR], wc[TC];
 #pragma unroll
-    for (int a = 0; a < TR; ++a)
+            for (int a = 0; a < TR; ++a) wi[a] = wk[i0 + a];
 #pragma unroll
-        for (int b = 0; b < TC; ++b) buf[(i0 + a) * D + cb + CS * b] = make_float2(accr[a][b], acci[a][b]);
-    __syncthreads();
-    // exact Hermitian symmetry: lower triangle := conj(upper), real diagonal
-    for (int e = t; e < D * D; e += NT) {
-        const int i = e / D, j = e % D;
-        if (i > j) { const float2 u = buf[j * D + i]; buf[e] = make_float2(u.x, -u.y); }
-        else if (i == j) buf[e].y = 0.f;
-    }
-    __syncthreads();
-    if (R.rho_off >= 0) {
-        float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off);
-        const float4* srcv = reinterpret_cast<const float4*>(buf);
-        for (int e = t; e < D * D / 2; e += NT) dst[e] = srcv[e];
-    }
-    float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
-    for (int q = R.child_begin; q < R.child_end; ++q) {
-        const PairInfo pi = P.child_info[q];
-        const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
-        for (int o = t; o < Df * Df; o += NT) {
-            const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
-            float sr = 0.f, si = 0.f;
-            for (int c = 0; c < nrest; ++c) {
-                const int x = pdep7(c, Mc);
-                const float2 v = buf[(ra | x) * D + (rbb | x)];
-                sr += v.x; si += v.y;
+            for (int b = 0; b < TC; ++b) wc[b] = wk[cb + CS * b];
+#pragma unroll
+            for (int a = 0; a < TR; ++a)
+#pragma unroll
+                for (int b = 0; b < TC; ++b) {
+                    accr[a][b] += wi[a].x * wc[b].x + wi[a].y * wc[b].y;
+                    acci[a][b] += wi[a].y * wc[b].x - wi[a].x * wc[b].y;
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) buf[(i0 + a) * D + cb + CS * b] = make_float2(accr[a][b], acci[a][b]);
+        __syncthreads();
+        // exact Hermitian symmetry: lower triangle := conj(upper), real diagonal
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            if (i > j) { const float2 u = buf[j * D + i]; buf[e] = make_float2(u.x, -u.y); }
+            else if (i == j) buf[e].y = 0.f;
+        }
+        __syncthreads();
+        if (R.rho_off >= 0) {
+            float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off);
+            const float4* srcv = reinterpret_cast<const float4*>(buf);
+            for (int e = t; e < D * D / 2; e += NT) dst[e] = srcv[e];
+        }
+        float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
+            for (int o = t; o < Df * Df; o += NT) {
+                const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
+                float sr = 0.f, si = 0.f;
+                for (int c = 0; c < nrest; ++c) {
+                    const int x = pdep7(c, Mc);
+                    const float2 v = buf[(ra | x) * D + (rbb | x)];
+                    sr += v.x; si += v.y;
+                }
+                trb[pi.off + o] = make_float2(sr, si);
             }
-            trb[pi.off + o] = make_float2(sr, si);
         }
     }
     if (t == 0) {

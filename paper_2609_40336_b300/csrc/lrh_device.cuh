@@ -135,12 +135,15 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
         const bool done = (off <= thresh) || (sweeps >= max_sweeps);
         if (__all_sync(kFull, done)) break;
         ++sweeps;
-        for (int r = 0; r < D - 1; ++r) {
+        // One round of the tournament: pair parameters from (xr, xi), column rotations of
+        // (xr, xi) and V in place, and the row rotation with the tournament permutation into
+        // (yr, yi).  Rounds alternate between the two register arrays (no copies).
+        auto round = [&](T (&xr)[D], T (&xi)[D], T (&yr)[D], T (&yi)[D]) {
             // (1) parameters of pair k = s >> 1 (both lanes of the pair compute them from the
             //     same shuffled values, so they agree bit for bit)
             T e0r, e1r, e0i, e1i;
-            pick_pair<D>(ar, s, e0r, e1r);
-            pick_pair<D>(ai, s, e0i, e1i);
+            pick_pair<D>(xr, s, e0r, e1r);
+            pick_pair<D>(xi, s, e0i, e1i);
             const bool odd = (s & 1) != 0;
             const T mydiag = odd ? e1r : e0r;
             const T offr = odd ? e0r : e1r;
@@ -158,29 +161,27 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
 #pragma unroll
             for (int k = 0; k < D / 2; ++k) {
                 const Rot<T> P = prm[k];
-                mix_cols(ar[2 * k], ai[2 * k], ar[2 * k + 1], ai[2 * k + 1], P.c, P.wr, P.wi);
+                mix_cols(xr[2 * k], xi[2 * k], xr[2 * k + 1], xi[2 * k + 1], P.c, P.wr, P.wi);
                 if (WANT_V) mix_cols(vr[2 * k], vi[2 * k], vr[2 * k + 1], vi[2 * k + 1], P.c, P.wr, P.wi);
             }
             // (3) row rotation fused with the tournament permutation of rows and columns:
-            //     new A[s][c] = (J^H A)[o][rr_src(c)] with o = rr_src(s)
+            //     new A[s][c] = (J^H A)[o][rr_src(c)] with o = rr_src(s); for an odd source row
+            //     the sign of the rotation's second term is folded into its coefficients
             const int o = rr_src(s, D);
             const Rot<T> Q = prm[o >> 1];
             const bool oodd = (o & 1) != 0;
-            const T sgn = oodd ? T(-1) : T(1);
-            const T qwi = oodd ? -Q.wi : Q.wi;
-            T nr[D], ni[D];
+            const T qwr = oodd ? -Q.wr : Q.wr;
+            const T qwi = Q.wi;
 #pragma unroll
             for (int cc = 0; cc < D; ++cc) {
                 const int sc = rr_src(cc, D);
-                const T r1r = __shfl_sync(kFull, ar[sc], o, D);
-                const T r1i = __shfl_sync(kFull, ai[sc], o, D);
-                const T r2r = __shfl_sync(kFull, ar[sc], o ^ 1, D);
-                const T r2i = __shfl_sync(kFull, ai[sc], o ^ 1, D);
-                nr[cc] = Q.c * r1r + sgn * (Q.wr * r2r - qwi * r2i);
-                ni[cc] = Q.c * r1i + sgn * (Q.wr * r2i + qwi * r2r);
+                const T r1r = __shfl_sync(kFull, xr[sc], o, D);
+                const T r1i = __shfl_sync(kFull, xi[sc], o, D);
+                const T r2r = __shfl_sync(kFull, xr[sc], o ^ 1, D);
+                const T r2i = __shfl_sync(kFull, xi[sc], o ^ 1, D);
+                yr[cc] = Q.c * r1r + (qwr * r2r - qwi * r2i);
+                yi[cc] = Q.c * r1i + (qwr * r2i + qwi * r2r);
             }
-#pragma unroll
-            for (int cc = 0; cc < D; ++cc) { ar[cc] = nr[cc]; ai[cc] = ni[cc]; }
             if (WANT_V) {
                 T tr_[D], ti_[D];
 #pragma unroll
@@ -189,7 +190,17 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
                 for (int cc = 0; cc < D; ++cc) { vr[cc] = tr_[cc]; vi[cc] = ti_[cc]; }
             }
             __syncwarp();
+        };
+        T br_[D], bi_[D];
+#pragma unroll 1
+        for (int r = 0; r + 1 < D - 1; r += 2) {
+            round(ar, ai, br_, bi_);
+            round(br_, bi_, ar, ai);
         }
+        // D - 1 rounds per sweep is odd: the last one lands in (br_, bi_)
+        round(ar, ai, br_, bi_);
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) { ar[cc] = br_[cc]; ai[cc] = bi_[cc]; }
     }
     return sweeps;
 }

@@ -79,7 +79,7 @@ struct DevProblem {
     int32_t n_inst;
     int32_t n_regions;
     int32_t n_pairs;
-    int32_t pad;
+    int32_t tc_backtransform;   // bit k - 6 set: the D = 2^k CTA pass forms rho on the tensor cores
     int64_t h_elems;       // complex entries per instance
     int64_t rho_elems;
     int64_t msg_elems;
@@ -91,6 +91,7 @@ struct DevProblem {
     const int64_t* chunk_rho;    // [msg_elems / 4] child-state offset minus message offset of that pair
     const PairInfo* child_info;  // PairInfo in child CSR order (child_pairs[q] resolved)
     const PairInfo* parent_info; // PairInfo in parent CSR order
+    int32_t class_base[8];       // [k]: first region id when the class of k sites is a contiguous id range, else -1
     const float2* h32;     // [n_inst][h_elems]
     const double2* h64;    // [n_inst][h_elems]
     float2* nu;            // [n_inst][msg_elems]
@@ -178,6 +179,8 @@ struct PersistPlan {
 };
 int persistent_tile_regions(int k);
 cudaError_t persistent_prepare(int kmax, int* blocks_per_sm);
+// One region pass of every class of the plan in one ordinary launch (grid = plan tiles).
+cudaError_t launch_class_pass(const DevProblem& P, const PersistPlan& L, int kmax, const PassIO& io, cudaStream_t s);
 // unreleased = true (self-test of the bounded wait): every barrier expects one CTA more than the
 // grid, so the first barrier never opens and every CTA returns after its wait limit with
 // DEV_ERR_TIMEOUT.

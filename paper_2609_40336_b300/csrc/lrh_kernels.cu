@@ -66,7 +66,14 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
     const int64_t unit = tile * G + g;
     const bool valid = unit < (int64_t)P.n_inst * count;
     const int inst = valid ? (int)(unit / count) : 0;
-    const int r = valid ? cls[unit % count] : 0;
+    // contiguous class of a latency-bound size: the region id without a dependent load
+    int r = 0;
+    if constexpr (D <= 8) {
+        const int cb = P.class_base[D == 4 ? 2 : 3];
+        r = valid ? (cb >= 0 ? cb + (int)(unit % count) : cls[unit % count]) : 0;
+    } else {
+        r = valid ? cls[unit % count] : 0;
+    }
     const bool nest = P.st->variant == 1;
     const int max_sweeps = P.st->max_sweeps;
     const Thetas T = pass_thetas(P, io);
@@ -214,7 +221,7 @@ __device__ __forceinline__ void region_d2_unit(const DevProblem& P, const PassIO
                                                const int32_t* __restrict__ cls, const int32_t count, const int64_t unit) {
     if (unit >= (int64_t)P.n_inst * count) return;
     const int inst = (int)(unit / count);
-    const int r = cls[unit % count];
+    const int r = P.class_base[1] >= 0 ? P.class_base[1] + (int)(unit % count) : cls[unit % count];
     const bool nest = P.st->variant == 1;
     const RegionInfo R = P.reg[r];
     float a = 0.f, d = 0.f, br = 0.f, bi = 0.f;
@@ -298,7 +305,7 @@ __global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem 
     int sweeps = 0;
     if (unit < (int64_t)P.n_inst * count) {
         const int inst = (int)(unit / count);
-        const int r = cls[unit % count];
+        const int r = P.class_base[2] >= 0 ? P.class_base[2] + (int)(unit % count) : cls[unit % count];
         const RegionInfo R = P.reg[r];
         const bool nest = P.st->variant == 1;
         float ar[4][4], ai[4][4], vr[4][4], vi[4][4];
@@ -725,6 +732,41 @@ __device__ __forceinline__ PassIO nesterov_io(const DevProblem& P, const int j) 
 // live around the per-region code): no spills up to k = 3; a small one at k = 4.
 template <int KMAX> struct PersistCap { static constexpr int v = KMAX == 2 ? 96 : (KMAX == 3 ? 128 : 168); };
 
+// One tile of a pass over all classes of a plan: 128 / D regions of class k (128 for k = 1),
+// with the per-region code of the per-class kernels.
+template <int KMAX>
+__device__ __forceinline__ void plan_tile(const DevProblem& P, const PersistPlan& L, const PassIO& io, const Thetas& T,
+                                          const int64_t tile) {
+    // class of this tile, with compile-time indices into the plan (no local copy of it)
+    int k = L.k[0];
+    const int32_t* cls = L.cls[0];
+    int32_t count = L.count[0];
+    int64_t first = L.tile0[0];
+#pragma unroll
+    for (int q = 1; q < kPersistClasses; ++q)
+        if (q < L.n_classes && tile >= L.tile0[q]) { k = L.k[q]; cls = L.cls[q]; count = L.count[q]; first = L.tile0[q]; }
+    const int64_t lt = tile - first;
+    if (k == 1) {
+        region_d2_unit(P, io, T, cls, count, lt * kBlock + threadIdx.x);
+    } else if (k == 2) {
+        region_pass_impl<4, kBlock>(P, io, cls, count, 2, lt);
+    } else if (k == 3) {
+        if constexpr (KMAX >= 3) region_pass_impl<8, kBlock>(P, io, cls, count, 3, lt);
+    } else {
+        if constexpr (KMAX >= 4) region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
+    }
+}
+
+// One region pass of every class in one ordinary launch (one CTA per tile): the alternative to
+// one launch per class on forked streams; same per-region code, same results.
+template <int KMAX>
+__global__ void __launch_bounds__(kBlock) __maxnreg__(PersistCap<KMAX>::v)
+    class_pass_kernel(const DevProblem P, const PersistPlan L, const PassIO io) {
+    if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
+    const Thetas T = pass_thetas(P, io);
+    plan_tile<KMAX>(P, L, io, T, blockIdx.x);
+}
+
 template <int KMAX>
 __global__ void __launch_bounds__(kBlock) __maxnreg__(PersistCap<KMAX>::v)
     persist_kernel(const DevProblem P, const PersistPlan L) {
@@ -740,26 +782,7 @@ __global__ void __launch_bounds__(kBlock) __maxnreg__(PersistCap<KMAX>::v)
             io.tr_out = P.tr;
         }
         const Thetas T = pass_thetas(P, io);
-        for (int64_t tile = blockIdx.x; tile < L.tiles; tile += gridDim.x) {
-            // class of this tile, with compile-time indices into the plan (no local copy of it)
-            int k = L.k[0];
-            const int32_t* cls = L.cls[0];
-            int32_t count = L.count[0];
-            int64_t first = L.tile0[0];
-#pragma unroll
-            for (int q = 1; q < kPersistClasses; ++q)
-                if (q < L.n_classes && tile >= L.tile0[q]) { k = L.k[q]; cls = L.cls[q]; count = L.count[q]; first = L.tile0[q]; }
-            const int64_t lt = tile - first;
-            if (k == 1) {
-                region_d2_unit(P, io, T, cls, count, lt * kBlock + threadIdx.x);
-            } else if (k == 2) {
-                region_pass_impl<4, kBlock>(P, io, cls, count, 2, lt);
-            } else if (k == 3) {
-                if constexpr (KMAX >= 3) region_pass_impl<8, kBlock>(P, io, cls, count, 3, lt);
-            } else {
-                if constexpr (KMAX >= 4) region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
-            }
-        }
+        for (int64_t tile = blockIdx.x; tile < L.tiles; tile += gridDim.x) plan_tile<KMAX>(P, L, io, T, tile);
         if (!grid_sync(P.err, L.bar, L.expect)) return;
         if (!L.nesterov) {
             const int par = (L.par0 + j) & 1;
@@ -787,6 +810,8 @@ template <int KMAX>
 cudaError_t persist_prepare(int* blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(persist_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)persist_smem<KMAX>());
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(class_pass_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)persist_smem<KMAX>());
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, persist_kernel<KMAX>, kBlock, persist_smem<KMAX>());
 }
@@ -937,6 +962,17 @@ cudaError_t persistent_prepare(int kmax, int* blocks_per_sm) {
         case 4: return persist_prepare<4>(blocks_per_sm);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_class_pass(const DevProblem& P, const PersistPlan& L, int kmax, const PassIO& io, cudaStream_t s) {
+    const unsigned grid = (unsigned)L.tiles;
+    switch (kmax) {
+        case 2: class_pass_kernel<2><<<grid, kBlock, persist_smem<2>(), s>>>(P, L, io); break;
+        case 3: class_pass_kernel<3><<<grid, kBlock, persist_smem<3>(), s>>>(P, L, io); break;
+        case 4: class_pass_kernel<4><<<grid, kBlock, persist_smem<4>(), s>>>(P, L, io); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_persistent(const DevProblem& P, const PersistPlan& Lin, int kmax, int grid, cudaStream_t s,

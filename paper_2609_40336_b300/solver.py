@@ -137,7 +137,7 @@ class Solver:
                     lambda_G=inf.lambda_G, gamma_G=inf.gamma_G, iteration=inf.iteration,
                     class_sites=list(inf.class_sites[:nc]), class_regions=list(inf.class_regions[:nc]),
                     sweeps=[int(x) for x in inf.sweeps[:nc]], class_block=list(inf.class_block[:nc]),
-                    concurrent_classes=bool(inf.concurrent_classes), loop=_LOOP_NAMES[inf.loop],
+                    concurrent_classes=int(inf.concurrent_classes), loop=_LOOP_NAMES[inf.loop],
                     persistent_grid=inf.persistent_grid, persistent_tiles=inf.persistent_tiles)
 
     def pairs(self):
@@ -186,6 +186,10 @@ class Solver:
     def launch_region_pass(self, k_sites: int) -> None:
         """Region pass of one size class only (no update); used to time the dominant kernel."""
         L.check(self._lib.lrh_launch_region_pass(self._h, int(k_sites)), "lrh_launch_region_pass")
+
+    def set_class_mode(self, mode: int) -> None:
+        """0: classes one after another, 1: forked streams, 2: all classes in one launch."""
+        L.check(self._lib.lrh_set_class_mode(self._h, int(mode)), "lrh_set_class_mode")
 
     def selftest_barrier_timeout(self) -> int:
         """Run the persistent driver's bounded-wait self-test (see lrh_selftest_barrier_timeout);

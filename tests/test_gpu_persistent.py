@@ -148,3 +148,32 @@ def test_barrier_wait_times_out_and_problem_stays_usable():
     b.step(6)
     assert np.array_equal(a.messages("nu"), b.messages("nu"))
     assert np.array_equal(a.bound("certified"), b.bound("certified"))
+
+
+@pytest.mark.parametrize("name", ["heis8x8_level1", "chain_L4_D16", "xxz_tri4_plaq"])
+def test_one_launch_class_pass_bitwise_equals_forked_streams(name):
+    """All classes of a pass in one launch (class mode 2) against forked streams and one
+    class after another, through the graph driver."""
+    p = ELIGIBLE[name]()
+    P = Poset(p.regions)
+    nu = random_traceless_messages(P, p.n_instances, seed=24, scale=0.4)
+    runs = []
+    for mode in (2, 1, 0):
+        s = Solver(p, beta=4.0, loop="graph")
+        s.set_class_mode(mode)
+        assert s.info()["concurrent_classes"] == mode
+        s.set_messages("nu", nu)
+        s.restart()
+        s.step(3)
+        s.step(14)
+        runs.append(s)
+    for s in runs[1:]:
+        for which in ("nu", "zeta"):
+            assert np.array_equal(runs[0].messages(which), s.messages(which)), which
+
+
+def test_one_launch_class_pass_unavailable_with_a_32x32_class():
+    s = Solver(L.random_chain(23, 9, L=5, scale=0.4))
+    with pytest.raises(_lib.LrhError) as e:
+        s.set_class_mode(2)
+    assert e.value.code == -8
