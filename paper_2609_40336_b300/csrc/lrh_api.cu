@@ -1115,22 +1115,23 @@ int cache_lookup(const std::vector<std::pair<std::string, int>>& c, const std::s
 // Time `reps` calls of fn on the problem's stream with CUDA events (milliseconds per call).
 template <typename F>
 int time_ms(lrh_problem* p, int reps, F fn, float* ms) {
-    cudaEvent_t a, b;
-    LRH_CK(cudaEventCreate(&a));
-    LRH_CK(cudaEventCreate(&b));
-    int rc = fn();
-    if (!rc) {
-        LRH_CK(cudaEventRecord(a, p->stream));
-        for (int i = 0; i < reps && !rc; ++i) rc = fn();
-        LRH_CK(cudaEventRecord(b, p->stream));
-        LRH_CK(cudaEventSynchronize(b));
-        float t = 0;
-        LRH_CK(cudaEventElapsedTime(&t, a, b));
-        *ms = t / reps;
-    }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
-    return rc;
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+    } ev;
+    LRH_CK(cudaEventCreate(&ev.a));
+    LRH_CK(cudaEventCreate(&ev.b));
+    int rc = fn();   // warm-up (and graph capture)
+    if (rc) return rc;
+    LRH_CK(cudaEventRecord(ev.a, p->stream));
+    for (int i = 0; i < reps && !rc; ++i) rc = fn();
+    if (rc) return rc;
+    LRH_CK(cudaEventRecord(ev.b, p->stream));
+    LRH_CK(cudaEventSynchronize(ev.b));
+    float t = 0;
+    LRH_CK(cudaEventElapsedTime(&t, ev.a, ev.b));
+    *ms = t / reps;
+    return LRH_OK;
 }
 
 }  // namespace

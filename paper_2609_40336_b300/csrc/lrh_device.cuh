@@ -136,9 +136,10 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
         if (__all_sync(kFull, done)) break;
         ++sweeps;
         // One round of the tournament: pair parameters from (xr, xi), column rotations of
-        // (xr, xi) and V in place, and the row rotation with the tournament permutation into
-        // (yr, yi).  Rounds alternate between the two register arrays (no copies).
-        auto round = [&](T (&xr)[D], T (&xi)[D], T (&yr)[D], T (&yi)[D]) {
+        // (xr, xi) and of V (ur, ui) in place, the row rotation with the tournament permutation
+        // into (yr, yi) and V's column permutation into (wr_, wi_).  Rounds alternate between
+        // the two register arrays of each matrix (no copies).
+        auto round = [&](T (&xr)[D], T (&xi)[D], T (&yr)[D], T (&yi)[D], T (&ur)[D], T (&ui)[D], T (&wr_)[D], T (&wi_)[D]) {
             // (1) parameters of pair k = s >> 1 (both lanes of the pair compute them from the
             //     same shuffled values, so they agree bit for bit)
             T e0r, e1r, e0i, e1i;
@@ -162,7 +163,7 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
             for (int k = 0; k < D / 2; ++k) {
                 const Rot<T> P = prm[k];
                 mix_cols(xr[2 * k], xi[2 * k], xr[2 * k + 1], xi[2 * k + 1], P.c, P.wr, P.wi);
-                if (WANT_V) mix_cols(vr[2 * k], vi[2 * k], vr[2 * k + 1], vi[2 * k + 1], P.c, P.wr, P.wi);
+                if (WANT_V) mix_cols(ur[2 * k], ui[2 * k], ur[2 * k + 1], ui[2 * k + 1], P.c, P.wr, P.wi);
             }
             // (3) row rotation fused with the tournament permutation of rows and columns:
             //     new A[s][c] = (J^H A)[o][rr_src(c)] with o = rr_src(s); for an odd source row
@@ -183,24 +184,25 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
                 yi[cc] = Q.c * r1i + (qwr * r2i + qwi * r2r);
             }
             if (WANT_V) {
-                T tr_[D], ti_[D];
 #pragma unroll
-                for (int cc = 0; cc < D; ++cc) { tr_[cc] = vr[rr_src(cc, D)]; ti_[cc] = vi[rr_src(cc, D)]; }
-#pragma unroll
-                for (int cc = 0; cc < D; ++cc) { vr[cc] = tr_[cc]; vi[cc] = ti_[cc]; }
+                for (int cc = 0; cc < D; ++cc) { wr_[cc] = ur[rr_src(cc, D)]; wi_[cc] = ui[rr_src(cc, D)]; }
             }
             __syncwarp();
         };
-        T br_[D], bi_[D];
+        T br_[D], bi_[D], ubr[D], ubi[D];
 #pragma unroll 1
         for (int r = 0; r + 1 < D - 1; r += 2) {
-            round(ar, ai, br_, bi_);
-            round(br_, bi_, ar, ai);
+            round(ar, ai, br_, bi_, vr, vi, ubr, ubi);
+            round(br_, bi_, ar, ai, ubr, ubi, vr, vi);
         }
-        // D - 1 rounds per sweep is odd: the last one lands in (br_, bi_)
-        round(ar, ai, br_, bi_);
+        // D - 1 rounds per sweep is odd: the last one lands in (br_, bi_) and (ubr, ubi)
+        round(ar, ai, br_, bi_, vr, vi, ubr, ubi);
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) { ar[cc] = br_[cc]; ai[cc] = bi_[cc]; }
+        if (WANT_V) {
+#pragma unroll
+            for (int cc = 0; cc < D; ++cc) { vr[cc] = ubr[cc]; vi[cc] = ubi[cc]; }
+        }
     }
     return sweeps;
 }
