@@ -720,6 +720,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     }
     // size classes
     for (int k = 0; k < 8; ++k) P.class_base[k] = -1;
+    P.class_uniform = 0;
     for (int k = 1; k <= kMaxSites; ++k) {
         std::vector<int32_t> lst;
         for (int e = 0; e < R; ++e) if ((int)regs[e].size() == k) lst.push_back(e);
@@ -733,6 +734,20 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         bool contiguous = true;
         for (size_t i = 1; i < lst.size(); ++i) contiguous = contiguous && lst[i] == lst[0] + (int32_t)i;
         P.class_base[k] = contiguous ? lst[0] : -1;
+        // uniform class: every record is the first one shifted (checked field by field)
+        bool uniform = contiguous;
+        const int64_t D2 = (int64_t)1 << (2 * k);
+        for (size_t i = 0; uniform && i < lst.size(); ++i) {
+            const RegionInfo u = uniform_region(rinfo[lst[0]], (int64_t)i, D2);
+            const RegionInfo& g = rinfo[lst[i]];
+            uniform = u.h_off == g.h_off && u.rho_off == g.rho_off && u.child_begin == g.child_begin &&
+                      u.child_end == g.child_end && u.parent_begin == g.parent_begin && u.parent_end == g.parent_end &&
+                      u.all_off == g.all_off;
+        }
+        if (uniform) {
+            P.class_first[k] = rinfo[lst[0]];
+            P.class_uniform |= 1 << k;
+        }
     }
     // most expensive class first (it stays on the problem's stream)
     {

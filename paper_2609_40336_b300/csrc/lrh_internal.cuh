@@ -72,6 +72,20 @@ struct PassIO {
     int32_t pad;
 };
 
+// Record of region i of a uniform class of size D (see DevProblem::class_first).
+__host__ __device__ inline RegionInfo uniform_region(const RegionInfo& f, int64_t i, int64_t D2) {
+    RegionInfo R = f;
+    const int32_t nc = f.child_end - f.child_begin, np = f.parent_end - f.parent_begin;
+    R.child_begin = f.child_begin + (int32_t)(i * nc);
+    R.child_end = R.child_begin + nc;
+    R.parent_begin = f.parent_begin + (int32_t)(i * np);
+    R.parent_end = R.parent_begin + np;
+    if (f.h_off >= 0) R.h_off = f.h_off + i * D2;
+    if (f.rho_off >= 0) R.rho_off = f.rho_off + i * D2;
+    R.all_off = f.all_off + i * D2;
+    return R;
+}
+
 // Error bits raised by kernels.
 enum : int32_t { DEV_ERR_NUMERIC = 1, DEV_ERR_TIMEOUT = 2 };
 
@@ -92,6 +106,12 @@ struct DevProblem {
     const PairInfo* child_info;  // PairInfo in child CSR order (child_pairs[q] resolved)
     const PairInfo* parent_info; // PairInfo in parent CSR order
     int32_t class_base[8];       // [k]: first region id when the class of k sites is a contiguous id range, else -1
+    // [k]: record of the class's first region when every region r = class_base[k] + i of the class
+    // has the record of the first shifted by i (child / parent ranges by their lengths, term and
+    // state offsets by D^2 where present); lets the small-region passes build the record without
+    // a dependent load.  class_uniform bit k marks such classes.
+    RegionInfo class_first[8];
+    int32_t class_uniform;
     const float2* h32;     // [n_inst][h_elems]
     const double2* h64;    // [n_inst][h_elems]
     float2* nu;            // [n_inst][msg_elems]

@@ -81,7 +81,13 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
     float ar[D], ai[D], vr[D], vi[D];
     RegionInfo R;
     if (valid) {
-        R = P.reg[r];
+        if constexpr (D <= 8) {   // uniform class: the region record without a dependent load
+            constexpr int KD = D == 4 ? 2 : 3;
+            R = ((P.class_uniform >> KD) & 1) ? uniform_region(P.class_first[KD], r - P.class_base[KD], (int64_t)D * D)
+                                               : P.reg[r];
+        } else {
+            R = P.reg[r];
+        }
         assemble_row_io<D>(P, R, inst, s, io, T, ar, ai);
     } else {
         R = RegionInfo{-1, -1, 0, 0, 0, 0, 0};
@@ -223,7 +229,7 @@ __device__ __forceinline__ void region_d2_unit(const DevProblem& P, const PassIO
     const int inst = (int)(unit / count);
     const int r = P.class_base[1] >= 0 ? P.class_base[1] + (int)(unit % count) : cls[unit % count];
     const bool nest = P.st->variant == 1;
-    const RegionInfo R = P.reg[r];
+    const RegionInfo R = ((P.class_uniform >> 1) & 1) ? uniform_region(P.class_first[1], r - P.class_base[1], 4) : P.reg[r];
     float a = 0.f, d = 0.f, br = 0.f, bi = 0.f;
     if (R.h_off >= 0) {
         const float2* h = P.h32 + (int64_t)inst * P.h_elems + R.h_off;
