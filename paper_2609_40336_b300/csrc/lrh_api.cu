@@ -1149,6 +1149,18 @@ int time_ms(lrh_problem* p, int reps, F fn, float* ms) {
     return LRH_OK;
 }
 
+// time_ms with enough repetitions for about `min_ms` of timed work (at least 2, at most 200):
+// one call estimates the cost, so that microsecond-scale candidates are not compared on noise.
+template <typename F>
+int time_adaptive(lrh_problem* p, float min_ms, F fn, float* ms) {
+    float est = 0.f;
+    int rc = time_ms(p, 1, fn, &est);
+    if (rc) return rc;
+    int reps = est > 0.f ? (int)std::ceil(min_ms / est) : 200;
+    reps = std::max(2, std::min(200, reps));
+    return time_ms(p, reps, fn, ms);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1174,7 +1186,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
                     int rc = lrh_set_launch_shape(p, k, cand);
                     if (rc) return rc;
                     float ms = 0;
-                    rc = time_ms(p, 2, [&]() -> int {
+                    rc = time_adaptive(p, 2.0f, [&]() -> int {
                         LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, 0));
                         return LRH_OK; }, &ms);
                     if (rc) return rc;
@@ -1195,7 +1207,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
                 if (cand > 0 && cand < (1 << k)) continue;
                 if (cand < 0 && k != 2) continue;   // thread-per-region layout: 4 x 4 regions
                 float ms = 0;
-                int rc = time_ms(p, 3, [&]() -> int {
+                int rc = time_adaptive(p, 2.0f, [&]() -> int {
                     LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, cand));
                     return LRH_OK; }, &ms);
                 if (rc) return rc;
@@ -1265,7 +1277,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
                 p->fused = mode == 2;
                 drop_graphs(p);
                 float ms = 0;
-                rc = time_ms(p, 2, [&]() { return lrh_step(p, kTuneIters); }, &ms);
+                rc = time_adaptive(p, 4.0f, [&]() { return lrh_step(p, kTuneIters); }, &ms);
                 const int rc2 = copy_all(false);
                 p->iteration = saved_it;
                 if (rc || rc2) {
