@@ -349,3 +349,154 @@ def test_subgradient_bound_below_e0_tfim():
     st = dual.run_subgradient(P, h, 300)
     q0 = dual.dual_value(P, h, dual.zeros_messages(P, 1))[0]
     assert st.q_best[0] <= E0 and st.q_best[0] > q0 + 1.0
+
+
+# ---------------------------------------------------------------- Alg. 2 update form, by hand
+def _classical_edge_problem():
+    """One edge (0, 1) with a diagonal term and diagonal site terms: every theta, Gibbs state
+    and gradient stays diagonal, and with traceless diagonal messages x Z (edge -> site 0) and
+    y Z (edge -> site 1) the whole iteration reduces to two real numbers."""
+    e = np.array([0.3, -1.1, 0.7, 0.2])        # basis |00>, |01>, |10>, |11>
+    h0 = np.array([0.25, -0.4])
+    h1 = np.array([-0.1, 0.35])
+    p = g.Problem(2, [(0, 1), (0,), (1,)], [(0, 1), (0,), (1,)],
+                  [np.diag(e).astype(complex)[None], np.diag(h0).astype(complex)[None],
+                   np.diag(h1).astype(complex)[None]])
+    return p, e, h0, h1
+
+
+def _hand_gibbs(diag, beta):
+    w = [np.exp(-beta * (v - min(diag))) for v in diag]
+    z = sum(w)
+    return [x / z for x in w], min(diag) - np.log(z) / beta
+
+
+def _hand_smoothed_pass(x, y, e, h0, h1, beta):
+    """Q_beta and the Z-components of g_{e->0}, g_{e->1} at messages x Z, y Z, from scalars
+    only: theta_e[ab] = e_ab - x z_a - y z_b (z_0 = 1, z_1 = -1), theta_0 = h0 + x Z,
+    theta_1 = h1 + y Z; Gibbs states of diagonal matrices are softmaxes of the diagonal."""
+    z = (1.0, -1.0)
+    te = [e[2 * a + b] - x * z[a] - y * z[b] for a in (0, 1) for b in (0, 1)]
+    re, fe = _hand_gibbs(te, beta)
+    r0, f0 = _hand_gibbs([h0[0] + x, h0[1] - x], beta)
+    r1, f1 = _hand_gibbs([h1[0] + y, h1[1] - y], beta)
+    marg0 = re[0] + re[1]            # <0| Tr_1 rho_e |0>
+    marg1 = re[0] + re[2]            # <0| Tr_0 rho_e |0>
+    return fe + f0 + f1, r0[0] - marg0, r1[0] - marg1
+
+
+def test_nesterov_three_steps_by_hand():
+    """Alg. 2 from nu = zeta = 0, theta_0 = 1: eta = (1 - theta) nu + theta zeta, gradient at
+    eta, zeta += g / (theta L_hat), nu = (1 - theta) nu + theta zeta, theta update.  The first
+    two iterations have eta = nu = zeta; the third is the first where eta differs from nu, so
+    three steps fix the whole update."""
+    p, e, h0, h1 = _classical_edge_problem()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    beta, lhat = 3.0, 2.5
+    st = dual.NesterovState(nu=dual.zeros_messages(P, 1), zeta=dual.zeros_messages(P, 1))
+    nx = ny = zx = zy = 0.0
+    th = 1.0
+    for _ in range(3):
+        ex, ey = (1 - th) * nx + th * zx, (1 - th) * ny + th * zy
+        q, gx, gy = _hand_smoothed_pass(ex, ey, e, h0, h1, beta)
+        zx, zy = zx + gx / (th * lhat), zy + gy / (th * lhat)
+        nx, ny = (1 - th) * nx + th * zx, (1 - th) * ny + th * zy
+        th = (np.sqrt(th ** 4 + 4 * th ** 2) - th ** 2) / 2
+        res = dual.nesterov_step(P, h, st, beta, lhat)
+        assert abs(res.value.sum() - q) < 1e-12
+        for arr, (a, b) in ((st.nu, (nx, ny)), (st.zeta, (zx, zy))):
+            want = np.array([a, 0, 0, -a, b, 0, 0, -b], complex)     # x Z then y Z, row-major
+            assert np.abs(arr[0] - want).max() < 1e-12
+        assert abs(st.theta - th) < 1e-15
+    assert abs(nx - zx) > 1e-3          # the three steps did separate nu from zeta
+
+
+def test_nesterov_rate_of_the_accelerated_corollary():
+    """Thm 5 (its proof cites Tseng's corollary): Q_beta* - Q_beta(nu_T) <= 2 L_hat R^2 / (T+1)^2
+    with L_hat = beta Lambda / 2 and R = ||nu_beta* - nu_0||.  On this chain plain gradient ascent
+    with step 1/L_hat exceeds the bound by up to 2x at T = 40 .. 160, so the test fixes the
+    accelerated form, not only convergence."""
+    p = L.random_chain(5, 5, L=2, scale=1.0)
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    beta = 8.0
+    lhat = beta * P.lipschitz_lambda() / 2
+    st = dual.NesterovState(nu=dual.zeros_messages(P, 1), zeta=dual.zeros_messages(P, 1))
+    q = []
+    for _ in range(4000):
+        dual.nesterov_step(P, h, st, beta, lhat)
+        if len(q) < 160:
+            q.append(dual.smoothed_value(P, h, st.nu, beta)[0])
+    qstar = dual.smoothed_value(P, h, st.nu, beta)[0]
+    R2 = float(np.sum(np.abs(st.nu) ** 2))
+    for T in (5, 10, 20, 40, 80, 160):
+        assert qstar - q[T - 1] <= 2 * lhat * R2 / (T + 1) ** 2
+
+
+# ---------------------------------------------------------------- Alg. 1 step rule, by hand
+def test_subgradient_inv_sqrt_steps_by_hand():
+    """Alg. 1 with alpha_t = alpha / sqrt(t + 1) on the classical edge: ground states of
+    diagonal matrices are basis states, the degenerate site Hamiltonian at x = 0 gives the
+    uniform mixture I/2, and every update is nu += alpha_t (mu_f - Tr mu_e).  Six steps
+    computed from scalars fix the rule (1/(t+1) or a constant step differ from t = 2 on),
+    q_best and nu_best; a field on site 1 against the edge's ground state keeps the
+    subgradient from vanishing after the first step."""
+    p, e, _, _ = _classical_edge_problem()
+    f1 = np.array([-0.45, 0.6])     # site-1 field against the edge's ground state |01>: frustration
+    p = g.Problem(2, [(0, 1), (0,), (1,)], [(0, 1), (1,)],
+                  [np.diag(e).astype(complex)[None], np.diag(f1).astype(complex)[None]])
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    alpha, tol = 0.7, 1e-9
+    st = dual.SubgradientState(nu=dual.zeros_messages(P, 1))
+    x = y = 0.0
+    qb, xb, yb = -np.inf, 0.0, 0.0
+    z = (1.0, -1.0)
+
+    def site_ground(d0, d1):       # <0|mu|0> for diag(d0, d1): 1, 0, or 1/2 when degenerate
+        if abs(d1 - d0) <= tol * max(1.0, np.hypot(d0, d1)):
+            return 0.5
+        return 1.0 if d0 < d1 else 0.0
+
+    for t in range(6):
+        te = [e[2 * a + b] - x * z[a] - y * z[b] for a in (0, 1) for b in (0, 1)]
+        k = int(np.argmin(te))
+        q = min(te) - abs(x) + min(f1[0] + y, f1[1] - y)
+        gx = site_ground(x, -x) - (1.0 if k in (0, 1) else 0.0)
+        gy = site_ground(f1[0] + y, f1[1] - y) - (1.0 if k in (0, 2) else 0.0)
+        if q > qb:
+            qb, xb, yb = q, x, y
+        at = alpha / np.sqrt(t + 1.0)
+        x, y = x + at * gx, y + at * gy
+        dual.subgradient_step(P, h, st, "sqrt", alpha, tol)
+        assert abs(st.history[-1][0] - q) < 1e-12
+        assert np.abs(st.nu[0] - np.array([x, 0, 0, -x, y, 0, 0, -y])).max() < 1e-12
+        assert abs(st.q_best[0] - qb) < 1e-12
+        assert np.abs(st.nu_best[0] - np.array([xb, 0, 0, -xb, yb, 0, 0, -yb])).max() < 1e-12
+
+
+# ---------------------------------------------------------------- degenerate ground spaces
+@pytest.mark.parametrize("spectrum,mult", [((-1, -1, 1, 1), 2), ((-2, -2, -2, 0.5), 3), ((-1, 0, 0.5, 2), 1)])
+def test_ground_mixture_is_the_normalised_ground_projector(spectrum, mult):
+    """Alg. 1's sampled ground state, read as the uniform mixture over the ground space, is the
+    ground-space projector divided by its rank, whatever eigenbasis the solver returns inside
+    the degenerate space: theta = U diag(spectrum) U^dagger has mixture U P U^dagger / mult."""
+    rng = np.random.default_rng(17)
+    U = L.random_unitary(rng, 4)
+    th = U @ np.diag(np.array(spectrum, float)) @ U.conj().T
+    p = g.Problem(2, [(0, 1)], [(0, 1)], [(0.5 * (th + th.conj().T))[None]])
+    P = Poset(p.regions)
+    res = dual.region_pass(P, dual.local_terms(p, P), dual.zeros_messages(P, 1), "ground", tol=1e-9)
+    proj = np.diag([1.0 if s == min(spectrum) else 0.0 for s in spectrum])
+    assert np.abs(res.states[2][0, 0] - U @ proj @ U.conj().T / mult).max() < 1e-12
+    assert abs(res.value[0, 0] - min(spectrum)) < 1e-12
+
+
+def test_near_degenerate_level_outside_the_tolerance_is_excluded():
+    """A level 1e-6 above lambda_min is outside tol = 1e-9 * max(1, ||theta||_F): pure state."""
+    th = np.diag([-1.0, -1.0 + 1e-6, 0.3, 0.9]).astype(complex)
+    p = g.Problem(2, [(0, 1)], [(0, 1)], [th[None]])
+    P = Poset(p.regions)
+    res = dual.region_pass(P, dual.local_terms(p, P), dual.zeros_messages(P, 1), "ground", tol=1e-9)
+    assert np.abs(res.states[2][0, 0] - np.diag([1.0, 0, 0, 0])).max() < 1e-12
