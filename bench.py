@@ -1,18 +1,23 @@
-"""Benchmark: 2D Heisenberg antiferromagnet, periodic 64 x 64, level-1 relaxation
-(8192 edge regions 4x4 + 4096 site regions 2x2), accelerated smoothing (Alg. 2) under
-beta continuation beta = 1, 2, ..., 1024 with 200 iterations per stage, FP32 eigensolves,
-FP64 bound reduction and FP64 certification of the final bound.
+"""Benchmark: 256 XXZ instances on the periodic 32 x 32 triangular lattice (Jxy = 1, Jz ~ U[0, 2]
+per instance), rhombic 2 x 2 plaquettes (16 x 16) + bonds (4 x 4) + sites (2 x 2) as the region
+family, all instances batched in one problem; accelerated smoothing (Alg. 2) under beta
+continuation beta = 1, 2, ..., 1024 with 200 iterations per stage, FP32 eigensolves, FP64 bound
+reduction and FP64 certification of the final bound.
 
-One step = one whole solve from nu = 0 (11 x 200 = 2200 iterations over all 12288
-regions) plus the certified bound.  Metric: region eigensolves per second (regions x
-iterations / time); the JSON line also carries the certified bound per site, the gap to
-a converged reference value, the time to a 1e-4/site gap, the roofline of the dominant
-kernel, the plain FP64 GPU comparator and the CPU oracle baseline.
+One step = one whole solve of every instance from nu = 0 (11 x 200 = 2200 iterations over all
+256 x 5120 regions) run by the library (lrh_reset + lrh_solve), ending with the certified bound
+read back to the host.  Metric: region eigensolves per second (regions x iterations / time).  The
+JSON line also carries the time to a certified 1e-4 / site gap (against converged FP64 oracle
+values of four instances), the roofline of the dominant kernel, the plain FP64 GPU comparator
+and the CPU oracle baselines (one core and all host cores).  Other workloads (--workload): the
+configurations of the hot-path table (64 x 64 Heisenberg, TFIM chain, perturbed chain L = 4..7,
+J1-J2 48 x 48).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrh|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lrh|reference] [--workload NAME]
 
-Multi-GPU: one process per GPU (torchrun); every rank solves its own copy of the
-workload (independent problems, no collective on the data path: weak scaling).
+Multi-GPU (torchrun, one process per GPU): the batched workload is sharded by instance, rank r
+solving instances [256 r, 256 r + 256) of a family of 256 N instances (weak scaling, no
+collective on the data path); single-instance workloads run one independent copy per GPU.
 """
 from __future__ import annotations
 
@@ -34,10 +39,10 @@ if ROOT not in sys.path:
 import lrh_gen as g  # noqa: E402
 
 BETAS11 = [2.0 ** s for s in range(11)]
-CERT_EVERY = 25
 METRIC = "region eigensolves/s (time-to-1e-4/site bound, vs plain FP64 GPU path)"
 FP32_LANES_PER_SM = 128
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+BATCH = 256   # instances per GPU of the batched workload
 
 
 class Workload:
@@ -45,30 +50,44 @@ class Workload:
     from nu = 0 followed by the certified bound) and the dominant region class."""
 
     def __init__(self, name, build, variant, betas=None, iters_per_stage=200, iters=0, alpha=1.0,
-                 step_rule="inv_sqrt", dominant_k=2, golden=None, note=""):
+                 step_rule="inv_sqrt", dominant_k=2, golden=None, note="", cert_every=25, sharded=False):
         self.name, self.build, self.variant = name, build, variant
         self.betas, self.iters_per_stage, self.iters = betas, iters_per_stage, iters
         self.alpha, self.step_rule, self.dominant_k = alpha, step_rule, dominant_k
-        self.golden, self.note = golden, note
+        self.golden, self.note, self.cert_every, self.sharded = golden, note, cert_every, sharded
 
     def n_iterations(self):
         return len(self.betas) * self.iters_per_stage if self.variant == "nesterov" else self.iters
+
+    def problem(self, rank=0, world=1):
+        """This rank's problem: for a sharded (batched) workload, instances [BATCH rank, BATCH
+        (rank + 1)) of the family of BATCH * world instances; else the whole workload."""
+        if not self.sharded:
+            return self.build()
+        full = self.build(BATCH * world)
+        if world == 1:
+            return full
+        lo = BATCH * rank
+        return g.Problem(full.n_sites, full.regions, full.term_sites, [m[lo:lo + BATCH] for m in full.term_mats],
+                         meta=dict(full.meta, instances=[lo, lo + BATCH]))
 
 
 def workloads():
     L = g.lattices
     w = {
-        "heisenberg64": Workload("heisenberg_square_64x64_periodic_level1_nesterov_beta1-1024",
-                                 lambda: L.heisenberg_square(64), "nesterov", BETAS11, 200, dominant_k=2,
-                                 golden="heisenberg64_level1_fstar.json"),
-        "tfim16": Workload("tfim_open_chain_n16_level1_subgradient_2000_inv_sqrt",
-                           lambda: L.tfim_chain(16, 1001), "subgradient", iters=2000, alpha=1.0,
-                           step_rule="inv_sqrt", dominant_k=2, golden="tfim16_level1_fstar.json"),
         "xxz_tri32_x256": Workload("xxz_triangular_32x32_periodic_256_instances_plaquettes_nesterov_beta1-1024",
-                                   lambda: L.xxz_triangular(32, 256), "nesterov", BETAS11, 200, dominant_k=4),
+                                   lambda ni=BATCH: L.xxz_triangular(32, ni), "nesterov", BETAS11, 200, dominant_k=4,
+                                   golden="xxz_tri32_fstar.json", cert_every=100, sharded=True),
         "xxz_tri32_x32": Workload("xxz_triangular_32x32_periodic_32_instances_plaquettes_nesterov_beta1-1024",
                                   lambda: L.xxz_triangular(32, 32), "nesterov", BETAS11, 200, dominant_k=4,
                                   note="32 of the 256 instances (profiling size)"),
+        "heisenberg64": Workload("heisenberg_square_64x64_periodic_level1_nesterov_beta1-1024",
+                                 lambda: L.heisenberg_square(64), "nesterov", BETAS11, 200, dominant_k=2,
+                                 golden="heisenberg64_level1_fstar.json",
+                                 note="level-1 optimum at nu = 0 (fixed-point throughput test)"),
+        "tfim16": Workload("tfim_open_chain_n16_level1_subgradient_2000_inv_sqrt",
+                           lambda: L.tfim_chain(16, 1001), "subgradient", iters=2000, alpha=1.0,
+                           step_rule="inv_sqrt", dominant_k=2, golden="tfim16_level1_fstar.json"),
         "j1j2_48": Workload("j1j2_square_48x48_periodic_J2_0_0.25_0.5_plaquettes_nesterov_beta256",
                             lambda: L.j1j2_square(48), "nesterov", [256.0], 200, dominant_k=4,
                             golden="j1j2_48_fstar.json"),
@@ -82,21 +101,31 @@ def workloads():
     return w
 
 
-WL = None   # the selected Workload
+WL = None       # the selected Workload
+WL_KEY = "xxz_tri32_x256"
 
 
-def config(extra=None):
-    p_regions = getattr(WL, "_regions_by_D", {})
-    c = {"workload": WL.name, "regions": p_regions, "algorithm": WL.variant,
-         "iterations_per_step": WL.n_iterations(), "l2": "flushed between steps (256 MiB write)"}
+def regions_by_size(p):
+    out = {}
+    for r in p.regions:
+        key = f"{2 ** len(r)}x{2 ** len(r)}"
+        out[key] = out.get(key, 0) + p.n_instances
+    return dict(sorted(out.items(), key=lambda kv: -int(kv[0].split("x")[0])))
+
+
+def config(p, world):
+    """The workload (identical in both arms of the benchmark)."""
+    c = {"workload": WL.name, "regions_per_gpu": regions_by_size(p), "instances_per_gpu": p.n_instances,
+         "algorithm": WL.variant, "iterations_per_step": WL.n_iterations(),
+         "l2": "inputs larger than L2 (the message arrays and states of one pass exceed 126 MB)"
+         if WL.sharded else "flushed between steps (256 MiB write)",
+         "parallelism": (f"instances sharded over {world} GPU(s)" if WL.sharded else f"independent copy per GPU x{world}")}
     if WL.variant == "nesterov":
         c.update({"betas": [WL.betas[0], WL.betas[-1], len(WL.betas)], "iters_per_stage": WL.iters_per_stage})
     else:
         c.update({"alpha": WL.alpha, "step_rule": WL.step_rule})
     if WL.note:
         c["note"] = WL.note
-    if extra:
-        c.update(extra)
     return c
 
 
@@ -345,8 +374,8 @@ def next_theta(th):
 
 
 def time_fp64_comparator(p, device, seconds=5.0):
-    """Seconds per iteration of the plain FP64 comparator (warm-up 2 iterations, then as many
-    as fit in `seconds`, at least 3)."""
+    """Seconds per iteration of the plain FP64 comparator on instance 0 (warm-up 2 iterations,
+    then as many as fit in `seconds`, at least 3)."""
     import torch
     comp = TorchFP64Level1(p, device) if WL_KEY == "heisenberg64" else TorchFP64Poset(p, device)
     th = 1.0
@@ -362,26 +391,41 @@ def time_fp64_comparator(p, device, seconds=5.0):
     return (time.perf_counter() - t0) / n
 
 
+def next_theta(th):
+    return (np.sqrt(th ** 4 + 4 * th ** 2) - th ** 2) / 2
+
+
 # ---------------------------------------------------------------- CPU oracle baseline
-def cpu_problem():
-    """The workload itself, or for the largest ones a smaller member of the same family
-    (same regions and terms per site, fewer sites / instances) so that a bounded sample of
-    FP64 oracle iterations fits in seconds."""
+def cpu_problems():
+    """Problems of the oracle sample: the workload itself, or for the largest ones members of the
+    same family (same regions and terms per site, fewer sites or one instance per worker) so that
+    a bounded sample of FP64 oracle iterations fits in seconds."""
     L = g.lattices
     key = WL_KEY
     if key.startswith("chain4096_L"):
         Lint = int(key[-1])
         n = {4: 1024, 5: 256, 6: 32, 7: 12}[Lint]
-        return L.perturbed_chain(n, L=Lint, delta=0.1, seed=1003), f"same family with n={n} sites"
+        return (lambda i: L.perturbed_chain(n, L=Lint, delta=0.1, seed=1003)), f"same family with n={n} sites"
     if key in ("xxz_tri32_x256", "xxz_tri32_x32"):
-        return L.xxz_triangular(32, 4), "same lattice with 4 instances"
-    return WL.build(), "the full workload"
+        def one(i):
+            full = L.xxz_triangular(32, 256)
+            return g.Problem(full.n_sites, full.regions, full.term_sites, [m[i:i + 1] for m in full.term_mats])
+        return one, "one instance of the 256 per worker"
+    return (lambda i: WL.build()), "the full workload"
 
 
-def cpu_oracle_sample(seconds=12.0):
+def _oracle_worker(args):
+    """One host core: FP64 oracle iterations of the workload's algorithm for `seconds`."""
+    key, inst, seconds = args
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    global WL, WL_KEY
+    WL_KEY = key
+    WL = workloads()[key]
     from oracle import dual
     from oracle.poset import Poset
-    p, what = cpu_problem()
+    build, _ = cpu_problems()
+    p = build(inst)
     P = Poset(p.regions)
     h = dual.local_terms(p, P)
     I = p.n_instances
@@ -399,9 +443,27 @@ def cpu_oracle_sample(seconds=12.0):
         while time.perf_counter() - t0 < seconds:
             dual.subgradient_step(P, h, st, "sqrt", WL.alpha)
             n_it += 1
-    dt = time.perf_counter() - t0
-    R = len(p.regions) * I
-    return R * n_it / dt, f"{n_it} FP64 oracle iterations ({WL.variant}) over all {R} regions of {what}, {dt:.1f} s"
+    return len(p.regions) * I * n_it, time.perf_counter() - t0, n_it
+
+
+def cpu_oracle_sample(seconds, workers):
+    """The FP64 oracle as it stands on `workers` host cores (one process and one BLAS thread
+    each, spawned), each running the workload's iteration for `seconds`."""
+    import multiprocessing as mp
+    _, what = cpu_problems()
+    args = [(WL_KEY, i, seconds) for i in range(workers)]
+    t0 = time.perf_counter()
+    if workers == 1:
+        res = [_oracle_worker(args[0])]
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_oracle_worker, args)
+    wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    rate = sum(r[0] / r[1] for r in res)
+    its = sum(r[2] for r in res)
+    return rate, (f"{its} FP64 oracle iterations ({WL.variant}) on {workers} core(s), {what}, "
+                  f"about {seconds:.0f} s per core ({units} region eigensolves, {wall:.1f} s wall)")
 
 
 # ---------------------------------------------------------------- helpers
@@ -420,29 +482,355 @@ def load_fstar():
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on all host cores of this machine, on the same
+    workload, metric and unit (rank 0 only under torchrun)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    val, sample = cpu_oracle_sample(seconds=max(4.0, 4.0 * args.steps))
-    iters = WL.n_iterations()
-    n_reg = len(WL.build().regions) if WL_KEY != "xxz_tri32_x256" else 5120 * 256
-    line = {"metric": METRIC, "value": val, "unit": "region eigensolves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_reg * iters / val,
+    cores = os.cpu_count() or 1
+    per_core = max(4.0, min(20.0, 4.0 * args.steps))
+    val, sample = cpu_oracle_sample(per_core, cores)
+    p = WL.problem(0, ws)
+    units = sum(v for v in regions_by_size(p).values()) * WL.n_iterations()
+    line = {"metric": METRIC, "value": val * ws, "unit": "region eigensolves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * units / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(), "impl": "reference",
-            "cpu_baseline": {"value": val, "unit": "region eigensolves/s", "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": val, "unit": "region eigensolves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": config(p, ws), "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": "region eigensolves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "region eigensolves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "ms_per_step extrapolates the sampled rate to one whole solve of the workload"}
     print(json.dumps(line), flush=True)
+
+
+def max_over_ranks(x, device):
+    """Slowest rank's value (the job's time); identity on one process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, iters, steps, total_ms_max, world):
+    """Whole-job region eigensolves/s: every rank solves its own share (weak scaling)."""
+    return world * units_per_rank * iters * steps / (total_ms_max / 1e3)
+
+
+def make_solver(p, stream, tune_cache=None, certify_every=0):
+    from paper_2609_40336_b300 import Solver
+    common = dict(loop="auto", stream=stream.cuda_stream, tune_cache=tune_cache, certify_every=certify_every)
+    if WL.variant == "nesterov":
+        return Solver(p, variant="nesterov", beta=WL.betas[0], betas=WL.betas, iters_per_stage=WL.iters_per_stage,
+                      **common)
+    return Solver(p, variant="subgradient", alpha=WL.alpha, step_rule=WL.step_rule, iters_per_stage=WL.iters,
+                  **common)
+
+
+def solve(s):
+    """One step: nu = 0, the whole schedule inside the library, certified bound (host read)."""
+    s.reset()
+    return s.solve()["bound"]
+
+
+def launches_per_step(info):
+    """Kernels of the library per step: lrh_reset 1; per Alg. 2 stage 1 (restart) + the
+    iterations (graph: one pass per iteration, nc kernels or 1 with the one-launch class mode,
+    + final update + advance; persistent: 1 + 2); Alg. 1: 1 (restart) + per iteration a pass,
+    a reduction and an update, or 1 cooperative kernel; then nc certification kernels + 1
+    reduction."""
+    nc = len(info["class_sites"])
+    per_pass = 1 if info["concurrent_classes"] == 2 else nc
+    persistent = info["loop"] == "persistent"
+    if WL.variant == "nesterov":
+        body = 3 if persistent else WL.iters_per_stage * per_pass + 2
+        return 1 + len(WL.betas) * (1 + body) + nc + 1
+    body = 1 if persistent else WL.iters * (per_pass + 2)
+    return 1 + 1 + body + nc + 1
+
+
+def run_lrh(args, ws, rank, dev, stream):
+    import torch
+    import torch.distributed as dist
+    p = WL.problem(rank, ws)
+    tune = os.path.join(ROOT, "gpurun_out", f"tune_{WL_KEY}_rank{rank}.jsonl") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    s = make_solver(p, stream)
+    n_units = s.n_regions * s.n_instances
+    iters = WL.n_iterations()
+    flush = None if WL.sharded else torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tuned = None
+    # launch shapes picked on this problem after one untimed solve (a converged point: the pass
+    # costs there are those of the timed region, not of nu = 0), outside the timed region
+    if args.warmup == 0 and not args.no_autotune:
+        tuned = s.autotune(tune, force=True)
+    for w in range(args.warmup):
+        solve(s)
+        if w == 0 and not args.no_autotune:
+            tuned = s.autotune(tune, force=True)
+    if args.cta_bt:
+        for k in s.info()["class_sites"]:
+            if k >= 6:   # the tensor-core back-transform exists for 128 x 128 only
+                s.set_launch_shape(k, 2 if (args.cta_bt == "tensor" and k == 7) else 1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = []
+    bounds = None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bounds = solve(s)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks.stop()
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    value = job_throughput(n_units, iters, args.steps, total_ms, ws)
+    fstar = load_fstar()
+    extras = {}
+    info = s.info()
+    if rank == 0 and not args.no_extras:
+        extras = measure_extras(s, p, dev, stream, args, fstar, value, tune)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "region eigensolves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 bound reduction and certification)",
+                "data": "synthetic", "config": config(p, ws),
+                "launch": {"shapes": tuned, "loop_driver": info["loop"],
+                           "sweeps_capped": dict(zip(info["class_sites"], info["sweep_capped"]))},
+                "certified_bound_per_site": [float(b) / p.n_sites for b in bounds][:8],
+                "us_per_iteration": 1e3 * total_ms / args.steps / iters,
+                "wall_s_timed_region": wall, "clocks": clocks.summary(),
+                "gpu_launches": launches_per_step(info) * args.steps}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+KERNEL_SOURCES = ["lrh_kernels.cu", "lrh_device.cuh", "lrh_internal.cuh", "lrh_cta.cu", "lrh_block.cu", "lrh_block.cuh"]
+
+
+def kernel_source_hash(sources=None):
+    """First 16 hex digits of the SHA-256 of the listed kernel sources (default: all)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in (sources or KERNEL_SOURCES):
+        with open(os.path.join(ROOT, "paper_2609_40336_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(shape):
+    """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/traffic.json),
+    only while the sources that kernel is built from are the ones that capture measured and the
+    capture was of the same launch shape."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(WL_KEY)
+    if not rec or rec.get("kernel_sources_sha256_16") != kernel_source_hash(rec.get("sources")):
+        return None
+    if rec.get("launch_shape") is not None and rec["launch_shape"] != shape:
+        return None
+    return rec
+
+
+def fp32_peak(dev):
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    return sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12, \
+        f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)"
+
+
+def roofline(s, dev, stream, k):
+    """Dominant kernel: the region pass of class k, timed with CUDA events around a CUDA graph
+    of back-to-back launches on the library's stream (no host launch gaps)."""
+    import torch
+    peak, basis = fp32_peak(dev)
+    inf0 = s.info()
+    ci = inf0["class_sites"].index(k)
+    n_reg = inf0["class_regions"][ci] * s.n_instances
+    shape = inf0["class_block"][ci]
+    D = 2 ** k
+    reps = 20 if k >= 4 else 400
+    s.launch_region_pass(k)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for _ in range(reps):
+            s.launch_region_pass(k)
+    graph.replay()
+    torch.cuda.synchronize()
+    inf0 = s.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    graph.replay()
+    e1.record(stream)
+    e1.synchronize()
+    dur = e0.elapsed_time(e1) / reps * 1e-3
+    inf1 = s.info()
+    sweeps = (inf1["sweeps"][ci] - inf0["sweeps"][ci]) / (reps * n_reg)
+    fpr = 20 * sweeps * D * D * (D - 1) + 8 * D ** 3
+    achieved = n_reg * fpr / dur / 1e12
+    tr = recorded_traffic(shape)
+    return {"bound": "alu", "kernel": f"region pass, {n_reg} regions of {D}x{D}, launch shape {shape}",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "traffic_note": tr.get("note") if tr else "no ncu capture of the current kernel sources and shape",
+            "peak_basis": basis, "launch_us": dur * 1e6, "sweeps_per_region": sweeps, "flops_per_region": fpr,
+            "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger"}
+
+
+def roofline_persistent(s, dev, stream, n_iter):
+    """Dominant kernel under the persistent driver: one cooperative launch running n_iter
+    iterations of every class (timed with CUDA events on the library's stream around the
+    lrh_step call, which adds the small final-update and advance kernels)."""
+    import torch
+    peak, basis = fp32_peak(dev)
+    s.restart()
+    s.step(n_iter)                      # warm
+    s.restart()
+    torch.cuda.synchronize()
+    inf0 = s.info()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(n_iter)
+    e1.record(stream)
+    e1.synchronize()
+    dur = e0.elapsed_time(e1) * 1e-3
+    inf1 = s.info()
+    flops, parts = 0.0, []
+    for ci, k in enumerate(inf1["class_sites"]):
+        D = 2 ** k
+        regions = inf1["class_regions"][ci] * s.n_instances
+        if D == 2:
+            parts.append(f"{regions} regions of 2x2 (closed form, not counted)")
+            continue
+        sweeps = inf1["sweeps"][ci] - inf0["sweeps"][ci]
+        flops += 20.0 * sweeps * D * D * (D - 1) + 8.0 * D ** 3 * regions * n_iter
+        parts.append(f"{regions} regions of {D}x{D} ({sweeps / (regions * n_iter):.2f} sweeps)")
+    achieved = flops / dur / 1e12
+    return {"bound": "alu", "kernel": f"persist_kernel: {n_iter} iterations of " + ", ".join(parts),
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "traffic_note": "cooperative launch not captured with ncu (multi-pass replay of a grid barrier)",
+            "peak_basis": basis, "launch_us": dur * 1e6, "us_per_iteration": dur * 1e6 / n_iter,
+            "flop_model": "sum over classes of 20*S*D^2*(D-1) + 8*D^3 per region and iteration"}
+
+
+def time_to_target(s, p, fstar):
+    """Time until the FP64-certified bound is within 1e-3 / 1e-4 per site of the converged oracle
+    value on every instance that has one: the library's own schedule with a certified record every
+    cert_every iterations (lrh_solve; the certifications are inside the measured time)."""
+    ref = np.atleast_1d(np.asarray(fstar["fstar"], dtype=np.float64))
+    inst = np.asarray(fstar.get("instances", list(range(len(ref)))))
+    s.set_options(certify_every=WL.cert_every)
+    s.reset()
+    nrec = WL.n_iterations() // WL.cert_every + 2
+    out = s.solve(max_records=nrec)
+    s.set_options(certify_every=0)
+    hit, gap = {}, None
+    for r in out["records"]:
+        gap = float(np.max(ref - r["bound"][inst]) / p.n_sites)
+        for thr in (1e-3, 1e-4):
+            if thr not in hit and gap <= thr:
+                hit[thr] = (r["seconds"], r["iteration"])
+    return {"time_to_1e-4_per_site_s": hit.get(1e-4, (None,))[0], "time_to_1e-3_per_site_s": hit.get(1e-3, (None,))[0],
+            "iters_to_1e-4": hit.get(1e-4, (None, None))[1], "iters_to_1e-3": hit.get(1e-3, (None, None))[1],
+            "final_gap_per_site": gap, "certify_every": WL.cert_every,
+            "fstar_reference": {k: fstar[k] for k in ("iters_per_stage", "betas", "source") if k in fstar} |
+            {"instances": [int(i) for i in inst], "fstar_per_site": [float(x) / p.n_sites for x in ref]}}
+
+
+def measure_extras(s, p, dev, stream, args, fstar, value, tune):
+    import torch
+    out = {}
+    n_units = s.n_regions * s.n_instances
+    iters = WL.n_iterations()
+    if s.info()["loop"] == "persistent":
+        out["roofline"] = roofline_persistent(s, dev, stream, WL.iters_per_stage if WL.variant == "nesterov" else 200)
+        out["roofline_region_pass"] = roofline(s, dev, stream, WL.dominant_k)
+    else:
+        out["roofline"] = roofline(s, dev, stream, WL.dominant_k)
+    # ---- time to 1e-4/site (certified records inside the library's schedule)
+    if fstar:
+        out.update(time_to_target(s, p, fstar))
+        out["gap_per_site_vs_converged"] = out["final_gap_per_site"]
+    # ---- plain FP64 GPU comparator (torch complex128 + linalg.eigh, one instance)
+    try:
+        per_it = time_fp64_comparator(p, dev)
+        n_inst = p.n_instances
+        regs1 = s.n_regions
+        ttt = per_it * out["iters_to_1e-4"] * n_inst if out.get("iters_to_1e-4") else None
+        out["fp64_torch_comparator"] = {
+            "ms_per_iteration_one_instance": per_it * 1e3,
+            "time_to_1e-4_per_site_s_estimate": ttt,
+            "time_to_1e-4_speedup": (ttt / out["time_to_1e-4_per_site_s"]) if ttt and out.get("time_to_1e-4_per_site_s") else None,
+            "region_eigensolves_per_s": regs1 / per_it,
+            "speedup_per_region_eigensolve": value / (regs1 / per_it),
+            "note": f"single instance, same Alg. 2 iteration in complex128; the job's {n_inst} instances one after "
+                    f"another for the time-to-1e-4 estimate (same iteration count)"}
+    except Exception as ex:   # the comparator is context, not the product
+        out["fp64_torch_comparator"] = {"error": str(ex)[:200]}
+    # ---- end to end through the public API with host buffers (create from host arrays, solve, read)
+    steps = max(1, min(2, args.steps))
+    h2d = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s2 = make_solver(p, stream, tune_cache=tune)
+        if tune:
+            s2.autotune()   # reads the cached choices of this problem (no timing)
+        h2d = sum(v.nbytes for v in s2._keep.values())
+        solve(s2)
+        s2.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / steps
+    out["e2e"] = {"value": n_units * iters / e2e_s, "unit": "region eigensolves/s", "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": 8 * s.n_instances, "s_per_step": e2e_s}
+    # ---- CPU oracle baselines on bounded samples: one core, and every host core
+    cores = os.cpu_count() or 1
+    v1, smp1 = cpu_oracle_sample(10.0, 1)
+    vn, smpn = cpu_oracle_sample(10.0, cores)
+    out["cpu_baseline"] = {"value": vn, "unit": "region eigensolves/s", "cores": cores, "kind": "oracle", "sample": smpn}
+    out["cpu_baseline_1core"] = {"value": v1, "unit": "region eigensolves/s", "cores": 1, "kind": "oracle", "sample": smp1}
+    return out
 
 
 def main():
     global WL, WL_KEY
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lrh", choices=["lrh", "reference"])
-    ap.add_argument("--workload", default="heisenberg64", choices=sorted(workloads()))
+    ap.add_argument("--workload", default="xxz_tri32_x256", choices=sorted(workloads()))
     ap.add_argument("--no-extras", action="store_true", help="skip comparator / CPU baseline / e2e legs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--cta-bt", choices=["fp32", "tensor"], default=None,
@@ -478,339 +866,6 @@ def main():
     if ws > 1:
         dist.destroy_process_group()
 
-
-def max_over_ranks(x, device):
-    """Slowest rank's value (the job's time); identity on one process."""
-    import torch
-    import torch.distributed as dist
-    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
-        return float(x)
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_throughput(units_per_rank, iters, steps, total_ms_max, world):
-    """Whole-job region eigensolves/s: every rank solves its own problem (weak scaling)."""
-    return world * units_per_rank * iters * steps / (total_ms_max / 1e3)
-
-
-def make_solver(p, stream):
-    from paper_2609_40336_b300 import Solver
-    if WL.variant == "nesterov":
-        return Solver(p, variant="nesterov", beta=WL.betas[0], loop="auto", stream=stream.cuda_stream)
-    return Solver(p, variant="subgradient", alpha=WL.alpha, step_rule=WL.step_rule, loop="auto",
-                  stream=stream.cuda_stream)
-
-
-def solve(s, zero):
-    """One step: nu = 0, the whole schedule, certified bound (host read)."""
-    s.set_messages("nu", zero)
-    if WL.variant == "nesterov":
-        s.run_schedule(WL.betas, WL.iters_per_stage)
-    else:
-        s.set_messages("nu_best", zero)
-        s.restart()
-        s.step(WL.iters)
-    return s.bound("certified")
-
-
-def launches_per_step(n_classes, loop):
-    """Kernels of the library per step: Alg. 2 stage = 2 state kernels (options, restart) +
-    one pass (n_classes kernels) per iteration + final update + advance, or with the persistent
-    driver one cooperative kernel + final update + advance; Alg. 1 = restart kernel + per
-    iteration n_classes passes + reduce + update, or one cooperative kernel; then n_classes
-    certification kernels + 1 reduction."""
-    if WL.variant == "nesterov":
-        per_stage = 1 + 2 if loop == "persistent" else WL.iters_per_stage * n_classes + 2
-        return len(WL.betas) * (2 + per_stage) + n_classes + 1
-    body = 1 if loop == "persistent" else WL.n_iterations() * (n_classes + 2)
-    return 1 + body + n_classes + 1
-
-
-def run_lrh(args, ws, rank, dev, stream):
-    import torch
-    import torch.distributed as dist
-    p = WL.build()
-    s = make_solver(p, stream)
-    inf = s.info()
-    WL._regions_by_D = {f"{2 ** k}x{2 ** k}": c * s.n_instances for k, c in zip(inf["class_sites"], inf["class_regions"])}
-    n_units = s.n_regions * s.n_instances
-    iters = WL.n_iterations()
-    zero = torch.zeros(s.n_instances * s.msg_elems * 2, dtype=torch.float32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    tuned = None
-    # launch shapes picked on this problem after one untimed solve (a converged point: the pass
-    # costs there are those of the timed region, not of nu = 0), outside the timed region
-    if args.warmup == 0 and not args.no_autotune:
-        tuned = s.autotune(None, force=True)
-    for w in range(args.warmup):
-        solve(s, zero)
-        if w == 0 and not args.no_autotune:
-            tuned = s.autotune(None, force=True)
-    if args.cta_bt:
-        for k in s.info()["class_sites"]:
-            if k >= 6:   # the tensor-core back-transform exists for 128 x 128 only
-                s.set_launch_shape(k, 2 if (args.cta_bt == "tensor" and k == 7) else 1)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clocks = ClockSampler()
-    clocks.start()
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    step_ms = []
-    bounds = None
-    wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        bounds = solve(s, zero)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
-    clocks.stop()
-    total_ms = max_over_ranks(float(sum(step_ms)), dev)
-    value = job_throughput(n_units, iters, args.steps, total_ms, ws)
-    fstar = load_fstar()
-    extras = {}
-    if rank == 0 and not args.no_extras:
-        extras = measure_extras(s, p, dev, stream, args, fstar, zero, value)
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "region eigensolves/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 bound reduction and certification)",
-                "data": "synthetic", "config": config({"parallelism": f"independent problem per GPU x{ws}",
-                                                       "launch_shapes": tuned, "loop_driver": s.info()["loop"]}),
-                "certified_bound_per_site": [float(b) / p.n_sites for b in bounds][:8],
-                "gap_per_site_vs_converged": (float(np.max(np.atleast_1d(fstar["fstar"]) - np.asarray(bounds))) / p.n_sites)
-                if fstar else None,
-                "us_per_iteration": 1e3 * total_ms / args.steps / iters,
-                "wall_s_timed_region": wall, "clocks": clocks.summary(),
-                "gpu_launches": launches_per_step(len(inf["class_sites"]), s.info()["loop"]) * args.steps}
-        line.update(extras)
-        print(json.dumps(line), flush=True)
-    s.close()
-
-
-KERNEL_SOURCES = ["lrh_kernels.cu", "lrh_device.cuh", "lrh_internal.cuh", "lrh_cta.cu"]
-
-
-def kernel_source_hash(sources=None):
-    """First 16 hex digits of the SHA-256 of the listed kernel sources (default: all)."""
-    import hashlib
-    h = hashlib.sha256()
-    for f in (sources or KERNEL_SOURCES):
-        with open(os.path.join(ROOT, "paper_2609_40336_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
-
-
-def recorded_traffic():
-    """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/traffic.json),
-    only while the sources that kernel is built from are the ones that capture measured."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        rec = json.load(f).get(WL_KEY)
-    if not rec or rec.get("kernel_sources_sha256_16") != kernel_source_hash(rec.get("sources")):
-        return None
-    return rec
-
-
-def roofline(s, dev, stream, k):
-    """Dominant kernel: the region pass of class k, timed with CUDA events around a CUDA graph
-    of back-to-back launches on the library's stream (no host launch gaps)."""
-    import torch
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    inf0 = s.info()
-    ci = inf0["class_sites"].index(k)
-    n_reg = inf0["class_regions"][ci] * s.n_instances
-    D = 2 ** k
-    reps = 50 if k >= 4 else 400
-    s.launch_region_pass(k)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        for _ in range(reps):
-            s.launch_region_pass(k)
-    graph.replay()
-    torch.cuda.synchronize()
-    inf0 = s.info()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    graph.replay()
-    e1.record(stream)
-    e1.synchronize()
-    dur = e0.elapsed_time(e1) / reps * 1e-3
-    inf1 = s.info()
-    sweeps = (inf1["sweeps"][ci] - inf0["sweeps"][ci]) / (reps * n_reg)
-    fpr = 20 * sweeps * D * D * (D - 1) + 8 * D ** 3
-    achieved = n_reg * fpr / dur / 1e12
-    tr = recorded_traffic()
-    return {"bound": "alu", "kernel": f"region pass, {n_reg} regions of {D}x{D}", "achieved": achieved,
-            "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "traffic_note": tr.get("note") if tr else "no ncu capture of the current kernel sources",
-            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)",
-            "launch_us": dur * 1e6, "sweeps_per_region": sweeps, "flops_per_region": fpr,
-            "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger"}
-
-
-def roofline_persistent(s, dev, stream, n_iter):
-    """Dominant kernel under the persistent driver: one cooperative launch running n_iter
-    iterations of every class (timed with CUDA events on the library's stream around the
-    lrh_step call, which adds the small final-update and advance kernels)."""
-    import torch
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    peak_fp32 = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    s.restart()
-    s.step(n_iter)                      # warm
-    s.restart()
-    torch.cuda.synchronize()
-    inf0 = s.info()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(n_iter)
-    e1.record(stream)
-    e1.synchronize()
-    dur = e0.elapsed_time(e1) * 1e-3
-    inf1 = s.info()
-    flops, parts = 0.0, []
-    for ci, k in enumerate(inf1["class_sites"]):
-        D = 2 ** k
-        regions = inf1["class_regions"][ci] * s.n_instances
-        if D == 2:
-            parts.append(f"{regions} regions of 2x2 (closed form, not counted)")
-            continue
-        sweeps = inf1["sweeps"][ci] - inf0["sweeps"][ci]
-        flops += 20.0 * sweeps * D * D * (D - 1) + 8.0 * D ** 3 * regions * n_iter
-        parts.append(f"{regions} regions of {D}x{D} ({sweeps / (regions * n_iter):.2f} sweeps)")
-    achieved = flops / dur / 1e12
-    return {"bound": "alu", "kernel": f"persist_kernel: {n_iter} iterations of " + ", ".join(parts),
-            "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-            "traffic": None, "traffic_note": "cooperative launch not captured with ncu (multi-pass replay of a grid barrier)",
-            "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)",
-            "launch_us": dur * 1e6, "us_per_iteration": dur * 1e6 / n_iter,
-            "flop_model": "sum over classes of 20*S*D^2*(D-1) + 8*D^3 per region and iteration"}
-
-
-def time_to_target(s, p, zero, fstar):
-    """Wall time until the FP64-certified bound is within 1e-3 / 1e-4 per site of the
-    converged reference (worst instance), certifying every CERT_EVERY iterations."""
-    import torch
-    ref = np.atleast_1d(np.asarray(fstar["fstar"], dtype=np.float64))
-    s.set_messages("nu", zero)
-    if WL.variant == "subgradient":
-        s.set_messages("nu_best", zero)
-        s.restart()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    hit, done_it, gap = {}, 0, None
-
-    def check():
-        nonlocal gap
-        gap = float(np.max(ref - s.bound("certified")) / p.n_sites)
-        for thr in (1e-3, 1e-4):
-            if thr not in hit and gap <= thr:
-                hit[thr] = (time.perf_counter() - t0, done_it)
-
-    if WL.variant == "nesterov":
-        for b in WL.betas:
-            s.set_options(beta=b, lhat=None)
-            s.restart()
-            for _ in range(max(1, WL.iters_per_stage // CERT_EVERY)):
-                s.step(CERT_EVERY)
-                done_it += CERT_EVERY
-                check()
-    else:
-        for _ in range(max(1, WL.iters // CERT_EVERY)):
-            s.step(CERT_EVERY)
-            done_it += CERT_EVERY
-            check()
-    return {"time_to_1e-4_per_site_s": hit.get(1e-4, (None,))[0], "time_to_1e-3_per_site_s": hit.get(1e-3, (None,))[0],
-            "iters_to_1e-4": hit.get(1e-4, (None, None))[1], "iters_to_1e-3": hit.get(1e-3, (None, None))[1],
-            "final_gap_per_site": gap,
-            "fstar_reference": {k: fstar[k] for k in ("fstar_per_site", "iters_per_stage", "betas", "source")}}
-
-
-def measure_extras(s, p, dev, stream, args, fstar, zero, value):
-    import torch
-    out = {}
-    n_units = s.n_regions * s.n_instances
-    iters = WL.n_iterations()
-    if s.info()["loop"] == "persistent":
-        out["roofline"] = roofline_persistent(s, dev, stream, WL.iters_per_stage if WL.variant == "nesterov" else 200)
-        out["roofline_region_pass"] = roofline(s, dev, stream, WL.dominant_k)
-    else:
-        out["roofline"] = roofline(s, dev, stream, WL.dominant_k)
-    # ---- time to 1e-4/site (certify every CERT_EVERY iterations, certification time included)
-    if fstar:
-        out.update(time_to_target(s, p, zero, fstar))
-    # ---- plain FP64 GPU comparator (torch complex128 + linalg.eigh, one instance)
-    if True:
-        try:
-            per_it = time_fp64_comparator(p, dev)
-            ttt = None
-            if out.get("iters_to_1e-4"):
-                ttt = per_it * out["iters_to_1e-4"]
-            out["fp64_torch_comparator"] = {"ms_per_iteration": per_it * 1e3,
-                                            "time_to_1e-4_per_site_s_estimate": ttt,
-                                            "time_to_1e-4_speedup": (ttt / out["time_to_1e-4_per_site_s"])
-                                            if ttt and out.get("time_to_1e-4_per_site_s") else None,
-                                            "region_eigensolves_per_s": s.n_regions / per_it,
-                                            "speedup_per_region_eigensolve": value / (s.n_regions / per_it),
-                                            "note": "single instance, same Alg. 2 iteration in complex128"}
-        except Exception as ex:
-            out["fp64_torch_comparator"] = {"error": str(ex)[:200]}
-    # ---- end to end through the public API with host buffers
-    steps = max(1, min(3, args.steps))
-    h2d = 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        s2 = make_solver(p, stream)
-        h2d = sum(v.nbytes for v in s2._keep.values())
-        zero2 = torch.zeros(s2.n_instances * s2.msg_elems * 2, dtype=torch.float32, device=dev)
-        solve(s2, zero2)
-        s2.close()
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / steps
-    out["e2e"] = {"value": n_units * iters / e2e_s, "unit": "region eigensolves/s", "h2d_bytes_per_step": int(h2d),
-                  "d2h_bytes_per_step": 8 * s.n_instances, "s_per_step": e2e_s}
-    # ---- CPU oracle baseline on a bounded sample
-    val, sample = cpu_oracle_sample(seconds=12.0)
-    out["cpu_baseline"] = {"value": val, "unit": "region eigensolves/s", "cores": 1, "kind": "oracle", "sample": sample}
-    return out
-
-
-WL_KEY = "heisenberg64"
 
 if __name__ == "__main__":
     main()

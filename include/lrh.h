@@ -68,6 +68,11 @@ extern "C" {
 #define LRH_ETIMEOUT     (-6)  /* a bounded device wait gave up (grid barrier of the persistent launch) */
 #define LRH_ENUMERIC     (-7)  /* a non-finite eigenvalue, value or message was produced */
 #define LRH_EUNSUPPORTED (-8)  /* region size beyond the kernels built into this library */
+#define LRH_ENOCONV      (-9)  /* an FP64 certification eigensolve stopped at its sweep cap before
+                                  converging; the bound returned with it is still a valid lower
+                                  bound (Weyl-corrected), only looser */
+#define LRH_EDEADLINE   (-10)  /* lrh_solve stopped at lrh_options.deadline_s (results are those of
+                                  the last completed certification) */
 
 /* ---------------------------------------------------------------- enums */
 #define LRH_SUBGRADIENT   0    /* Alg. 1: ground projectors, nu += alpha_t g            */
@@ -81,6 +86,10 @@ extern "C" {
 #define LRH_LOOP_PERSISTENT 2  /* one cooperative launch for all iterations of an lrh_step    */
 #define LRH_LOOP_AUTO       3  /* chosen by lrh_autotune (graph or persistent)                */
 
+#define LRH_SHAPE_BLOCKS  4096  /* lrh_set_launch_shape, classes of 3-4 sites: LRH_SHAPE_BLOCKS + 64 / 128 / 256
+                                   selects the Hermitian 2x2-block layout (theta's upper triangle in
+                                   shared memory, each stored entry rotated once per round) with that
+                                   many threads per CTA; D lanes per region as in the lane-row layout */
 #define LRH_SHAPE_CTA_FP32   1  /* lrh_set_launch_shape, classes of 6-7 sites: rho = W W^dagger on the FP32 cores */
 #define LRH_SHAPE_CTA_TENSOR 2  /* ... on the tensor cores (tcgen05, three TF32 products per term, FP32
                                    accumulate); 7-site (128 x 128) regions only */
@@ -94,6 +103,12 @@ extern "C" {
 #define LRH_BOUND_LAST      1  /* FP64 sum of the per-region FP32 values of the last region pass:
                                   Q_beta(eta) for Alg. 2, Q(nu) for Alg. 1                   */
 #define LRH_BOUND_BEST      2  /* Alg. 1 q_best = max over past iterations of Q(nu^(t))      */
+
+/* The certified value of a region is min_i a_ii - ||offdiag(A)||_F of the matrix A the FP64
+ * Jacobi iteration ends with (Weyl's inequality: a lower bound on lambda_min(theta) whether or
+ * not the iteration converged; at convergence the correction is below 1e-14 ||theta||_F).  If a
+ * region stopped at the sweep cap with ||offdiag||_F^2 > 1e-28 ||theta||_F^2, lrh_bound returns
+ * LRH_ENOCONV and still fills `out`. */
 
 /* ---------------------------------------------------------------- problem description */
 typedef struct {
@@ -109,6 +124,14 @@ typedef struct {
     const double* term_mats;      /* [n_instances][term_mat_total][2] (re, im), row-major
                                      2^k x 2^k per term; instance i holds its own matrices     */
     int32_t n_instances;          /* >= 1 Hamiltonians sharing one region family (batch)       */
+    /* Optional explicit pairs e -> f (n_pairs > 0): consistency constraints between region
+     * pair_parent[q] and region pair_child[q], whose sites must be a proper subset of the
+     * parent's; duplicates are rejected (LRH_EPOSET).  Any set of such pairs gives a valid
+     * relaxation (Sec. 4.2 notes that the covering pairs suffice); they are stored in pair order
+     * whatever order they are given in.  n_pairs = 0: the covering relation of inclusion.     */
+    int64_t n_pairs;
+    const int32_t* pair_parent;
+    const int32_t* pair_child;
 } lrh_problem_desc;
 
 typedef struct {
@@ -128,6 +151,18 @@ typedef struct {
                              choice of lrh_autotune; GRAPH before it).  All drivers give
                              bit-identical messages for the same launch shapes; the
                              persistent one runs every class in the lane layout.             */
+    int32_t cert_sweeps;  /* sweep cap of the FP64 certification eigensolver; <= 0 selects 40  */
+    /* Schedule run by lrh_solve (all host values, copied by lrh_create / lrh_set_options):   */
+    int32_t n_beta;              /* Alg. 2: beta-continuation stages (0: one stage at `beta`)  */
+    const double* beta_sched;    /* [n_beta] stage inverse temperatures (> 0); each stage sets
+                                    L_hat = lhat if lhat > 0 else beta_s Lambda_G / 2 and restarts
+                                    (theta = 1, zeta = nu)                                     */
+    int32_t iters_per_stage;     /* Alg. 2: iterations of every stage; Alg. 1: of the run      */
+    int32_t certify_every;       /* lrh_solve records the certified bound every this many
+                                    iterations (<= 0: at the end of the run only)              */
+    double deadline_s;           /* lrh_solve stops at the first record after this many
+                                    seconds of wall time (<= 0: no deadline)                  */
+    const char* tune_cache;      /* cache file lrh_autotune uses when called with NULL (copied) */
 } lrh_options;
 
 typedef struct lrh_problem lrh_problem;
@@ -154,7 +189,35 @@ typedef struct {
     int32_t loop;                 /* driver lrh_step uses now (LRH_LOOP_EAGER/GRAPH/PERSISTENT)  */
     int32_t persistent_grid;      /* CTAs of the persistent launch (0: not available)             */
     int64_t persistent_tiles;     /* region tiles per pass in the persistent launch               */
+    uint64_t sweep_capped[8];     /* cumulative FP32 eigensolves per class that stopped at
+                                     lrh_options.max_sweeps before reaching the threshold
+                                     ||offdiag||_F^2 <= 1e-12 ||theta||_F^2                      */
+    int32_t n_sites;
+    int32_t kappa_G;              /* max over sites i of |{e->f : i in f}| (Thm 6; Delta_G at level 1) */
 } lrh_info;
+
+/* Parameter rules of the convergence theorems for a target error density eps (per site):
+ *   Alg. 2 (Thm 5, Thm 7): beta = 2 Gamma_G / (n eps), L_hat = beta Lambda_G / 2,
+ *                          T >= ceil(2 R sqrt(Gamma_G Lambda_G) / (n eps)) - 1;
+ *   Alg. 1 (Thm 4, Thm 6): alpha = c eps with c = c_frac / kappa_G (0 < c_frac < 1),
+ *                          T >= ceil(R^2 / (2 c (1 - c kappa_G) n eps^2)).
+ * R is the distance from nu^(0) to the optimal multipliers (caller's estimate; <= 0: the
+ * iteration counts are returned as -1).  Lambda_G is Delta_G + d for pure level-1 posets and
+ * max_{e->f} (m_f + m_e D_e / D_f) otherwise (the two lemmas on L_hat). */
+typedef struct {
+    double beta, lhat, alpha, c;
+    double lambda_G, gamma_G;
+    int32_t kappa_G;
+    int32_t n_sites;
+    int64_t T_nesterov, T_subgradient;
+} lrh_params;
+
+/* One record of lrh_solve: the certified bound after `iteration` iterations of the run. */
+typedef struct {
+    int64_t iteration;   /* iterations since the start of this lrh_solve call               */
+    double seconds;      /* host wall time since the start of the call, after the bound was read */
+    double beta;         /* stage inverse temperature (Alg. 2; 0 for Alg. 1)                */
+} lrh_record;
 
 /* ---------------------------------------------------------------- entry points */
 
@@ -228,7 +291,7 @@ int lrh_set_terms(lrh_problem* p, const double* term_mats);
  *   rho_bar_e = sum_parents g_bar - sum_children 1 (x) g_bar,
  *   theta_bar = V[(V^dagger rho_bar V) o K + (beta <rho_bar, rho> + q_bar) diag(p)] V^dagger,
  *   K_kl = (p_k - p_l)/(lambda_k - lambda_l), K_kk = -beta p_k  (eigenbasis recomputed),
- *   nu_bar_{e->f} = theta_bar_f - Tr_{e} theta_bar_e,  term_bar_t = Tr_{R	} theta_bar_R.
+ *   nu_bar_{e->f} = theta_bar_f - Tr_{e\f} theta_bar_e,  term_bar_t = Tr_{R\t} theta_bar_R.
  * The derivative with respect to nu_{e->f} of eta-evaluated quantities is returned for eta
  * itself.  Outputs are device pointers when out_is_device (each may be NULL).
  * The first call allocates the adjoint buffers.  Synchronises. */
@@ -287,25 +350,48 @@ int lrh_synchronize(lrh_problem* p);
  * memory is reserved up front) and therefore cannot use lrh_create.  It computes what
  * lrh_evaluate computes for a Nesterov problem whose regions are the given edges and all
  * sites (with eta = nu): Q_beta = sum of F_beta over edges and sites, and the gradient
- * g_{e->v} = rho_v - Tr_{e} rho_e, using only caller-owned buffers plus a fixed scratch
- * array compiled into the library (about 5.5 MB of device memory on every GPU that loads the
+ * g_{e->v} = rho_v - Tr_{e\v} rho_e, using only caller-owned buffers plus a fixed scratch
+ * array compiled into the library (about 5 MB of device memory on every GPU that loads the
  * library, held until the process exits).  Limits: n_sites <= 65536, n_edges <= 131072;
  * larger sizes return LRH_EINVAL.
- *   edges    device int32 [n_edges][2]: the two DISTINCT sites of each edge; the first one
- *            is the most significant factor of the edge's 4 x 4 index
+ *   edges    device int32 [n_edges][2]: two distinct sites 0 <= site < n_sites per edge; the
+ *            first one is the most significant factor of the edge's 4 x 4 index.  An endpoint
+ *            out of range or repeated is not used: the edge's gradient blocks and *value_out
+ *            are set to NaN (the call still returns LRH_OK; the check runs on the device)
  *   h_edge   device complex64 [n_edges][4][4] edge terms in that order, or NULL (zero)
  *   h_site   device complex64 [n_sites][2][2] site terms, or NULL (zero)
  *   nu       device complex64 [n_edges][2][2][2]: nu_{e->first site}, then nu_{e->second site}
  *   beta     smoothing inverse temperature (> 0)
  *   value_out device double [1] receives Q_beta; grad_out device complex64 [n_edges][2][2][2]
  * Every matrix must be Hermitian (only upper triangles of 2 x 2 blocks are read for sites).
- * Asynchronous on `stream` (a cudaStream_t or NULL).  Calls share the scratch array: calls that
- * may overlap on the GPU race and must be ordered by the caller.  The first call on a device
- * looks up the scratch address for that device; make it before any stream capture.  Calls no
- * allocating routine. */
+ * Each site sums its incoming messages in ascending edge order, so repeated calls with the same
+ * inputs give bit-identical outputs.  Asynchronous on `stream` (a cudaStream_t or NULL).  Calls
+ * share the scratch array: calls that may overlap on the GPU race and must be ordered by the
+ * caller.  The first call on a device looks up the scratch address for that device; make it
+ * before any stream capture.  Calls no allocating routine. */
 int lrh_level1_eval_noalloc(int32_t n_sites, int32_t n_edges, const int32_t* edges, const void* h_edge,
                             const void* h_site, const void* nu, double beta, double* value_out,
                             void* grad_out, void* stream);
+
+/* Theorem parameter rules (see lrh_params) for target error density eps > 0; host only. */
+int lrh_theorem_parameters(const lrh_problem* p, double eps, double R, double c_frac, lrh_params* out);
+
+/* Zero nu, zeta, nu_best (Alg. 1 / Alg. 2 initialisation), set theta = 1, t = 0 and
+ * q_best = -inf.  Stream-ordered. */
+int lrh_reset(lrh_problem* p);
+
+/* Run the schedule of lrh_options from the current multipliers: Alg. 2 runs one stage per
+ * beta_sched entry (or one stage at `beta`), each stage setting beta and L_hat and restarting
+ * (theta = 1, zeta = nu; reading of the paper: Alg. 2 with one fixed beta, continued over
+ * stages), then iters_per_stage iterations; Alg. 1 restarts and runs iters_per_stage
+ * iterations.  Every certify_every iterations (and at the end) the certified bound
+ * (LRH_BOUND_CERTIFIED) is computed; up to max_records records are written to rec[] with the
+ * per-instance bounds in rec_bounds[max_records][n_instances] (both host, may be NULL with
+ * max_records = 0), their count to *n_records (may be NULL).  bound_out[n_instances] (host)
+ * receives the last certified bound.  With deadline_s > 0 the run stops at the first record
+ * taken after the deadline and returns LRH_EDEADLINE.  Synchronises at every record. */
+int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_bounds, int32_t* n_records,
+              double* bound_out);
 
 /* Static message for an error code, and the thread-local detail of the last failure. */
 const char* lrh_strerror(int code);

@@ -2,7 +2,7 @@
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -19,6 +19,8 @@ class Problem:
                 sites in sorted order, first site = most significant bit.
     n_sites_per_instance: the n used for per-site normalisation (= n_sites).
     meta      : free-form description (seed, conventions) for reports.
+    pairs     : optional explicit consistency pairs (parent region index, child region index);
+                None = the covering relation of inclusion.
     """
 
     n_sites: int
@@ -26,6 +28,7 @@ class Problem:
     term_sites: List[Tuple[int, ...]]
     term_mats: List[np.ndarray]
     meta: dict = field(default_factory=dict)
+    pairs: Optional[List[Tuple[int, int]]] = None   # explicit (parent, child) region pairs, or covering
 
     @property
     def n_instances(self) -> int:

@@ -307,3 +307,62 @@ def run_subgradient(P: Poset, h, iters: int, rule: str = "sqrt", alpha: float = 
     for _ in range(iters):
         subgradient_step(P, h, st, rule, alpha, tol)
     return st
+
+
+# ------------------------------------------------------------------ sampled evaluation
+def terms_by_region(problem, P: Poset) -> Dict[int, List[int]]:
+    """Indices of the terms placed on each region (see place_terms)."""
+    out: Dict[int, List[int]] = {}
+    for t, e in enumerate(place_terms(problem, P)):
+        out.setdefault(e, []).append(t)
+    return out
+
+
+def region_theta(problem, P: Poset, on: Dict[int, List[int]], msg: np.ndarray, e: int, inst: int) -> np.ndarray:
+    """theta_e of one region (Sec. 4.2) at the multipliers of one instance:
+    h_e - sum_{f in D(e)} 1_{e\f} (x) nu_{e->f} + sum_{g in A(e)} nu_{g->e}, with h_e the
+    embedded sum of the terms ``on[e]`` placed on e."""
+    k = int(P.k[e])
+    th = np.zeros((P.d ** k, P.d ** k), np.complex128)
+    for t in on.get(e, []):
+        th += embed(problem.term_mats[t][inst], [P.regions[e].index(s) for s in problem.term_sites[t]], k, P.d)
+    for q in np.nonzero(P.pair_parent == e)[0]:
+        Df = int(P.D[P.pair_child[q]])
+        nu = msg[inst, P.msg_off[q]:P.msg_off[q] + Df * Df].reshape(Df, Df)
+        th = th - embed(nu, P.pair_pos[q], k, P.d)
+    for q in np.nonzero(P.pair_child == e)[0]:
+        D = int(P.D[e])
+        th = th + msg[inst, P.msg_off[q]:P.msg_off[q] + D * D].reshape(D, D)
+    return th
+
+
+def sampled_pass(problem, P: Poset, msg: np.ndarray, pairs: Sequence[int], insts: Sequence[int], mode: str,
+                 beta: Optional[float] = None, tol: float = 1e-9):
+    """region_pass restricted to the given (pair, instance) samples: for each sampled pair
+    e -> f, the states of e and f at the multipliers ``msg`` and the gradient component
+    g_{e->f} = rho_f - Tr_{e\f} rho_e (Sec. 4.1.2, 4.2), plus the value of e and f (F_beta or
+    lambda_min) and ||theta||_F.  Returns (grads, values, norms): grads[i] is the D_f x D_f
+    block of sample i; values and norms map (instance, region) to floats."""
+    on = terms_by_region(problem, P)
+    cache = {}
+
+    def state(e, inst):
+        if (e, inst) not in cache:
+            th = region_theta(problem, P, on, msg, e, inst)
+            lam, V = np.linalg.eigh(th)
+            if mode == "smooth":
+                w, val = gibbs_weights(lam, beta), softmin(lam, beta)
+            else:
+                w, val = ground_weights(lam, th, tol), lam[0]
+            cache[(e, inst)] = (state_from(w, V), float(val), float(np.linalg.norm(th)))
+        return cache[(e, inst)]
+
+    grads = []
+    for q, inst in zip(pairs, insts):
+        e, f = int(P.pair_parent[q]), int(P.pair_child[q])
+        rho_e = state(e, inst)[0]
+        rho_f = state(f, inst)[0]
+        grads.append(rho_f - partial_trace(rho_e, P.pair_pos[q], int(P.k[e]), P.d))
+    values = {(inst, e): v[1] for (e, inst), v in cache.items()}
+    norms = {(inst, e): v[2] for (e, inst), v in cache.items()}
+    return grads, values, norms

@@ -21,7 +21,10 @@ import numpy as np
 
 
 class Poset:
-    def __init__(self, regions: Sequence[Sequence[int]], d: int = 2):
+    def __init__(self, regions: Sequence[Sequence[int]], d: int = 2, pairs=None):
+        """``pairs``: optional explicit (parent, child) region pairs, each child a proper
+        subset of its parent (any such set of consistency constraints defines a valid
+        relaxation; the covering relation is the minimal one, Sec. 4.2).  Default: covering."""
         self.d = d
         self.regions: List[Tuple[int, ...]] = [tuple(r) for r in regions]
         R = len(self.regions)
@@ -34,7 +37,16 @@ class Poset:
         self.k = np.array([len(r) for r in self.regions], dtype=np.int64)
         self.D = self.d ** self.k
         children: List[List[int]] = [[] for _ in range(R)]
+        for e, f in (pairs or []):
+            if not set(self.regions[f]) < set(self.regions[e]):
+                raise ValueError(f"pair {e}->{f}: child is not a proper subset of the parent")
+            if f in children[e]:
+                raise ValueError(f"duplicate pair {e}->{f}")
+            children[e].append(f)
         for e, r in enumerate(self.regions):
+            if pairs:
+                children[e].sort()
+                continue
             subs = []
             for m in range(1, len(r)):
                 for comb in itertools.combinations(r, m):

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "liblrh.so")
 
 LRH_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOTHERM", -3: "EPOSET", -4: "ENOMEM", -5: "ECUDA",
-          -6: "ETIMEOUT", -7: "ENUMERIC", -8: "EUNSUPPORTED"}
+          -6: "ETIMEOUT", -7: "ENUMERIC", -8: "EUNSUPPORTED", -9: "ENOCONV", -10: "EDEADLINE"}
+ENOCONV, EDEADLINE = -9, -10
 SUBGRADIENT, NESTEROV = 0, 1
 STEP_CONST, STEP_INV_SQRT = 0, 1
 MSG_NU, MSG_ZETA, MSG_NU_BEST, MSG_GRAD = 0, 1, 2, 3
@@ -33,6 +34,9 @@ class ProblemDesc(C.Structure):
         ("term_mat_total", C.c_int64),
         ("term_mats", C.POINTER(C.c_double)),
         ("n_instances", C.c_int32),
+        ("n_pairs", C.c_int64),
+        ("pair_parent", C.POINTER(C.c_int32)),
+        ("pair_child", C.POINTER(C.c_int32)),
     ]
 
 
@@ -46,6 +50,13 @@ class Options(C.Structure):
         ("degen_tol", C.c_double),
         ("max_sweeps", C.c_int32),
         ("loop", C.c_int32),
+        ("cert_sweeps", C.c_int32),
+        ("n_beta", C.c_int32),
+        ("beta_sched", C.POINTER(C.c_double)),
+        ("iters_per_stage", C.c_int32),
+        ("certify_every", C.c_int32),
+        ("deadline_s", C.c_double),
+        ("tune_cache", C.c_char_p),
     ]
 
 
@@ -68,7 +79,23 @@ class Info(C.Structure):
         ("loop", C.c_int32),
         ("persistent_grid", C.c_int32),
         ("persistent_tiles", C.c_int64),
+        ("sweep_capped", C.c_uint64 * 8),
+        ("n_sites", C.c_int32),
+        ("kappa_G", C.c_int32),
     ]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("beta", C.c_double), ("lhat", C.c_double), ("alpha", C.c_double), ("c", C.c_double),
+        ("lambda_G", C.c_double), ("gamma_G", C.c_double),
+        ("kappa_G", C.c_int32), ("n_sites", C.c_int32),
+        ("T_nesterov", C.c_int64), ("T_subgradient", C.c_int64),
+    ]
+
+
+class Record(C.Structure):
+    _fields_ = [("iteration", C.c_int64), ("seconds", C.c_double), ("beta", C.c_double)]
 
 
 class LrhError(RuntimeError):
@@ -104,6 +131,9 @@ SIGNATURES = {
     "lrh_vjp": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
     "lrh_level1_eval_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lrh_theorem_parameters": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.POINTER(Params)]),
+    "lrh_reset": (C.c_int, [C.c_void_p]),
+    "lrh_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lrh_strerror": (C.c_char_p, [C.c_int]),
     "lrh_last_error": (C.c_char_p, []),
 }

@@ -13,14 +13,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblrh.so")
-SOURCES = ["lrh_api.cu", "lrh_kernels.cu", "lrh_cta.cu", "lrh_vjp.cu", "lrh_noalloc.cu"]
+SOURCES = ["lrh_api.cu", "lrh_kernels.cu", "lrh_cta.cu", "lrh_block.cu", "lrh_vjp.cu", "lrh_noalloc.cu"]
+HEADERS = ["lrh_internal.cuh", "lrh_device.cuh", "lrh_block.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
 def sources():
-    return [os.path.join(CSRC, s) for s in SOURCES] + [
-        os.path.join(CSRC, "lrh_internal.cuh"), os.path.join(CSRC, "lrh_device.cuh"), os.path.join(ROOT, "include", "lrh.h")]
+    return [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(ROOT, "include", "lrh.h")]
 
 
 def up_to_date() -> bool:

@@ -5,6 +5,7 @@
 #include "lrh_internal.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <limits>
 #include <memory>
 #include <new>
+#include <set>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -63,6 +65,9 @@ struct lrh_problem {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     lrh_options opt{};
+    std::vector<double> beta_sched;   // owned copies of the options' host arrays
+    std::string tune_cache;
+    int32_t n_sites = 0, kappa = 0;
     double lhat_eff = 1.0;
     int32_t n_inst = 1, n_regions = 0, n_pairs = 0, max_k = 0;
     int64_t msg_elems = 0, h_elems = 0, rho_elems = 0;
@@ -137,6 +142,11 @@ namespace {
 
 int validate_options(const lrh_options* o) {
     if (!o) return fail(LRH_EINVAL, "options is NULL");
+    if (o->n_beta < 0 || (o->n_beta > 0 && !o->beta_sched)) return fail(LRH_EINVAL, "beta_sched is NULL or n_beta < 0");
+    for (int i = 0; i < o->n_beta; ++i)
+        if (!(o->beta_sched[i] > 0.0) || !std::isfinite(o->beta_sched[i])) return fail(LRH_EINVAL, "beta_sched entries must be finite and > 0");
+    if (o->iters_per_stage < 0 || o->certify_every < 0) return fail(LRH_EINVAL, "iters_per_stage and certify_every must be >= 0");
+    if (!std::isfinite(o->deadline_s)) return fail(LRH_EINVAL, "non-finite deadline_s");
     if (o->variant != LRH_SUBGRADIENT && o->variant != LRH_NESTEROV) return fail(LRH_EINVAL, "unknown variant");
     if (o->step_rule != LRH_STEP_CONST && o->step_rule != LRH_STEP_INV_SQRT) return fail(LRH_EINVAL, "unknown step rule");
     if (o->variant == LRH_SUBGRADIENT && !(o->alpha > 0.0)) return fail(LRH_EINVAL, "alpha must be > 0");
@@ -146,13 +156,23 @@ int validate_options(const lrh_options* o) {
     return LRH_OK;
 }
 
+// Options with their host arrays copied into the problem (the caller's may go away).
+void copy_options(lrh_problem* p, const lrh_options* o) {
+    p->opt = *o;
+    p->beta_sched.assign(o->beta_sched, o->beta_sched + (o->n_beta > 0 ? o->n_beta : 0));
+    p->opt.beta_sched = p->beta_sched.empty() ? nullptr : p->beta_sched.data();
+    p->tune_cache = o->tune_cache ? o->tune_cache : "";
+    p->opt.tune_cache = o->tune_cache ? p->tune_cache.c_str() : nullptr;
+}
+
 int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
     const lrh_options& o = p->opt;
     p->lhat_eff = o.lhat > 0.0 ? o.lhat : (o.beta > 0.0 ? o.beta * p->lambda_G / 2.0 : 1.0);
     const double degen = o.degen_tol > 0.0 ? o.degen_tol : 1e-5;
     const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
+    const int cert = o.cert_sweeps > 0 ? o.cert_sweeps : 40;
     LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), theta, t, set_theta_t ? 1 : 0, o.beta,
-                            1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, p->stream));
+                            1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, cert, p->stream));
     return LRH_OK;
 }
 
@@ -300,6 +320,14 @@ int run_persistent(lrh_problem* p, int n) {
     return LRH_OK;
 }
 
+// Classes of 3 and 4 sites whose launch shape selects the 2x2-block layout (bit k).
+int32_t blk_mask_of(const lrh_problem* p) {
+    int32_t m = 0;
+    for (size_t c = 0; c < p->class_k.size(); ++c)
+        if ((p->class_k[c] == 3 || p->class_k[c] == 4) && p->class_block[c] > LRH_SHAPE_BLOCKS) m |= 1 << p->class_k[c];
+    return m;
+}
+
 // Plan of the persistent launch: classes in cost order (heaviest first), tiles of
 // persistent_tile_regions(k) regions, grid = min(tiles, resident CTAs).  Not available when a
 // class has more than 4 sites or the device lacks cooperative launches.
@@ -330,6 +358,7 @@ int plan_persistent(lrh_problem* p) {
     int rc;
     if ((rc = p->dalloc(&L.bar, 2))) return rc;
     LRH_CK(cudaMemset(L.bar, 0, 2 * sizeof(unsigned)));
+    L.blk_mask = blk_mask_of(p);
     p->plan = L;
     p->persist_kmax = kmax;
     p->persist_cap = (int64_t)nb * sms;
@@ -419,17 +448,23 @@ int build_graph(lrh_problem* p) {
     return LRH_OK;
 }
 
+// Wait for the stream and report the device error word; every reported condition is cleared,
+// so it is returned once, by the first synchronising call after it was raised.
 int read_err(lrh_problem* p) {
     int32_t h = 0;
     LRH_CK(cudaMemcpyAsync(&h, p->P.err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
-    if (h & DEV_ERR_TIMEOUT) {
+    if (h) {
         LRH_CK(cudaMemsetAsync(p->P.err, 0, sizeof(int32_t), p->stream));
         LRH_CK(cudaStreamSynchronize(p->stream));
-        return fail(LRH_ETIMEOUT, "a grid barrier of the persistent iteration waited longer than its limit; "
-                                  "the launch stopped (messages are those of an unfinished step)");
     }
+    if (h & DEV_ERR_TIMEOUT)
+        return fail(LRH_ETIMEOUT, "a bounded device wait (grid barrier of the persistent iteration, or a "
+                                  "tensor-core commit) gave up; the results of that launch are incomplete");
     if (h & DEV_ERR_NUMERIC) return fail(LRH_ENUMERIC, "a non-finite eigenvalue, value or message was produced");
+    if (h & DEV_ERR_NOCONV)
+        return fail(LRH_ENOCONV, "an FP64 certification eigensolve stopped at its sweep cap; the bound is "
+                                 "Weyl-corrected (still a lower bound) but looser");
     return LRH_OK;
 }
 
@@ -448,6 +483,8 @@ const char* lrh_strerror(int code) {
         case LRH_ETIMEOUT: return "device wait timed out";
         case LRH_ENUMERIC: return "non-finite value";
         case LRH_EUNSUPPORTED: return "unsupported region size";
+        case LRH_ENOCONV: return "certification eigensolve not converged (bound still valid)";
+        case LRH_EDEADLINE: return "deadline reached";
         default: return "unknown error";
     }
 }
@@ -485,11 +522,33 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         maxk = std::max<int>(maxk, (int)k);
     }
     if (maxk > kMaxKernelSites)
-        return fail(LRH_EUNSUPPORTED, "regions of " + std::to_string(maxk) + " sites need the D > 32 kernels, not in this build");
+        return fail(LRH_EUNSUPPORTED, "regions of " + std::to_string(maxk) + " sites have no region-pass kernel in this build (at most " +
+                                          std::to_string(kMaxKernelSites) + ")");
 
-    // covering pairs (children of e: proper sub-regions with no region strictly between)
     std::vector<std::vector<std::pair<int, int>>> kids(R);   // (child, index-bit mask)
-    for (int e = 0; e < R; ++e) {
+    if (d->n_pairs < 0) return fail(LRH_EINVAL, "n_pairs < 0");
+    if (d->n_pairs > 0) {
+        // explicit pairs: the child's sites must be a proper subset of the parent's
+        if (!d->pair_parent || !d->pair_child) return fail(LRH_EINVAL, "pair arrays are NULL");
+        std::set<std::pair<int, int>> seen;
+        for (int64_t q = 0; q < d->n_pairs; ++q) {
+            const int e = d->pair_parent[q], f = d->pair_child[q];
+            if (e < 0 || e >= R || f < 0 || f >= R) return fail(LRH_EINVAL, "pair region index out of range");
+            if (!seen.insert({e, f}).second) return fail(LRH_EPOSET, "duplicate pair " + std::to_string(e) + "->" + std::to_string(f));
+            const int k = (int)regs[e].size();
+            if (regs[f].size() >= regs[e].size()) return fail(LRH_EPOSET, "pair child is not a proper subset of its parent");
+            int im = 0;
+            for (int32_t site : regs[f]) {
+                const auto it = std::find(regs[e].begin(), regs[e].end(), site);
+                if (it == regs[e].end()) return fail(LRH_EPOSET, "pair child is not a subset of its parent");
+                im |= 1 << (k - 1 - (int)(it - regs[e].begin()));
+            }
+            kids[e].emplace_back(f, im);
+        }
+        for (auto& v : kids) std::sort(v.begin(), v.end());
+    }
+    // covering pairs (children of e: proper sub-regions with no region strictly between)
+    for (int e = 0; e < R && d->n_pairs == 0; ++e) {
         const int k = (int)regs[e].size();
         std::vector<std::pair<int, int>> subs;   // (region, position mask: bit p = position p)
         std::vector<int32_t> tmp;
@@ -513,7 +572,8 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     lrh_problem* p = new (std::nothrow) lrh_problem();
     if (!p) return fail(LRH_ENOMEM, "host allocation");
     std::unique_ptr<lrh_problem> guard(p);
-    p->opt = *opts;
+    copy_options(p, opts);
+    p->n_sites = d->n_sites;
     p->n_inst = d->n_instances;
     p->n_regions = R;
     p->max_k = maxk;
@@ -568,6 +628,11 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     }
     p->gamma_G = 0;
     for (int e = 0; e < R; ++e) p->gamma_G += (double)regs[e].size() * std::log(2.0);
+    {   // kappa_G = max over sites i of |{e->f : i in f}| (Thm 6)
+        std::vector<int32_t> cnt(d->n_sites, 0);
+        for (auto& pi : pairs) for (int32_t site : regs[pi.child]) ++cnt[site];
+        p->kappa = cnt.empty() ? 0 : *std::max_element(cnt.begin(), cnt.end());
+    }
 
     // ---------------------------------------------------------------- terms
     std::vector<std::vector<int32_t>> by_site(d->n_sites);
@@ -691,7 +756,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     }
     if ((rc = p->dalloc(&P.val, NI * R)) || (rc = p->dalloc(&P.val64, NI * R)) || (rc = p->dalloc(&P.q_sum, NI)) ||
         (rc = p->dalloc(&P.q_best, NI)) || (rc = p->dalloc(&P.best_flag, NI)) || (rc = p->dalloc(&P.st, 1)) ||
-        (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)))
+        (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)) || (rc = p->dalloc(&P.capped, 8)))
         return rc;
     P.reg = dreg; P.pair = dpair; P.child_pairs = dcp; P.parent_pairs = dpp; P.h32 = h32; P.h64 = dh64;
     P.all_elems = p->all_elems;
@@ -711,6 +776,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     LRH_CK(cudaMemset(P.best_flag, 0, sizeof(int32_t) * NI));
     LRH_CK(cudaMemset(P.err, 0, sizeof(int32_t)));
     LRH_CK(cudaMemset(P.sweeps, 0, sizeof(unsigned long long) * 8));
+    LRH_CK(cudaMemset(P.capped, 0, sizeof(unsigned long long) * 8));
     LRH_CK(cudaMemset(P.val64, 0, sizeof(double) * NI * R));
     LRH_CK(cudaMemset(P.val, 0, sizeof(double) * NI * R));
     LRH_CK(cudaMemset(P.st, 0, sizeof(IterState)));
@@ -763,8 +829,10 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         p->class_k = k2; p->class_count = c2; p->class_list = l2;
     }
     p->class_block.assign(p->class_k.size(), 128);
-    for (size_t c = 0; c < p->class_k.size(); ++c)
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
         if (p->class_k[c] >= 6) p->class_block[c] = LRH_SHAPE_CTA_FP32;   // CTA classes: FP32 back-transform
+        if (p->class_k[c] == 3 || p->class_k[c] == 4) p->class_block[c] = LRH_SHAPE_BLOCKS + 128;   // 2x2-block layout
+    }
     p->P.tc_backtransform = 0;
     if ((rc = plan_persistent(p))) return rc;
     LRH_CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
@@ -804,15 +872,19 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
     info->gamma_G = p->gamma_G;
     info->iteration = p->iteration;
     info->n_classes = (int32_t)p->class_k.size();
-    unsigned long long sw[8] = {0};
+    unsigned long long sw[8] = {0}, cap[8] = {0};
     LRH_CK(cudaMemcpyAsync(sw, p->P.sweeps, sizeof(sw), cudaMemcpyDeviceToHost, p->stream));
+    LRH_CK(cudaMemcpyAsync(cap, p->P.capped, sizeof(cap), cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
     for (size_t c = 0; c < p->class_k.size() && c < 8; ++c) {
         info->class_sites[c] = p->class_k[c];
         info->class_regions[c] = p->class_count[c];
         info->sweeps[c] = sw[p->class_k[c]];
+        info->sweep_capped[c] = cap[p->class_k[c]];
         info->class_block[c] = p->class_block[c];
     }
+    info->n_sites = p->n_sites;
+    info->kappa_G = p->kappa;
     info->concurrent_classes = (p->fused && p->persist_grid > 0) ? 2 : (p->concurrent ? 1 : 0);
     info->loop = effective_loop(p);
     info->persistent_grid = p->persist_grid;
@@ -833,7 +905,7 @@ int lrh_set_options(lrh_problem* p, const lrh_options* opts) {
     int rc = validate_options(opts);
     if (rc) return rc;
     DeviceGuard dg(p->device);
-    p->opt = *opts;
+    copy_options(p, opts);
     return push_state(p, false, 0.0, 0.0);
 }
 
@@ -923,9 +995,9 @@ int lrh_bound(lrh_problem* p, int32_t kind, double* out) {
         return fail(LRH_EINVAL, "unknown bound kind");
     }
     int rc = read_err(p);
-    if (rc) return rc;
-    std::copy(p->h_pinned, p->h_pinned + NI, out);
-    return LRH_OK;
+    if (rc && rc != LRH_ENOCONV) return rc;
+    std::copy(p->h_pinned, p->h_pinned + NI, out);   // with LRH_ENOCONV: valid, looser bounds
+    return rc;
 }
 
 int lrh_get_region_values(lrh_problem* p, int32_t kind, double* out) {
@@ -1171,6 +1243,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
     int sms = 0;
     LRH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     const bool force = (flags & 1) != 0;
+    if (!cache_path && p->opt.tune_cache) cache_path = p->opt.tune_cache;
     auto cache = force ? std::vector<std::pair<std::string, int>>() : read_cache(cache_path);
     std::vector<std::string> new_lines;
     for (size_t c = 0; c < p->class_k.size(); ++c) {
@@ -1203,9 +1276,11 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         int blk = 0;
         if (!cache_lookup(cache, key, &blk)) {
             float best = 1e30f;
-            for (int cand : {64, 128, 256, -64, -128, -256}) {
-                if (cand > 0 && cand < (1 << k)) continue;
+            for (int cand : {64, 128, 256, -64, -128, -256, LRH_SHAPE_BLOCKS + 64, LRH_SHAPE_BLOCKS + 128,
+                             LRH_SHAPE_BLOCKS + 256}) {
+                if (cand > 0 && cand < LRH_SHAPE_BLOCKS && cand < (1 << k)) continue;
                 if (cand < 0 && k != 2) continue;   // thread-per-region layout: 4 x 4 regions
+                if (cand > LRH_SHAPE_BLOCKS && k != 3 && k != 4) continue;   // 2x2-block layout: 8 x 8, 16 x 16
                 float ms = 0;
                 int rc = time_adaptive(p, 2.0f, [&]() -> int {
                     LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, cand));
@@ -1217,6 +1292,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         }
         p->class_block[c] = blk;
     }
+    p->plan.blk_mask = blk_mask_of(p);
     // Iteration driver: how the classes of a pass are launched (one after another, forked
     // streams, one launch) under the graph driver, and the persistent driver; each timed over
     // whole iterations on a saved copy of the multipliers and iteration scalars.
@@ -1310,6 +1386,9 @@ int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
     bool ok;
     if (k_sites >= 6) ok = block == LRH_SHAPE_CTA_FP32 || (block == LRH_SHAPE_CTA_TENSOR && k_sites == 7);
+    else if (block > LRH_SHAPE_BLOCKS)
+        ok = (k_sites == 3 || k_sites == 4) && (block - LRH_SHAPE_BLOCKS == 64 || block - LRH_SHAPE_BLOCKS == 128 ||
+                                                block - LRH_SHAPE_BLOCKS == 256);
     else ok = (block == 64 || block == 128 || block == 256 || (k_sites == 2 && (block == -64 || block == -128 || block == -256))) &&
               !(block > 0 && block < (1 << k_sites));
     if (!ok) return fail(LRH_EINVAL, "unsupported launch shape for this region size");
@@ -1320,6 +1399,7 @@ int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
                 const int bit = 1 << (k_sites - 6);
                 p->P.tc_backtransform = block == LRH_SHAPE_CTA_TENSOR ? (p->P.tc_backtransform | bit) : (p->P.tc_backtransform & ~bit);
             }
+            p->plan.blk_mask = blk_mask_of(p);
             drop_graphs(p);
             return LRH_OK;
         }
@@ -1354,6 +1434,113 @@ int lrh_synchronize(lrh_problem* p) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
     DeviceGuard dg(p->device);
     return read_err(p);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int lrh_theorem_parameters(const lrh_problem* p, double eps, double R, double c_frac, lrh_params* out) {
+    if (!p || !out) return fail(LRH_EINVAL, "NULL argument");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(LRH_EINVAL, "eps must be finite and > 0");
+    if (!(c_frac > 0.0 && c_frac < 1.0)) return fail(LRH_EINVAL, "c_frac must lie in (0, 1)");
+    const double n = (double)p->n_sites;
+    lrh_params r{};
+    r.n_sites = p->n_sites;
+    r.lambda_G = p->lambda_G;
+    r.gamma_G = p->gamma_G;
+    r.kappa_G = p->kappa;
+    r.beta = 2.0 * p->gamma_G / (n * eps);                     // Thm 5 / Thm 7: smoothing error eps/2
+    r.lhat = r.beta * p->lambda_G / 2.0;
+    r.c = c_frac / std::max(1, p->kappa);                      // Thm 4 / Thm 6: 0 < c < 1 / kappa_G
+    r.alpha = r.c * eps;
+    r.T_nesterov = -1;
+    r.T_subgradient = -1;
+    if (R > 0.0 && std::isfinite(R)) {
+        r.T_nesterov = (int64_t)std::ceil(2.0 * R * std::sqrt(p->gamma_G * p->lambda_G) / (n * eps)) - 1;
+        r.T_subgradient = (int64_t)std::ceil(R * R / (2.0 * r.c * (1.0 - r.c * p->kappa) * n * eps * eps));
+    }
+    *out = r;
+    return LRH_OK;
+}
+
+int lrh_reset(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    DeviceGuard dg(p->device);
+    const size_t m = sizeof(float2) * (size_t)p->n_inst * (size_t)p->msg_elems;
+    if (m) {
+        LRH_CK(cudaMemsetAsync(p->P.nu, 0, m, p->stream));
+        LRH_CK(cudaMemsetAsync(p->P.zeta, 0, m, p->stream));
+        LRH_CK(cudaMemsetAsync(p->P.nu_best, 0, m, p->stream));
+    }
+    std::vector<double> ninf(p->n_inst, -std::numeric_limits<double>::infinity());
+    LRH_CK(cudaMemcpyAsync(p->P.q_best, ninf.data(), sizeof(double) * p->n_inst, cudaMemcpyHostToDevice, p->stream));
+    LRH_CK(cudaMemsetAsync(p->P.best_flag, 0, sizeof(int32_t) * p->n_inst, p->stream));
+    int rc = push_state(p, true, 1.0, 0.0);
+    if (rc) return rc;
+    LRH_CK(cudaStreamSynchronize(p->stream));   // the host vector above must outlive the copy
+    return LRH_OK;
+}
+
+int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_bounds, int32_t* n_records,
+              double* bound_out) {
+    if (!p || !bound_out) return fail(LRH_EINVAL, "NULL argument");
+    if (max_records < 0 || (max_records > 0 && (!rec || !rec_bounds))) return fail(LRH_EINVAL, "bad record buffers");
+    DeviceGuard dg(p->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t NI = p->n_inst;
+    std::vector<double> cur((size_t)NI);
+    int32_t nrec = 0;
+    int64_t done = 0;
+    int status = LRH_OK;
+    bool stop = false;
+    if (n_records) *n_records = 0;
+    auto record = [&](double beta) -> int {
+        int r = lrh_bound(p, LRH_BOUND_CERTIFIED, cur.data());
+        if (r && r != LRH_ENOCONV) return r;
+        if (r == LRH_ENOCONV) status = LRH_ENOCONV;
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (nrec < max_records) {
+            rec[nrec] = lrh_record{done, secs, beta};
+            std::copy(cur.begin(), cur.end(), rec_bounds + (int64_t)nrec * NI);
+            ++nrec;
+            if (n_records) *n_records = nrec;
+        }
+        std::copy(cur.begin(), cur.end(), bound_out);
+        if (p->opt.deadline_s > 0.0 && secs > p->opt.deadline_s) stop = true;
+        return LRH_OK;
+    };
+    const int per = p->opt.iters_per_stage;
+    const int every = p->opt.certify_every > 0 ? p->opt.certify_every : std::max(per, 1);
+    int rc;
+    if (p->opt.variant == LRH_NESTEROV) {
+        std::vector<double> stages = p->beta_sched;
+        if (stages.empty()) stages.push_back(p->opt.beta);
+        for (size_t si = 0; si < stages.size() && !stop; ++si) {
+            p->opt.beta = stages[si];        // L_hat follows: lhat if set, else beta Lambda_G / 2
+            if ((rc = lrh_restart(p))) return rc;
+            for (int it = 0; it < per && !stop;) {
+                const int n = std::min(every, per - it);
+                if ((rc = lrh_step(p, n))) return rc;
+                it += n;
+                done += n;
+                if (p->opt.certify_every > 0 && (rc = record(stages[si]))) return rc;
+            }
+        }
+        if (p->opt.certify_every <= 0 && (rc = record(p->opt.beta))) return rc;
+    } else {
+        if ((rc = lrh_restart(p))) return rc;
+        for (int it = 0; it < per && !stop;) {
+            const int n = std::min(every, per - it);
+            if ((rc = lrh_step(p, n))) return rc;
+            it += n;
+            done += n;
+            if (p->opt.certify_every > 0 && (rc = record(0.0))) return rc;
+        }
+        if (p->opt.certify_every <= 0 && (rc = record(0.0))) return rc;
+    }
+    if (stop) return fail(LRH_EDEADLINE, "lrh_solve reached its deadline");
+    return status;
 }
 
 }  // extern "C"

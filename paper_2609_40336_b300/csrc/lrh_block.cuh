@@ -1,0 +1,366 @@
+// Region pass for regions of 3 and 4 sites (D = 8, 16) in the Hermitian 2x2-block layout, sm_103a:
+// device code shared by the per-class kernel (lrh_block.cu) and the one-launch / persistent
+// drivers (lrh_kernels.cu).
+//
+// A group of D lanes owns one region (32 / D regions per warp).  theta lives in shared memory as
+// the upper triangle of its D/2 x D/2 grid of 2x2 blocks (block (k, l), k <= l, holds rows 2k, 2k+1
+// and columns 2l, 2l+1), so every Hermitian pair of entries is stored and rotated once.  A sweep
+// of the cyclic two-sided Jacobi method runs D-1 rounds of the round-robin tournament with the
+// pairs always in slots (2k, 2k+1); the tournament's slot permutation is applied by writing every
+// rotated entry (i, j) to its next position (dst(i), dst(j)) (conjugated when that falls below the
+// diagonal) in a second buffer.  The permutation is the same in every round, so each lane computes
+// its source blocks and destination positions once.  Every round:
+//   1. lanes k < D/2 take the diagonal block (k, k): the rotation (c, w) that zeroes its
+//      off-diagonal entry and the two new diagonal entries (exact: the block becomes diagonal);
+//   2. lanes update the D(D-2)/8 off-diagonal blocks, B' = J_k^H B J_l (two-sided, one pass);
+//   3. lane s applies the column rotation and the tournament permutation to row s of V
+//      (registers, compile-time indices, two register arrays used in turn).
+// The rotation parameters use the fast reciprocal / reciprocal square root (rot_fast).
+// Arithmetic per round: 12 FMA-type instructions per stored entry of theta and 6 per entry of V,
+// against 18 per row entry (both triangles of theta, plus V) in the lane-row layout.
+// After the sweeps, the Gibbs state / ground projector, the partial traces and the values are
+// formed as in the lane-row pass (same conventions, same outputs).
+#pragma once
+#include "lrh_device.cuh"
+#include "lrh_internal.cuh"
+
+#include <cstdint>
+
+namespace lrh {
+namespace blk {
+
+using namespace dev;
+
+template <int D>
+struct Blk {
+    static constexpr int n = D / 2;                  // pairs per round
+    static constexpr int NB = n * (n + 1) / 2;       // stored blocks (k <= l)
+    static constexpr int NOFF = n * (n - 1) / 2;     // off-diagonal blocks
+    static constexpr int PER = (NOFF + D - 1) / D;   // off-diagonal blocks per lane
+    static constexpr int LD = D + 2;                 // padded row stride of the W / rho staging
+    // one buffer = two halves of NB float4: entries (0, 1) of every block, then entries (2, 3)
+    static constexpr size_t buf_bytes = (size_t)2 * NB * 16;
+    static constexpr size_t stage_bytes = (size_t)2 * D * LD * sizeof(float2);
+    static constexpr size_t union_bytes = 2 * buf_bytes > stage_bytes ? 2 * buf_bytes : stage_bytes;
+    static constexpr size_t per_group = union_bytes + n * sizeof(RotC<float>) + D * sizeof(float);
+};
+
+template <int D, int BLOCK>
+struct BlkSmem {
+    static constexpr size_t bytes = (BLOCK / D) * Blk<D>::per_group + 16;
+};
+
+// next slot of the entries in slot o (inverse of the tournament's rr_src)
+__host__ __device__ constexpr int rr_dst(int o, int D) {
+    return o == 0 ? 0 : (o == 1 ? 2 : ((o & 1) ? o - 2 : (o == D - 2 ? D - 1 : o + 2)));
+}
+
+template <int D>
+__device__ __forceinline__ int bidx(int k, int l) { return k * (D / 2) - ((k * (k - 1)) >> 1) + (l - k); }
+
+// float2 index (within one buffer) of entry (i, j), i <= j
+template <int D>
+__device__ __forceinline__ int eidx(int i, int j) {
+    const int e = ((i & 1) << 1) | (j & 1);
+    return (e >> 1) * (2 * Blk<D>::NB) + bidx<D>(i >> 1, j >> 1) * 2 + (e & 1);
+}
+
+// destination of entry (i, j), i <= j, after a round: its float2 index, negative (~index) when the
+// entry lands below the diagonal and is stored conjugated
+template <int D>
+__device__ __forceinline__ int dest(int i, int j) {
+    const int I = rr_dst(i, D), J = rr_dst(j, D);
+    return I <= J ? eidx<D>(I, J) : ~eidx<D>(J, I);
+}
+
+// Rotation of pair (p, q) from a_pp, a_qq, a_pq (the same rotation as rot_params_d) and the two
+// diagonal entries after it.  With h = a_qq - a_pp, den = |h| + sqrt(h^2 + 4 |a_pq|^2) and
+// q = 2 / den: t = -sgn(h) q |a_pq|, c = 1 / sqrt(1 + t^2) = rsqrt(1 + q^2 |a_pq|^2),
+// sigma = -sgn(h) q c, and t |a_pq| = -sgn(h) q |a_pq|^2, so |a_pq| itself is never needed:
+// one square root, one reciprocal and one reciprocal square root.  The rotation is unitary when
+// c^2 (1 + q^2 |a_pq|^2) = 1, whatever q is, so c gets one Newton step after the fast reciprocal
+// square root (about 1 ulp, like the IEEE forms); the fast square root and reciprocal only
+// perturb the angle, i.e. the pair's off-diagonal entry left before it is set to zero, an error
+// of the order of the rounding of the entries themselves.
+__device__ __forceinline__ void rot_fast(float app, float aqq, float br, float bi, RotC<float>& R, float2& dnew) {
+    const float h = aqq - app;
+    const float b2 = fmaf(br, br, bi * bi);
+    const float r2 = fmaf(h, h, 4.f * b2);
+    const float r = r2 > 0.f ? r2 * rsqrtf(r2) : 0.f;
+    const float den = fabsf(h) + r;
+    // den >= 2 |a_pq|; below 1e-18 the pair is diagonal at that absolute scale and is left as it
+    // is (identity rotation); above it q^2 <= 4e36 cannot overflow and q^2 |a_pq|^2 <= 1
+    const float q = den > 1e-18f ? __fdividef(2.f, den) : 0.f;
+    const float sg = h >= 0.f ? 1.f : -1.f;
+    const float x = fmaf(q * q, b2, 1.f);
+    float c = rsqrtf(x);
+    c = c * fmaf(-0.5f * x, c * c, 1.5f);   // Newton step: c^2 x = 1 to about one ulp
+    const float sig = -sg * q * c;
+    R.c = c;
+    R.wr = sig * br;
+    R.wi = sig * bi;
+    R.pad = 0.f;
+    const float tb = sg * q * b2;
+    dnew.x = app - tb;
+    dnew.y = aqq + tb;
+}
+
+template <int D, int BLOCK>
+__device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const PassIO& io,
+                                                     const int32_t* __restrict__ cls, const int32_t count, const int k,
+                                                     const int64_t tile) {
+    using B = Blk<D>;
+    constexpr int n = B::n, NB = B::NB, NOFF = B::NOFF, PER = B::PER, LD = B::LD;
+    constexpr int G = BLOCK / D;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x / D;
+    const int s = threadIdx.x % D;
+    unsigned char* base = smem_raw + g * B::per_group;
+    float2* bufA = reinterpret_cast<float2*>(base);
+    float2* bufB = bufA + 2 * NB * 2;
+    RotC<float>* prm = reinterpret_cast<RotC<float>*>(base + B::union_bytes);
+    float* pw = reinterpret_cast<float*>(prm + n);
+    __shared__ unsigned long long blk_sweeps, blk_capped;
+    if (threadIdx.x == 0) { blk_sweeps = 0ull; blk_capped = 0ull; }
+
+    const int64_t unit = tile * G + g;
+    const bool valid = unit < (int64_t)P.n_inst * count;
+    const int inst = valid ? (int)(unit / count) : 0;
+    const int r = valid ? cls[unit % count] : 0;
+    const bool nest = P.st->variant == 1;
+    const int max_sweeps = P.st->max_sweeps;
+    const Thetas T = pass_thetas(P, io);
+
+    // ---- assemble row s and store its upper part (the matrix is exactly Hermitian)
+    RegionInfo R;
+    {
+        float ar[D], ai[D];
+        if (valid) {
+            R = P.reg[r];
+            assemble_row_io<D>(P, R, inst, s, io, T, ar, ai);
+        } else {
+            R = RegionInfo{-1, -1, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (c >= s) bufA[eidx<D>(s, c)] = make_float2(ar[c], c == s ? 0.f : ai[c]);
+    }
+
+    // ---- blocks and destinations of every lane position (the same in every round and for every
+    //      region of the CTA): off-diagonal block j * D + s of lane s: byte offsets of the block
+    //      (first half) and of the rotations of its row and column pairs, the float2 indices of
+    //      its four entries' next positions, and +-1 for the entries stored conjugated
+    __shared__ int4 tab_off[PER * D];
+    __shared__ int4 tab_dst[PER * D];
+    __shared__ float4 tab_sgn[PER * D];
+    if (threadIdx.x < PER * D) {
+        const int j = threadIdx.x / D, ls = threadIdx.x % D;
+        int m = ls + D * j, kq = 0;
+        if (m >= NOFF) m = NOFF - 1;   // idle lane: a valid block, never stored
+        while (m >= n - 1 - kq) { m -= n - 1 - kq; ++kq; }
+        const int lq = kq + 1 + m;
+        tab_off[threadIdx.x] = make_int4(16 * bidx<D>(kq, lq), 16 * kq, 16 * lq, 0);
+        int d[4];
+        float sg[4];
+        for (int e = 0; e < 4; ++e) {
+            const int x = dest<D>(2 * kq + (e >> 1), 2 * lq + (e & 1));
+            d[e] = x < 0 ? ~x : x;
+            sg[e] = x < 0 ? -1.f : 1.f;
+        }
+        tab_dst[threadIdx.x] = make_int4(d[0], d[1], d[2], d[3]);
+        tab_sgn[threadIdx.x] = make_float4(sg[0], sg[1], sg[2], sg[3]);
+    }
+    __syncthreads();
+    const int sd = s < n ? bidx<D>(s, s) : 0;
+    // next positions of the diagonal block's entries (never conjugated: 0 and 3 stay on the
+    // diagonal, and entry 1 is written as zero)
+    const int d0 = dest<D>(2 * s, 2 * s), d3 = dest<D>(2 * s + 1, 2 * s + 1);
+    const int d1x = dest<D>(2 * s, 2 * s + 1), d1 = d1x < 0 ? ~d1x : d1x;
+
+    float vr[D], vi[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { vr[c] = (c == s) ? 1.f : 0.f; vi[c] = 0.f; }
+    __syncwarp();
+
+    // squared Frobenius norms: off-diagonal part (both triangles) and whole matrix
+    auto sums = [&](const float2* cur, float& off, float& all) {
+        const float4* c4 = reinterpret_cast<const float4*>(cur);
+        float o = 0.f, dg = 0.f;
+#pragma unroll 1
+        for (int j = 0; j < PER; ++j)
+            if (s + D * j < NOFF) {
+                const int b = tab_off[j * D + s].x >> 4;
+                const float4 h0 = c4[b], h1 = c4[NB + b];
+                o += h0.x * h0.x + h0.y * h0.y + h0.z * h0.z + h0.w * h0.w + h1.x * h1.x + h1.y * h1.y + h1.z * h1.z + h1.w * h1.w;
+            }
+        if (s < n) {
+            const float4 h0 = c4[sd], h1 = c4[NB + sd];
+            o += h0.z * h0.z + h0.w * h0.w;
+            dg = h0.x * h0.x + h1.z * h1.z;
+        }
+        off = 2.f * group_sum<D>(o);
+        all = off + group_sum<D>(dg);
+    };
+
+    // one round: rotations from the diagonal blocks of `cur`, all blocks rotated into `nxt` at
+    // their next positions, row s of V (x) rotated and written permuted into y
+    auto round = [&](const float2* cur, float2* nxt, float (&xr)[D], float (&xi)[D], float (&yr)[D], float (&yi)[D]) {
+        const float4* c4 = reinterpret_cast<const float4*>(cur);
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(cur);
+        const unsigned char* pb = reinterpret_cast<const unsigned char*>(prm);
+        if (s < n) {
+            const float4 h0 = c4[sd], h1 = c4[NB + sd];
+            RotC<float> Rk;
+            float2 dn;
+            rot_fast(h0.x, h1.z, h0.z, h0.w, Rk, dn);
+            prm[s] = Rk;
+            nxt[d0] = make_float2(dn.x, 0.f);
+            nxt[d3] = make_float2(dn.y, 0.f);
+            nxt[d1] = make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int j = 0; j < PER; ++j) {
+            if (PER * D == NOFF || s + D * j < NOFF) {
+                const int4 of = tab_off[j * D + s];
+                const float4 h0 = *reinterpret_cast<const float4*>(cb + of.x);
+                const float4 h1 = *reinterpret_cast<const float4*>(cb + of.x + 16 * NB);   // c4[NB + block]
+                float2 b00 = make_float2(h0.x, h0.y), b01 = make_float2(h0.z, h0.w);
+                float2 b10 = make_float2(h1.x, h1.y), b11 = make_float2(h1.z, h1.w);
+                const RotC<float> K = *reinterpret_cast<const RotC<float>*>(pb + of.y);
+                const RotC<float> Lr = *reinterpret_cast<const RotC<float>*>(pb + of.z);
+                two_sided<float>(b00, b01, b10, b11, K, Lr);
+                const int4 dd = tab_dst[j * D + s];
+                const float4 sg = tab_sgn[j * D + s];
+                nxt[dd.x] = make_float2(b00.x, sg.x * b00.y);
+                nxt[dd.y] = make_float2(b01.x, sg.y * b01.y);
+                nxt[dd.z] = make_float2(b10.x, sg.z * b10.y);
+                nxt[dd.w] = make_float2(b11.x, sg.w * b11.y);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            const RotC<float> Q = prm[q];
+            mix_cols(xr[2 * q], xi[2 * q], xr[2 * q + 1], xi[2 * q + 1], Q.c, Q.wr, Q.wi);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { yr[c] = xr[rr_src(c, D)]; yi[c] = xi[rr_src(c, D)]; }
+        __syncwarp();
+    };
+
+    float off2, norm2;
+    float2* cur = bufA;
+    float2* nxt = bufB;
+    sums(cur, off2, norm2);
+    const float thresh = 1e-12f * norm2;
+    int sweeps = 0;
+    for (;;) {
+        if (sweeps > 0) sums(cur, off2, norm2);
+        const bool done = (off2 <= thresh) || (sweeps >= max_sweeps);
+        if (__all_sync(kFull, done)) break;
+        ++sweeps;
+        float ur[D], ui[D];
+#pragma unroll 1
+        for (int rd = 0; rd + 1 < D - 1; rd += 2) {
+            round(cur, nxt, vr, vi, ur, ui);
+            round(nxt, cur, ur, ui, vr, vi);
+        }
+        round(cur, nxt, vr, vi, ur, ui);   // D - 1 rounds per sweep is odd
+        { float2* t = cur; cur = nxt; nxt = t; }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
+    }
+    // the slots are back in natural order: lambda_s on the diagonal, row s of V in (vr, vi)
+    const float lam = cur[eidx<D>(s, s)].x;
+    const float lmin = group_min<D>(lam);
+    float wgt, F;
+    if (nest) {
+        const float beta = (float)P.st->beta;
+        const float e = expf(-beta * (lam - lmin));
+        const float Z = group_sum<D>(e);
+        wgt = e / Z;
+        F = lmin - logf(Z) / beta;
+    } else {
+        const float tau = (float)P.st->degen_tol * fmaxf(1.0f, sqrtf(norm2));
+        const float in = (lam - lmin <= tau) ? 1.0f : 0.0f;
+        const float m = group_sum<D>(in);
+        wgt = in / m;
+        F = lmin;
+    }
+    __syncwarp();   // every lane has read its diagonal before the staging reuses the buffers
+    pw[s] = sqrtf(wgt);
+    float2* Wb = reinterpret_cast<float2*>(base);
+    float2* Rb = Wb + D * LD;
+    __syncwarp();
+    // W = V diag(sqrt(p)); rho = W W^dagger, row s per lane
+    float ur[D], ui[D];   // (the sweep loop's second V array is out of scope here)
+#pragma unroll
+    for (int c = 0; c < D; ++c) { const float q = pw[c]; ur[c] = vr[c] * q; ui[c] = vi[c] * q; }
+    {
+        float4* wrow = reinterpret_cast<float4*>(Wb + s * LD);
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) wrow[c] = make_float4(ur[2 * c], ui[2 * c], ur[2 * c + 1], ui[2 * c + 1]);
+    }
+    __syncwarp();
+    for (int j = s; j < D; ++j) {   // upper triangle of row s
+        const float4* wj = reinterpret_cast<const float4*>(Wb + j * LD);
+        float accr = 0.f, acci = 0.f;
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) {
+            const float4 x = wj[c];
+            accr += ur[2 * c] * x.x + ui[2 * c] * x.y;
+            acci += ui[2 * c] * x.x - ur[2 * c] * x.y;
+            accr += ur[2 * c + 1] * x.z + ui[2 * c + 1] * x.w;
+            acci += ui[2 * c + 1] * x.z - ur[2 * c + 1] * x.w;
+        }
+        Rb[s * LD + j] = make_float2(accr, j == s ? 0.f : acci);
+        if (j > s) Rb[j * LD + s] = make_float2(accr, -acci);   // exactly Hermitian
+    }
+    __syncwarp();
+    if (valid) {
+        if (R.rho_off >= 0) {
+            float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off + (int64_t)s * D);
+            const float4* srcr = reinterpret_cast<const float4*>(Rb + s * LD);
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c) dst[c] = srcr[c];
+        }
+        float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask;
+            const int Mc = (D - 1) & ~M;
+            const int kf = pi.kf;
+            const int Df = 1 << kf;
+            const int nrest = D >> kf;
+            for (int idx = s; idx < Df * Df; idx += D) {
+                const int ra = pdep_bits(idx >> kf, M);
+                const int rb = pdep_bits(idx & (Df - 1), M);
+                float accr = 0.f, acci = 0.f;
+                for (int c = 0; c < nrest; ++c) {
+                    const int x = pdep_bits(c, Mc);
+                    const float2 v = Rb[(ra | x) * LD + (rb | x)];
+                    accr += v.x;
+                    acci += v.y;
+                }
+                trb[pi.off + idx] = make_float2(accr, acci);
+            }
+        }
+        if (s == 0) {
+            P.val[(int64_t)inst * P.n_regions + r] = (double)F;
+            if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        }
+    }
+    __syncthreads();
+    if (valid && s == 0) {
+        atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+        if (off2 > thresh) atomicAdd(&blk_capped, 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
+    if (threadIdx.x == 0 && blk_capped) atomicAdd(&P.capped[k], blk_capped);
+}
+
+}  // namespace blk
+}  // namespace lrh

@@ -27,6 +27,9 @@ namespace lrh {
 
 namespace {
 
+using dev::RotC;
+using dev::rot_params_d;
+using dev::two_sided;
 constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int rr_src_c(int s, int D) {
@@ -53,12 +56,7 @@ template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
 template <> struct V2<double> { using t = double2; };
 
-template <typename T> struct alignas(4 * sizeof(T)) RotC { T c, wr, wi, pad; };
 
-template <typename T>
-__device__ __forceinline__ T sqrt_t(T x) { return sqrt(x); }
-template <>
-__device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
 
 __device__ __forceinline__ int tri(int i, int j, int D) { return i * D - ((i * (i - 1)) >> 1) + (j - i); }
 
@@ -81,11 +79,15 @@ struct Packed {
     }
     __device__ __forceinline__ C2 dget(int i) const { return a[tri(i, i, D)]; }
     __device__ __forceinline__ void dset(int i, C2 v) const { a[tri(i, i, D)] = v; }
-    // sums of |a_ij|^2 over the upper triangle (diagonal included) and over the diagonal
+    // sums of |a_ij|^2 over the strict upper triangle and over the diagonal (summed separately:
+    // the off-diagonal mass must not come out of a difference of two large sums)
     template <int NT>
-    __device__ __forceinline__ void sums(T& upper, T& diag) const {
-        upper = T(0); diag = T(0);
-        for (int e = threadIdx.x; e < D * (D + 1) / 2; e += NT) { const C2 v = a[e]; upper += v.x * v.x + v.y * v.y; }
+    __device__ __forceinline__ void sums(T& offd, T& diag) const {
+        offd = T(0); diag = T(0);
+        for (int e = threadIdx.x; e < D * D; e += NT) {
+            const int i = e / D, j = e - (e / D) * D;
+            if (i < j) { const C2 v = a[tri(i, j, D)]; offd += v.x * v.x + v.y * v.y; }
+        }
         for (int i = threadIdx.x; i < D; i += NT) { const C2 v = a[tri(i, i, D)]; diag += v.x * v.x + v.y * v.y; }
     }
 };
@@ -117,47 +119,22 @@ struct Full {
     }
     __device__ __forceinline__ C2 dget(int i) const { return a[i * (D + 2)]; }
     __device__ __forceinline__ void dset(int i, C2 v) const { a[i * (D + 2)] = v; }
-    // sums of |a_ij|^2 over the upper triangle (diagonal included) and over the diagonal
+    // sums of |a_ij|^2 over the strict upper triangle and over the diagonal (summed separately:
+    // the off-diagonal mass must not come out of a difference of two large sums)
     template <int NT>
-    __device__ __forceinline__ void sums(T& upper, T& diag) const {
-        upper = T(0);
+    __device__ __forceinline__ void sums(T& offd, T& diag) const {
+        offd = T(0);
         diag = T(0);
         for (int e = threadIdx.x; e < D * D; e += NT) {
             const int i = e / D, j = e - (e / D) * D;
             if (i <= j) {
                 const C2 v = a[i * (D + 1) + j];
                 const T m = v.x * v.x + v.y * v.y;
-                upper += m;
-                if (i == j) diag += m;
+                if (i == j) diag += m; else offd += m;
             }
         }
     }
 };
-
-// B' = J_k^H B J_l on a 2x2 block, J = [[c, -w], [conj(w), c]].
-template <typename T, typename C2>
-__device__ __forceinline__ void two_sided(C2& b00, C2& b01, C2& b10, C2& b11, const RotC<T>& K, const RotC<T>& Lr) {
-    // C = B J_l : x_p' = c x_p + conj(w) x_q ; x_q' = -w x_p + c x_q   (per row)
-    auto colmix = [&](C2& xp, C2& xq) {
-        const T pr = Lr.c * xp.x + (Lr.wr * xq.x + Lr.wi * xq.y);
-        const T pi = Lr.c * xp.y + (Lr.wr * xq.y - Lr.wi * xq.x);
-        const T qr = Lr.c * xq.x - (Lr.wr * xp.x - Lr.wi * xp.y);
-        const T qi = Lr.c * xq.y - (Lr.wr * xp.y + Lr.wi * xp.x);
-        xp.x = pr; xp.y = pi; xq.x = qr; xq.y = qi;
-    };
-    colmix(b00, b01);
-    colmix(b10, b11);
-    // J_k^H C : y_p' = c y_p + w y_q ; y_q' = -conj(w) y_p + c y_q   (per column)
-    auto rowmix = [&](C2& yp, C2& yq) {
-        const T pr = K.c * yp.x + (K.wr * yq.x - K.wi * yq.y);
-        const T pi = K.c * yp.y + (K.wr * yq.y + K.wi * yq.x);
-        const T qr = K.c * yq.x - (K.wr * yp.x + K.wi * yp.y);
-        const T qi = K.c * yq.y - (K.wr * yp.y - K.wi * yp.x);
-        yp.x = pr; yp.y = pi; yq.x = qr; yq.y = qi;
-    };
-    rowmix(b00, b10);
-    rowmix(b01, b11);
-}
 
 // V rows in registers: a warp holds 8 rows x 4 column chunks, lane = 8 chunk + (row mod 8).
 // The 8 lanes of a quarter-warp share one chunk, so the rotation parameters they read are one
@@ -210,39 +187,18 @@ struct CtaSmem {
     static constexpr size_t bytes = off_mbar + 32;
 };
 
-// Rotation J = [[c, -w], [conj(w), c]], w = sigma a_pq, of pair (p, q) from a_pp, a_qq, a_pq
-// (h = a_qq - a_pp, r = sqrt(h^2 + 4|a_pq|^2), t = -sgn(h) 2|a_pq| / (|h| + r), c = 1 / sqrt(1 + t^2),
-// sigma = -sgn(h) 2 c / (|h| + r)), and the diagonal after it, a_pp + t |a_pq| and a_qq - t |a_pq|.
-template <typename T>
-__device__ __forceinline__ void rot_params_d(T app, T aqq, T br, T bi, RotC<T>& R, typename V2<T>::t& dnew) {
-    const T h = aqq - app;
-    const T b2 = br * br + bi * bi;
-    const T r = sqrt_t<T>(h * h + T(4) * b2);
-    const T den = fabs(h) + r;
-    const T sg = h >= T(0) ? T(1) : T(-1);
-    const T bn = sqrt_t<T>(b2);
-    T t = T(0), sig = T(0);
-    if (den > T(0)) t = -sg * T(2) * bn / den;
-    const T c = T(1) / sqrt_t<T>(T(1) + t * t);
-    if (den > T(0)) sig = -sg * T(2) * c / den;
-    R.c = c;
-    R.wr = sig * br;
-    R.wi = sig * bi;
-    R.pad = T(0);
-    dnew.x = app + t * bn;
-    dnew.y = aqq - t * bn;
-}
-
 // Cyclic Jacobi on the Hermitian matrix behind accessor A; V (if WANT_V) holds row `row`,
 // columns [chunk * W, chunk * W + W) in slot order.  Two barriers per round: after the rotation
 // parameters, and after the block updates (the slot map is double-buffered and its next
-// state written during the update phase).  Returns the sweeps run.
+// state written during the update phase).  Returns the sweeps run; `off_out` receives the
+// squared Frobenius norm of the off-diagonal part left at exit.
 // (Computing the next round's rotations inside the block updates, to save the first barrier,
 // measured slower: the 64 parameter computations then fall on many warps, each of which runs
 // the divisions and square roots for one lane, instead of two warps running them for all.)
 template <int D, typename T, bool WANT_V, typename Acc>
 __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
-                          T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out) {
+                          T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out,
+                          T& off_out) {
     using C2 = typename V2<T>::t;
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
@@ -261,7 +217,7 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
     const int chunk = vchunk_of(t);
     T up, dg;
     A.template sums<NT>(up, dg);
-    const T norm2 = T(2) * block_sum<NT>(up, red) - block_sum<NT>(dg, red);
+    const T norm2 = T(2) * block_sum<NT>(up, red) + block_sum<NT>(dg, red);
     norm2_out = norm2;
     const T thresh = tol2 * norm2;
     int* ix = idx0;
@@ -269,7 +225,8 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
     int sweeps = 0;
     for (;;) {
         A.template sums<NT>(up, dg);
-        const T off = T(2) * (block_sum<NT>(up, red) - block_sum<NT>(dg, red));
+        const T off = T(2) * block_sum<NT>(up, red);
+        off_out = off;
         if (off <= thresh || sweeps >= max_sweeps) break;
         ++sweeps;
         for (int r = 0; r < D - 1; ++r) {
@@ -543,8 +500,8 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
 template <int D, int OFF>
 __device__ __forceinline__ void stage_rows(unsigned char* hi, unsigned char* lo, int row, const float* q,
                                            const float (&vr)[D / 4], const float (&vi)[D / 4], int c0) {
-#pragma unroll
     constexpr int KC = TcKC<D>::v;
+#pragma unroll
     for (int g = 0; g < KC / 8; ++g) {   // K groups of 4: real parts of c0 + 4g .. c0 + 4g + 3
         float wr[4], wi[4];
 #pragma unroll
@@ -608,11 +565,15 @@ __device__ bool backtransform_tc(const DevProblem& P, unsigned char* sm, float* 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    int last = -1;   // last chunk whose MMAs were issued and committed
     for (int j = 0; j < NCH; ++j) {
         const int b = j & 1;
         unsigned char* hi = sm + (size_t)(2 * b) * PART;
         unsigned char* lo = hi + PART;
-        if (j >= 2 && !tc::wait_parity(b ? mb1 : mb0, (uint32_t)((j / 2 - 1) & 1))) ok = false;
+        // the buffer is free once the MMAs of chunk j - 2 have completed; after a timed-out wait
+        // (any thread) nothing more is staged or issued
+        const bool late = j >= 2 && !tc::wait_parity(b ? mb1 : mb0, (uint32_t)((j / 2 - 1) & 1));
+        if (__syncthreads_or(late)) { ok = false; break; }
         const int c0 = KC / 2 * j;            // first c of the chunk
         if (chunk == c0 / W) {   // the chunk's KC / 2 columns start at 0 or at W / 2 of the thread's W
             if (c0 % W == 0) tc::stage_rows<D, 0>(hi, lo, row, pw, vr, vi, c0);
@@ -638,9 +599,11 @@ __device__ bool backtransform_tc(const DevProblem& P, unsigned char* sm, float* 
             }
             tc::commit(b ? mb1 : mb0);
         }
+        last = j;
     }
-    // the last commit covers every MMA issued before it
-    if (!tc::wait_parity(((NCH - 1) & 1) ? mb1 : mb0, (uint32_t)(((NCH - 1) / 2) & 1))) ok = false;
+    // the last commit covers every MMA issued before it: wait for it (bounded) before the
+    // accumulators are read and the tensor memory is released
+    if (last >= 0 && !tc::wait_parity((last & 1) ? mb1 : mb0, (uint32_t)((last / 2) & 1))) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // accumulators -> padded planes (the operand buffers are free now)
     float* Rr = reinterpret_cast<float*>(sm);
@@ -707,8 +670,9 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     float vr[W], vi[W];
 #pragma unroll
     for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
-    float norm2;
-    const int sweeps = jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2);
+    float norm2, off2;
+    const int sweeps =
+        jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2, off2);
     // the slot maps are back to the identity after whole sweeps: diag = eigenvalues
     if (t < D) lam[t] = A.dget(A.sig(t)).x;
     __syncthreads();
@@ -837,6 +801,7 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
         P.val[(int64_t)inst * P.n_regions + r] = (double)F;
         if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
         atomicAdd(&P.sweeps[k], (unsigned long long)sweeps);
+        if (off2 > 1e-12f * norm2) atomicAdd(&P.capped[k], 1ull);
     }
 }
 
@@ -862,13 +827,16 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
     assemble_packed<D, double>(P, R, inst, A, msg, nullptr, 0.0f, true);
     __syncthreads();
     double vr[W], vi[W];
-    double norm2;
-    jacobi_cta<D, double, false>(A, prm, idx0, idx1, tab, red, vr, vi, 40, 1e-28, norm2);
+    double norm2, off2;
+    jacobi_cta<D, double, false>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->cert_sweeps, 1e-28, norm2, off2);
     double lmin = buf[0].x;
     for (int i = 1; i < D; ++i) lmin = fmin(lmin, buf[tri(i, i, D)].x);
+    // Weyl: lambda_min >= min_i a_ii - ||offdiag||_F, a lower bound also when the cap stopped it
+    lmin -= sqrt(off2);
     if (t == 0) {
         P.val64[(int64_t)inst * P.n_regions + r] = lmin;
         if (!isfinite(lmin)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        if (off2 > 1e-28 * norm2) atomicOr(P.err, DEV_ERR_NOCONV);
     }
 }
 

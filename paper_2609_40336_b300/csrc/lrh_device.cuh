@@ -113,13 +113,70 @@ __device__ __forceinline__ void mix_cols(T& pr, T& pi, T& qr, T& qi, T c, T wr, 
     pr = npr; pi = npi; qr = nqr; qi = nqi;
 }
 
+// ------------------------------------------------------------------ 2x2-block Jacobi helpers
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using t = float2; };
+template <> struct Cplx<double> { using t = double2; };
+
+template <typename T> struct alignas(4 * sizeof(T)) RotC { T c, wr, wi, pad; };
+
+// Rotation J = [[c, -w], [conj(w), c]], w = sigma a_pq, of pair (p, q) from a_pp, a_qq, a_pq
+// (h = a_qq - a_pp, r = sqrt(h^2 + 4|a_pq|^2), t = -sgn(h) 2|a_pq| / (|h| + r), c = 1 / sqrt(1 + t^2),
+// sigma = -sgn(h) 2 c / (|h| + r)), and the diagonal after it, a_pp + t |a_pq| and a_qq - t |a_pq|.
+template <typename T>
+__device__ __forceinline__ void rot_params_d(T app, T aqq, T br, T bi, RotC<T>& R, typename Cplx<T>::t& dnew) {
+    const T h = aqq - app;
+    const T b2 = br * br + bi * bi;
+    const T r = my_sqrt(h * h + T(4) * b2);
+    const T den = fabs(h) + r;
+    const T sg = h >= T(0) ? T(1) : T(-1);
+    const T bn = my_sqrt(b2);
+    T t = T(0), sig = T(0);
+    if (den > T(0)) t = -sg * T(2) * bn / den;
+    const T c = T(1) / my_sqrt(T(1) + t * t);
+    if (den > T(0)) sig = -sg * T(2) * c / den;
+    R.c = c;
+    R.wr = sig * br;
+    R.wi = sig * bi;
+    R.pad = T(0);
+    dnew.x = app + t * bn;
+    dnew.y = aqq - t * bn;
+}
+
+// B' = J_k^H B J_l on a 2x2 block, J = [[c, -w], [conj(w), c]].
+template <typename T, typename C2>
+__device__ __forceinline__ void two_sided(C2& b00, C2& b01, C2& b10, C2& b11, const RotC<T>& K, const RotC<T>& Lr) {
+    // C = B J_l : x_p' = c x_p + conj(w) x_q ; x_q' = -w x_p + c x_q   (per row)
+    auto colmix = [&](C2& xp, C2& xq) {
+        const T pr = Lr.c * xp.x + (Lr.wr * xq.x + Lr.wi * xq.y);
+        const T pi = Lr.c * xp.y + (Lr.wr * xq.y - Lr.wi * xq.x);
+        const T qr = Lr.c * xq.x - (Lr.wr * xp.x - Lr.wi * xp.y);
+        const T qi = Lr.c * xq.y - (Lr.wr * xp.y + Lr.wi * xp.x);
+        xp.x = pr; xp.y = pi; xq.x = qr; xq.y = qi;
+    };
+    colmix(b00, b01);
+    colmix(b10, b11);
+    // J_k^H C : y_p' = c y_p + w y_q ; y_q' = -conj(w) y_p + c y_q   (per column)
+    auto rowmix = [&](C2& yp, C2& yq) {
+        const T pr = K.c * yp.x + (K.wr * yq.x - K.wi * yq.y);
+        const T pi = K.c * yp.y + (K.wr * yq.y + K.wi * yq.x);
+        const T qr = K.c * yq.x - (K.wr * yp.x + K.wi * yp.y);
+        const T qi = K.c * yq.y - (K.wr * yp.y - K.wi * yp.x);
+        yp.x = pr; yp.y = pi; yq.x = qr; yq.y = qi;
+    };
+    rowmix(b00, b10);
+    rowmix(b01, b11);
+}
+
 // Cyclic complex Jacobi on the D x D Hermitian matrix held by a group of D lanes (row per
 // lane).  Returns the sweeps run (uniform over the warp).  On return the slots are in natural
 // order: lane s holds lambda_s on its diagonal entry and, if WANT_V, row s of V whose column c
-// is the eigenvector of lambda_c.  `norm2` receives ||theta||_F^2.
+// is the eigenvector of lambda_c.  `norm2` receives ||theta||_F^2 and `off2` the squared
+// Frobenius norm of the off-diagonal part left at exit (at most tol2 * norm2 unless the sweep
+// cap stopped the iteration first).
 template <int D, typename T, bool WANT_V>
 __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], T (&vi)[D], const int s,
-                                            Rot<T>* prm, const int max_sweeps, const T tol2, T& norm2) {
+                                            Rot<T>* prm, const int max_sweeps, const T tol2, T& norm2, T& off2) {
     T n2 = T(0);
 #pragma unroll
     for (int c = 0; c < D; ++c) n2 += ar[c] * ar[c] + ai[c] * ai[c];
@@ -132,6 +189,7 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
 #pragma unroll
         for (int c = 0; c < D; ++c) off += (c == s) ? T(0) : (ar[c] * ar[c] + ai[c] * ai[c]);
         off = group_sum<D>(off);
+        off2 = off;
         const bool done = (off <= thresh) || (sweeps >= max_sweeps);
         if (__all_sync(kFull, done)) break;
         ++sweeps;

@@ -50,7 +50,7 @@ struct IterState {
     int32_t variant;
     int32_t step_rule;
     int32_t max_sweeps;
-    int32_t pad;
+    int32_t cert_sweeps;   // sweep cap of the FP64 certification Jacobi
 };
 
 // Inputs and outputs of one region pass.  A "pending" pass first applies the previous
@@ -86,8 +86,10 @@ __host__ __device__ inline RegionInfo uniform_region(const RegionInfo& f, int64_
     return R;
 }
 
-// Error bits raised by kernels.
-enum : int32_t { DEV_ERR_NUMERIC = 1, DEV_ERR_TIMEOUT = 2 };
+// Error bits raised by kernels.  DEV_ERR_NOCONV: an FP64 certification Jacobi stopped at its
+// sweep cap with off-diagonal mass above the convergence threshold (its value is still a valid
+// lower bound: the Weyl correction below covers the remaining off-diagonal part).
+enum : int32_t { DEV_ERR_NUMERIC = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_NOCONV = 4 };
 
 struct DevProblem {
     int32_t n_inst;
@@ -132,6 +134,7 @@ struct DevProblem {
     IterState* st;
     int32_t* err;
     unsigned long long* sweeps;   // [8] per size class (indexed by k)
+    unsigned long long* capped;   // [8] per size class: FP32 eigensolves stopped by the sweep cap
     // adjoint (allocated on the first lrh_vjp call)
     int64_t all_elems;     // complex entries of the every-region arena per instance
     int32_t n_terms;
@@ -150,6 +153,11 @@ int set_last_error(int code, const std::string& msg);
 // problem creation, outside any stream capture.
 cudaError_t prepare_kernels();
 cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128)
+cudaError_t prepare_blk_kernels();   // lrh_block.cu (D = 8, 16, 2x2-block layout)
+// D = 8, 16 in the Hermitian 2x2-block layout, `threads` per CTA (64, 128 or 256)
+cudaError_t launch_region_pass_blk(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
+                                   int32_t class_count, cudaStream_t s, int threads);
+constexpr int kShapeBlocks = 4096;   // LRH_SHAPE_BLOCKS
 cudaError_t launch_region_pass_cta(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
                                    int32_t class_count, cudaStream_t s);
 cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
@@ -168,7 +176,7 @@ cudaError_t launch_update(const DevProblem& P, int par, int mode, cudaStream_t s
 cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_best, cudaStream_t s);
 cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double t, int set_theta_t,
                              double beta, double inv_lhat, double alpha, double degen_tol,
-                             int variant, int step_rule, int max_sweeps, cudaStream_t s);
+                             int variant, int step_rule, int max_sweeps, int cert_sweeps, cudaStream_t s);
 cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t s);
 
 // Adjoint (lrh_vjp.cu): theta_bar per region for the classes, then nu_bar and term cotangents.
@@ -194,6 +202,7 @@ struct PersistPlan {
     int32_t n;            // iterations
     int32_t nesterov;     // 1: fused Alg. 2 passes; 0: Alg. 1 iterations
     int32_t par0;         // Alg. 1: parity of the first iteration
+    int32_t blk_mask;     // bit k: class k (3 or 4 sites) runs in the 2x2-block layout
     unsigned* bar;        // device arrival counter of the grid barrier (zeroed by launch_persistent)
     unsigned expect;      // arrivals per barrier (the grid; set by launch_persistent)
 };

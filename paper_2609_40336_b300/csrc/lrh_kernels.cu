@@ -22,6 +22,7 @@
 // certification pass (lambda_min of theta rebuilt in FP64) and by the bound reduction.
 #include "lrh_internal.cuh"
 #include "lrh_device.cuh"
+#include "lrh_block.cuh"
 
 #include <cfloat>
 #include <cmath>
@@ -60,8 +61,8 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
     float2* Wb = reinterpret_cast<float2*>(base + (D / 2) * sizeof(Rot<float>));
     float2* Rb = Wb + D * LD;
     float* pw = reinterpret_cast<float*>(Rb + D * LD);
-    __shared__ unsigned long long blk_sweeps;
-    if (threadIdx.x == 0) blk_sweeps = 0ull;
+    __shared__ unsigned long long blk_sweeps, blk_capped;
+    if (threadIdx.x == 0) { blk_sweeps = 0ull; blk_capped = 0ull; }
 
     const int64_t unit = tile * G + g;
     const bool valid = unit < (int64_t)P.n_inst * count;
@@ -97,8 +98,8 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
 #pragma unroll
     for (int c = 0; c < D; ++c) { vr[c] = (c == s) ? 1.f : 0.f; vi[c] = 0.f; }
 
-    float norm2;
-    const int sweeps = jacobi_lanes<D, float, true>(ar, ai, vr, vi, s, prm, max_sweeps, 1e-12f, norm2);
+    float norm2, off2;
+    const int sweeps = jacobi_lanes<D, float, true>(ar, ai, vr, vi, s, prm, max_sweeps, 1e-12f, norm2, off2);
 
     // eigenvalue of slot s, value and state weights
     float e0, e1;
@@ -195,11 +196,15 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
             if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
         }
     }
-    // sweep accounting (regions x sweeps), one global atomic per block
+    // sweep accounting (regions x sweeps, regions stopped by the sweep cap), one global atomic per block
     __syncthreads();
-    if (valid && s == 0) atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+    if (valid && s == 0) {
+        atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+        if (off2 > 1e-12f * norm2) atomicAdd(&blk_capped, 1ull);
+    }
     __syncthreads();
     if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
+    if (threadIdx.x == 0 && blk_capped) atomicAdd(&P.capped[k], blk_capped);
 }
 
 template <int D, int BLOCK>
@@ -302,8 +307,8 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem P, const PassIO io,
                                                                const int32_t* __restrict__ cls, const int32_t count,
                                                                const int k) {
-    __shared__ unsigned long long blk_sweeps;
-    if (threadIdx.x == 0) blk_sweeps = 0ull;
+    __shared__ unsigned long long blk_sweeps, blk_capped;
+    if (threadIdx.x == 0) { blk_sweeps = 0ull; blk_capped = 0ull; }
     const Thetas T = pass_thetas(P, io);
     if (io.writer && blockIdx.x == 0 && threadIdx.x == 0) advance_theta(P, io);
     __syncthreads();
@@ -381,8 +386,9 @@ __global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem 
             for (int j = 0; j < 4; ++j) n2 += ar[i][j] * ar[i][j] + ai[i][j] * ai[i][j];
         const float thresh = 1e-12f * n2;
         const int max_sweeps = P.st->max_sweeps;
+        float off = 0.f;
         for (;;) {
-            float off = 0.f;
+            off = 0.f;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -466,9 +472,11 @@ __global__ void __launch_bounds__(BLOCK) region_pass_t4_kernel(const DevProblem 
         P.val[(int64_t)inst * P.n_regions + r] = (double)F;
         if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
         atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+        if (off > thresh) atomicAdd(&blk_capped, 1ull);
     }
     __syncthreads();
     if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
+    if (threadIdx.x == 0 && blk_capped) atomicAdd(&P.capped[k], blk_capped);
 }
 
 // ---------------------------------------------------------------- FP64 certification
@@ -498,15 +506,19 @@ __global__ void __launch_bounds__(kBlock) certify_kernel(const DevProblem P, con
 #pragma unroll
         for (int c = 0; c < D; ++c) { ar[c] = 0.0; ai[c] = 0.0; }
     }
-    double norm2;
-    jacobi_lanes<D, double, false>(ar, ai, vr, vi, s, prm, 40, 1e-28, norm2);
+    double norm2, off2;
+    jacobi_lanes<D, double, false>(ar, ai, vr, vi, s, prm, P.st->cert_sweeps, 1e-28, norm2, off2);
     double e0, e1;
     pick_pair<D>(ar, s, e0, e1);
     const double lam = (s & 1) ? e1 : e0;
-    const double lmin = group_min<D>(lam);
+    // Weyl: the rotated matrix is diag(a) + E with ||E||_2 <= ||E||_F = sqrt(off2), so
+    // lambda_min >= min_i a_ii - sqrt(off2): a lower bound even when the sweep cap stopped the
+    // iteration (then flagged); at convergence the correction is below 1e-14 ||theta||_F.
+    const double lmin = group_min<D>(lam) - sqrt(off2);
     if (valid && s == 0) {
         P.val64[(int64_t)inst * P.n_regions + r] = lmin;
         if (!isfinite(lmin)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        if (off2 > 1e-28 * norm2) atomicOr(P.err, DEV_ERR_NOCONV);
     }
 }
 
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, con
 
 __global__ void set_state_kernel(IterState* st, int par, double theta, double t, int set_theta_t, double beta,
                                  double inv_lhat, double alpha, double degen_tol, int variant, int step_rule,
-                                 int max_sweeps) {
+                                 int max_sweeps, int cert_sweeps) {
     if (set_theta_t) {
         st->theta[par] = theta;
         st->t[par] = t;
@@ -650,6 +662,7 @@ __global__ void set_state_kernel(IterState* st, int par, double theta, double t,
     st->variant = variant;
     st->step_rule = step_rule;
     st->max_sweeps = max_sweeps;
+    st->cert_sweeps = cert_sweeps;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -757,9 +770,15 @@ __device__ __forceinline__ void plan_tile(const DevProblem& P, const PersistPlan
     } else if (k == 2) {
         region_pass_impl<4, kBlock>(P, io, cls, count, 2, lt);
     } else if (k == 3) {
-        if constexpr (KMAX >= 3) region_pass_impl<8, kBlock>(P, io, cls, count, 3, lt);
+        if constexpr (KMAX >= 3) {
+            if ((L.blk_mask >> 3) & 1) blk::region_pass_blk_impl<8, kBlock>(P, io, cls, count, 3, lt);
+            else region_pass_impl<8, kBlock>(P, io, cls, count, 3, lt);
+        }
     } else {
-        if constexpr (KMAX >= 4) region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
+        if constexpr (KMAX >= 4) {
+            if ((L.blk_mask >> 4) & 1) blk::region_pass_blk_impl<16, kBlock>(P, io, cls, count, 4, lt);
+            else region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
+        }
     }
 }
 
@@ -809,7 +828,9 @@ __global__ void __launch_bounds__(kBlock) __maxnreg__(PersistCap<KMAX>::v)
 template <int KMAX>
 size_t persist_smem() {
     constexpr int D = 1 << KMAX;
-    return PassSmem<(D < 4 ? 4 : D), kBlock>::bytes;
+    constexpr size_t a = PassSmem<(D < 4 ? 4 : D), kBlock>::bytes;
+    constexpr size_t b = KMAX >= 3 ? blk::BlkSmem<(D >= 8 ? D : 8), kBlock>::bytes : 0;
+    return a > b ? a : b;
 }
 
 template <int KMAX>
@@ -885,12 +906,15 @@ cudaError_t prepare_kernels() {
     if ((e = set_pass_attrs<8>()) != cudaSuccess) return e;
     if ((e = set_pass_attrs<16>()) != cudaSuccess) return e;
     if ((e = set_pass_attrs<32>()) != cudaSuccess) return e;
+    if ((e = prepare_blk_kernels()) != cudaSuccess) return e;
     return prepare_cta_kernels();
 }
 
 cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, const int32_t* cls, int32_t count,
                                cudaStream_t s, int block) {
     if (count <= 0) return cudaSuccess;
+    if (block > kShapeBlocks && (k == 3 || k == 4))
+        return launch_region_pass_blk(P, io, k, cls, count, s, block - kShapeBlocks);
     if (block > 0 && block != 64 && block != 256) block = 128;
     if (block < 0 && k != 2) block = 128;   // the one-thread-per-region layout exists for 4 x 4 only
     if (k == 1 && block < 0) block = 128;
@@ -1003,9 +1027,9 @@ cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_bes
 
 cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double t, int set_theta_t, double beta,
                              double inv_lhat, double alpha, double degen_tol, int variant, int step_rule,
-                             int max_sweeps, cudaStream_t s) {
+                             int max_sweeps, int cert_sweeps, cudaStream_t s) {
     set_state_kernel<<<1, 1, 0, s>>>(P.st, par, theta, t, set_theta_t, beta, inv_lhat, alpha, degen_tol, variant,
-                                     step_rule, max_sweeps);
+                                     step_rule, max_sweeps, cert_sweeps);
     return cudaGetLastError();
 }
 

@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, con
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) { vr[c] = (c == s) ? 1.f : 0.f; vi[c] = 0.f; }
-    float norm2;
-    jacobi_lanes<D, float, true>(ar, ai, vr, vi, s, prm, P.st->max_sweeps, 1e-12f, norm2);
+    float norm2, off2;
+    jacobi_lanes<D, float, true>(ar, ai, vr, vi, s, prm, P.st->max_sweeps, 1e-12f, norm2, off2);
     float e0, e1;
     pick_pair<D>(ar, s, e0, e1);
     const float lk = (s & 1) ? e1 : e0;

@@ -24,9 +24,10 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence[Sequence[int]],
-            term_mats: Sequence[np.ndarray]):
+            term_mats: Sequence[np.ndarray], pairs: Optional[Sequence[Sequence[int]]] = None):
     """Flat host arrays of lrh_problem_desc.  term_mats[t] has shape
-    (n_instances, 2^k, 2^k) or (2^k, 2^k)."""
+    (n_instances, 2^k, 2^k) or (2^k, 2^k); ``pairs`` optionally lists explicit (parent, child)
+    region pairs (default: the covering relation, derived by the library)."""
     region_ptr = np.zeros(len(regions) + 1, np.int64)
     region_ptr[1:] = np.cumsum([len(r) for r in regions])
     region_sites = np.ascontiguousarray([s for r in regions for s in r], np.int32)
@@ -46,14 +47,18 @@ def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence
         if m.shape[0] != n_inst:
             raise ValueError("all term matrices need the same number of instances")
         flat[:, o:o + m.shape[1] * m.shape[2]] = m.reshape(n_inst, -1)
+    pp = np.ascontiguousarray([q[0] for q in pairs] if pairs else [0], np.int32)
+    pc = np.ascontiguousarray([q[1] for q in pairs] if pairs else [0], np.int32)
     keep = dict(region_ptr=region_ptr, region_sites=region_sites, term_ptr=term_ptr, term_sites=tsites,
-                term_mat_off=off, term_mats=np.ascontiguousarray(flat).view(np.float64))
+                term_mat_off=off, term_mats=np.ascontiguousarray(flat).view(np.float64),
+                pair_parent=pp, pair_child=pc)
     desc = L.ProblemDesc(n_sites=int(n_sites), n_regions=len(regions),
                          region_ptr=_ptr(region_ptr, C.c_int64), region_sites=_ptr(region_sites, C.c_int32),
                          n_terms=len(mats), term_ptr=_ptr(term_ptr, C.c_int64),
                          term_sites=_ptr(tsites, C.c_int32), term_mat_off=_ptr(off, C.c_int64),
                          term_mat_total=total, term_mats=_ptr(keep["term_mats"], C.c_double),
-                         n_instances=int(n_inst))
+                         n_instances=int(n_inst), n_pairs=len(pairs) if pairs else 0,
+                         pair_parent=_ptr(pp, C.c_int32), pair_child=_ptr(pc, C.c_int32))
     return desc, keep
 
 
@@ -84,21 +89,31 @@ class Solver:
     """One (batched) relaxation problem on the GPU.
 
     ``problem`` is any object with ``n_sites``, ``regions``, ``term_sites`` and
-    ``term_mats`` (see include/lrh.h for the conventions).  ``loop`` selects the iteration
-    driver of ``step``: "eager" (kernel launches), "graph" (captured CUDA graph), "persistent"
-    (one cooperative launch per call, classes of <= 4 sites) or "auto" (the autotuner's choice);
-    ``use_graph`` True / False is shorthand for "graph" / "eager".
+    ``term_mats`` (and optionally ``pairs``; see include/lrh.h for the conventions).  ``loop``
+    selects the iteration driver of ``step``: "eager" (kernel launches), "graph" (captured CUDA
+    graph), "persistent" (one cooperative launch per call, classes of <= 4 sites) or "auto" (the
+    autotuner's choice); ``use_graph`` True / False is shorthand for "graph" / "eager".
+    ``betas``, ``iters_per_stage``, ``certify_every`` and ``deadline_s`` describe the schedule
+    that ``solve`` runs inside the library.
     """
 
     def __init__(self, problem, variant: str = "nesterov", beta: float = 1.0, lhat: Optional[float] = None,
                  alpha: float = 1.0, step_rule: str = "inv_sqrt", degen_tol: float = 1e-5,
-                 max_sweeps: int = 15, use_graph: Optional[bool] = None, loop: str = "auto", stream=None):
+                 max_sweeps: int = 15, use_graph: Optional[bool] = None, loop: str = "auto", stream=None,
+                 cert_sweeps: int = 0, betas: Optional[Sequence[float]] = None, iters_per_stage: int = 0,
+                 certify_every: int = 0, deadline_s: float = 0.0, tune_cache: Optional[str] = None):
         self._lib = L.load()
         self._h = C.c_void_p(0)
-        desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats)
+        desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats,
+                                   getattr(problem, "pairs", None))
         self._opt = L.Options(variant=_VARIANTS[variant], step_rule=_RULES[step_rule], alpha=float(alpha),
                               beta=float(beta), lhat=float(lhat) if lhat else 0.0, degen_tol=float(degen_tol),
-                              max_sweeps=int(max_sweeps), loop=_loop_code(loop, use_graph))
+                              max_sweeps=int(max_sweeps), loop=_loop_code(loop, use_graph),
+                              cert_sweeps=int(cert_sweeps), iters_per_stage=int(iters_per_stage),
+                              certify_every=int(certify_every), deadline_s=float(deadline_s))
+        self._set_betas(betas)
+        self._tune = tune_cache.encode() if tune_cache else None
+        self._opt.tune_cache = self._tune
         st = _current_stream() if stream is None else C.c_void_p(int(stream))
         L.check(self._lib.lrh_create(C.byref(desc), C.byref(self._opt), st, C.byref(self._h)), "lrh_create")
         inf = self.info()
@@ -138,7 +153,9 @@ class Solver:
                     class_sites=list(inf.class_sites[:nc]), class_regions=list(inf.class_regions[:nc]),
                     sweeps=[int(x) for x in inf.sweeps[:nc]], class_block=list(inf.class_block[:nc]),
                     concurrent_classes=int(inf.concurrent_classes), loop=_LOOP_NAMES[inf.loop],
-                    persistent_grid=inf.persistent_grid, persistent_tiles=inf.persistent_tiles)
+                    persistent_grid=inf.persistent_grid, persistent_tiles=inf.persistent_tiles,
+                    sweep_capped=[int(x) for x in inf.sweep_capped[:nc]], n_sites=inf.n_sites,
+                    kappa_G=inf.kappa_G)
 
     def pairs(self):
         par = np.zeros(self.n_pairs, np.int32)
@@ -148,8 +165,17 @@ class Solver:
         return par, chi, off
 
     # ------------------------------------------------------------ control
+    def _set_betas(self, betas) -> None:
+        self._betas = np.ascontiguousarray(betas if betas is not None else [1.0], np.float64)
+        self._opt.n_beta = len(betas) if betas is not None else 0
+        self._opt.beta_sched = _ptr(self._betas, C.c_double)
+
     def set_options(self, **kw) -> None:
         o = self._opt
+        if "betas" in kw: self._set_betas(kw.pop("betas"))
+        for k in ("cert_sweeps", "iters_per_stage", "certify_every"):
+            if k in kw: setattr(o, k, int(kw.pop(k)))
+        if "deadline_s" in kw: o.deadline_s = float(kw.pop("deadline_s"))
         if "variant" in kw: o.variant = _VARIANTS[kw.pop("variant")]
         if "step_rule" in kw: o.step_rule = _RULES[kw.pop("step_rule")]
         if "lhat" in kw:
@@ -203,44 +229,59 @@ class Solver:
         L.check(self._lib.lrh_synchronize(self._h), "lrh_synchronize")
 
     def kappa(self) -> int:
-        """kappa_G = max over sites i of the number of pairs e->f with i in f (Thm 6); at
-        level 1 this is Delta_G, the maximum node degree (Thm 4)."""
-        par, chi, _ = self.pairs()
-        regions = self._keep["region_sites"], self._keep["region_ptr"]
-        sites, ptr = regions
-        count = {}
-        for f in chi:
-            for sidx in sites[ptr[f]:ptr[f + 1]]:
-                count[int(sidx)] = count.get(int(sidx), 0) + 1
-        return max(count.values()) if count else 0
+        """kappa_G of Thm 6 (Delta_G at level 1), as computed by the library."""
+        return int(self.info()["kappa_G"])
 
-    def theorem_parameters(self, eps: float, n_sites: int, R: Optional[float] = None, c_frac: float = 0.5) -> dict:
-        """Parameter rules of the convergence theorems for a target error density eps:
-        Alg. 2 (Thm 5, Thm 7): beta = 2 Gamma_G / (n eps), L_hat = beta Lambda_G / 2 and, given
-        R = dist(nu0, argmax Q_beta), T >= 2 R sqrt(Gamma_G Lambda_G) / (n eps) - 1;
-        Alg. 1 (Thm 4, Thm 6): alpha = c eps with c = c_frac / kappa_G < 1 / kappa_G and, given R,
-        T >= R^2 / (2 c (1 - c kappa_G) n eps^2)."""
-        beta = 2.0 * self.gamma_G / (n_sites * eps)
-        kap = self.kappa()
-        c = c_frac / kap
-        out = dict(beta=beta, lhat=beta * self.lambda_G / 2.0, alpha=c * eps, kappa_G=kap)
-        if R is not None:
-            out["T_nesterov"] = int(np.ceil(2.0 * R * np.sqrt(self.gamma_G * self.lambda_G) / (n_sites * eps) - 1))
-            out["T_subgradient"] = int(np.ceil(R ** 2 / (2.0 * c * (1.0 - c * kap) * n_sites * eps ** 2)))
+    def theorem_parameters(self, eps: float, R: Optional[float] = None, c_frac: float = 0.5) -> dict:
+        """Parameter rules of the convergence theorems (lrh_theorem_parameters): beta, L_hat,
+        alpha = c eps and, given R, the iteration counts of Thm 4-7 (-1 without R)."""
+        prm = L.Params()
+        L.check(self._lib.lrh_theorem_parameters(self._h, float(eps), float(R) if R else 0.0, float(c_frac),
+                                                 C.byref(prm)), "lrh_theorem_parameters")
+        out = dict(beta=prm.beta, lhat=prm.lhat, alpha=prm.alpha, c=prm.c, kappa_G=prm.kappa_G,
+                   lambda_G=prm.lambda_G, gamma_G=prm.gamma_G)
+        if R:
+            out["T_nesterov"] = int(prm.T_nesterov)
+            out["T_subgradient"] = int(prm.T_subgradient)
         return out
 
-    def run_schedule(self, betas: Sequence[float], iters_per_stage: int) -> None:
-        """Alg. 2 under beta continuation: per beta, L_hat = beta Lambda_G / 2,
-        restart (theta = 1, zeta = nu), then iters_per_stage iterations."""
-        for b in betas:
-            self.set_options(beta=b, lhat=None)
-            self.restart()
-            self.step(iters_per_stage)
+    def reset(self) -> None:
+        """nu = zeta = nu_best = 0, theta = 1, t = 0, q_best = -inf (lrh_reset)."""
+        L.check(self._lib.lrh_reset(self._h), "lrh_reset")
+
+    def solve(self, max_records: int = 0) -> dict:
+        """Run the configured schedule inside the library (lrh_solve) from the current
+        multipliers.  Returns the final certified bound per instance and the records taken every
+        ``certify_every`` iterations (iteration, seconds, beta, bound per instance)."""
+        rec = (L.Record * max(max_records, 1))()
+        rb = np.zeros((max(max_records, 1), self.n_instances), np.float64)
+        n = C.c_int32(0)
+        out = np.zeros(self.n_instances, np.float64)
+        rc = self._lib.lrh_solve(self._h, int(max_records), C.cast(rec, C.c_void_p), rb.ctypes.data,
+                                 C.cast(C.pointer(n), C.c_void_p), out.ctypes.data)
+        if rc not in (0, L.ENOCONV, L.EDEADLINE):
+            L.check(rc, "lrh_solve")
+        return dict(bound=out, status=L.ERRORS.get(rc, "OK") if rc else "OK",
+                    records=[dict(iteration=int(rec[i].iteration), seconds=rec[i].seconds, beta=rec[i].beta,
+                                  bound=rb[i].copy()) for i in range(n.value)])
+
+    def run_schedule(self, betas: Sequence[float], iters_per_stage: int) -> np.ndarray:
+        """Alg. 2 under beta continuation inside the library: per beta, L_hat = beta Lambda_G / 2,
+        restart (theta = 1, zeta = nu), iters_per_stage iterations; returns the certified bound."""
+        self.set_options(betas=list(betas), iters_per_stage=iters_per_stage, certify_every=0, lhat=None)
+        return self.solve()["bound"]
 
     # ------------------------------------------------------------ data
     def bound(self, kind: str = "certified") -> np.ndarray:
+        """Per-instance bound (lrh_bound).  An FP64 certification that stopped at its sweep cap
+        (LRH_ENOCONV) still returns a valid, looser lower bound: a warning, not an error."""
         out = np.zeros(self.n_instances, np.float64)
-        L.check(self._lib.lrh_bound(self._h, _BOUNDS[kind], out.ctypes.data), "lrh_bound")
+        rc = self._lib.lrh_bound(self._h, _BOUNDS[kind], out.ctypes.data)
+        if rc == L.ENOCONV:
+            import warnings
+            warnings.warn("lrh_bound: certification eigensolve stopped at its sweep cap (bound still valid)")
+        elif rc:
+            L.check(rc, "lrh_bound")
         return out
 
     def region_values(self, kind: str = "last") -> np.ndarray:

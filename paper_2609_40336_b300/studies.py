@@ -97,7 +97,7 @@ def iterations_vs_eps(models: Sequence[str], n: int, eps_list: Sequence[float], 
             iters = []
             for eps in eps_list:
                 s = Solver(p, variant=variant)
-                prm = s.theorem_parameters(eps, n)
+                prm = s.theorem_parameters(eps)
                 if variant == "subgradient":
                     s.set_options(variant="subgradient", alpha=prm["alpha"], step_rule="const")
                 else:

@@ -1,7 +1,9 @@
 """GPU (CUDA library, through the C ABI) vs the FP64 oracle on the same seeded inputs.
 
-Tolerances: per-step objective 1e-5 relative; gradient per grad_tol (1e-5, or the
-beta-dependent FP32 perturbation bound of the Gibbs state); certified bound vs the
+Tolerances: per-region values 1e-5 relative to max(1, ||theta_e||_F); gradients element by
+element within max(1e-5, the FP32 perturbation bound of the state: (beta/2) for Gibbs states,
+sqrt(2)/gap for ground projectors, times the eigensolver's backward error; see
+tests/gpu_helpers.py); messages after a step element by element; certified bound vs the
 oracle's Q at the same multipliers 1e-12 per site; integer data (pairs) bit-exact.
 """
 import numpy as np
@@ -10,7 +12,8 @@ import pytest
 import lrh_gen as g
 from oracle import dual
 from oracle.poset import Poset
-from tests.gpu_helpers import grad_rel_err, grad_tol, random_traceless_messages, theta_norms
+from tests.gpu_helpers import (EPS32, check_grad, grad_entry_tol, ground_sensitivity, random_traceless_messages,
+                               region_norms)
 
 pytestmark = pytest.mark.gpu
 L = g.lattices
@@ -67,9 +70,11 @@ def test_smoothed_region_pass_parity(name, beta):
     ref = dual.region_pass(P, h, nu.astype(np.complex128), "smooth", beta=beta)
     q_gpu, q_or = vals.sum(axis=1), ref.value.sum(axis=1)
     assert np.all(np.abs(q_gpu - q_or) <= 1e-5 * np.maximum(1.0, np.abs(q_or)))
-    tn = theta_norms(P, h, nu)
-    assert np.max(np.abs(vals - ref.value)) <= 1e-5 * max(1.0, tn)
-    assert grad_rel_err(g_gpu, ref.grad, P.n_pairs) <= grad_tol(beta, tn)
+    norms = region_norms(P, h, nu)
+    assert np.all(np.abs(vals - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    err, worst = check_grad(g_gpu, ref.grad, grad_entry_tol(P, norms, beta / 2))
+    bare = err / (0.5 * beta * EPS32 * norms.max())
+    print(f"GRADERR {name} beta={beta:g} max_abs={err:.3e} of_tol={worst:.3f} per_beta_eps_theta={bare:.2f}")
     assert np.allclose(s.bound("last"), q_gpu, rtol=0, atol=1e-9)
 
 
@@ -83,9 +88,11 @@ def test_subgradient_region_pass_parity(name):
     s.evaluate()
     vals = s.region_values("last")
     ref = dual.region_pass(P, h, nu.astype(np.complex128), "ground", tol=1e-5)
-    tn = theta_norms(P, h, nu)
-    assert np.max(np.abs(vals - ref.value)) <= 1e-5 * max(1.0, tn)
-    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= 1e-4
+    norms = region_norms(P, h, nu)
+    assert np.all(np.abs(vals - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    err, worst = check_grad(s.messages("grad"), ref.grad,
+                            grad_entry_tol(P, norms, ground_sensitivity(P, h, nu, 1e-5)))
+    print(f"GRADERR {name} ground max_abs={err:.3e} of_tol={worst:.3f}")
 
 
 def test_degenerate_ground_space_at_zero_messages():
@@ -95,7 +102,7 @@ def test_degenerate_ground_space_at_zero_messages():
     s = Solver(p, variant="subgradient")
     s.evaluate()
     ref = dual.region_pass(P, h, dual.zeros_messages(P, 1), "ground", tol=1e-5)
-    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= 1e-5
+    check_grad(s.messages("grad"), ref.grad, np.full(ref.grad.shape, 1e-5))
     assert abs(s.bound("last")[0] - (-sum(p.meta["J"]) - sum(p.meta["h"]))) < 1e-5
 
 
@@ -113,9 +120,14 @@ def test_nesterov_steps_match_oracle_from_same_state(name):
     lhat = beta * P.lipschitz_lambda() / 2
     dual.nesterov_step(P, h, st, beta, lhat)
     dual.nesterov_step(P, h, st, beta, lhat)
+    # element by element: the step moves each entry by g / (theta L_hat), so its error is the
+    # gradient's (tolerance of check_grad) over theta L_hat, plus FP32 rounding of the entry
+    norms = region_norms(P, h, nu)
+    gtol = grad_entry_tol(P, norms, beta / 2)
     for which, ref in (("nu", st.nu), ("zeta", st.zeta)):
         got = s.messages(which).astype(np.complex128)
-        assert np.linalg.norm(got - ref) <= 1e-5 * max(1.0, np.linalg.norm(ref)), which
+        err = np.abs(got - ref)
+        assert np.all(err <= 4 * gtol / (dual.next_theta(1.0) * lhat) + 1e-6 * np.maximum(1.0, np.abs(ref))), which
 
 
 def test_subgradient_steps_match_oracle_and_track_best():
@@ -128,10 +140,11 @@ def test_subgradient_steps_match_oracle_and_track_best():
         s.step(1)
         dual.subgradient_step(P, h, st, "sqrt", 0.5, tol=1e-5)
     got = s.messages("nu").astype(np.complex128)
-    assert np.linalg.norm(got - st.nu) <= 1e-5 * max(1.0, np.linalg.norm(st.nu))
+    # element by element: three steps of size <= 0.5, gradient entries within 1e-4 (ground states)
+    assert np.all(np.abs(got - st.nu) <= 3 * 0.5 * 1e-4 + 1e-6 * np.maximum(1.0, np.abs(st.nu)))
     assert abs(s.bound("best")[0] - st.q_best[0]) <= 1e-5 * abs(st.q_best[0])
     best = s.messages("nu_best").astype(np.complex128)
-    assert np.linalg.norm(best - st.nu_best) <= 1e-5 * max(1.0, np.linalg.norm(st.nu_best))
+    assert np.all(np.abs(best - st.nu_best) <= 3 * 0.5 * 1e-4 + 1e-6 * np.maximum(1.0, np.abs(st.nu_best)))
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -225,16 +238,17 @@ def test_autotune_chooses_valid_shapes_and_uses_cache(tmp_path):
     g0, v0 = s.messages("grad"), s.region_values("last")
     cache = tmp_path / "tune.jsonl"
     shapes = s.autotune(str(cache), force=True)
-    assert all(b in (64, 128, 256) or (k == 2 and b in (-64, -128, -256))
+    assert all(b in (64, 128, 256) or (k == 2 and b in (-64, -128, -256)) or (k in (3, 4) and b - 4096 in (64, 128, 256))
                for k, b in zip(shapes["class_sites"], shapes["class_block"]))
     lines = cache.read_text().splitlines()
     assert len(lines) >= 1 and all(l.startswith("{") for l in lines)
     s.evaluate()
     g1, v1 = s.messages("grad"), s.region_values("last")
-    if all(b > 0 for b in shapes["class_block"]):
+    if all(0 < b < 4096 for b in shapes["class_block"]):   # lane layouts only: bit-identical
         assert np.array_equal(g1, g0) and np.array_equal(v1, v0)
     else:
-        assert np.max(np.abs(v1 - v0)) <= 1e-5 and grad_rel_err(g1, g0.astype(np.complex128), P.n_pairs) <= 1e-5
+        assert np.max(np.abs(v1 - v0)) <= 1e-5
+        check_grad(g1, g0.astype(np.complex128), np.full(g0.shape, 1e-5))
     s2 = Solver(p, beta=4.0)
     shapes2 = s2.autotune(str(cache))
     assert shapes2 == shapes and cache.read_text().splitlines() == lines
@@ -250,9 +264,9 @@ def test_launch_shapes_of_the_4x4_class_match_the_oracle(block):
     s.restart()
     s.evaluate()
     ref = dual.region_pass(P, h, nu.astype(np.complex128), "smooth", beta=4.0)
-    tn = theta_norms(P, h, nu)
-    assert np.max(np.abs(s.region_values("last") - ref.value)) <= 1e-5 * max(1.0, tn)
-    assert grad_rel_err(s.messages("grad"), ref.grad, P.n_pairs) <= grad_tol(4.0, tn)
+    norms = region_norms(P, h, nu)
+    assert np.all(np.abs(s.region_values("last") - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    check_grad(s.messages("grad"), ref.grad, grad_entry_tol(P, norms, 2.0))
     s.step(12)
     ref_s = Solver(p, variant="nesterov", beta=4.0)
     ref_s.set_messages("nu", nu)
@@ -262,7 +276,7 @@ def test_launch_shapes_of_the_4x4_class_match_the_oracle(block):
     if block > 0:
         assert np.array_equal(a, b)
     else:
-        assert np.linalg.norm(a - b) <= 1e-5 * max(1.0, np.linalg.norm(b))
+        assert np.all(np.abs(a - b) <= 1e-5 * np.maximum(1.0, np.abs(b)))
 
 
 @pytest.mark.parametrize("name", ["heis8x8_level1", "xxz_tri4_plaq", "chain_L6_D64", "chain_L7_D128"])

@@ -500,3 +500,29 @@ def test_near_degenerate_level_outside_the_tolerance_is_excluded():
     P = Poset(p.regions)
     res = dual.region_pass(P, dual.local_terms(p, P), dual.zeros_messages(P, 1), "ground", tol=1e-9)
     assert np.abs(res.states[2][0, 0] - np.diag([1.0, 0, 0, 0])).max() < 1e-12
+
+
+# ---------------------------------------------------------------- sampled pass = full pass
+@pytest.mark.parametrize("builder,mode", [(lambda: L.xxz_triangular(4, 3), "smooth"),
+                                          (lambda: L.random_chain(7, 3, L=4), "smooth"),
+                                          (lambda: L.random_chain(6, 4, L=3), "ground")])
+def test_sampled_pass_equals_full_pass(builder, mode):
+    """The per-sample evaluation used at benchmark sizes is the full region pass restricted to
+    the sampled pairs (same values, gradients and theta norms)."""
+    p = builder()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    rng = np.random.default_rng(9)
+    nu = rand_herm_msgs(P, p.n_instances, rng, 0.8)
+    full = dual.region_pass(P, h, nu, mode, beta=3.0, tol=1e-9)
+    th = dual.assemble(P, h, nu)
+    qs = rng.integers(0, P.n_pairs, 12)
+    ins = rng.integers(0, p.n_instances, 12)
+    grads, vals, norms = dual.sampled_pass(p, P, nu, qs, ins, mode, beta=3.0, tol=1e-9)
+    for q, i, gq in zip(qs, ins, grads):
+        Df = int(P.D[P.pair_child[q]])
+        assert np.abs(full.grad[i, P.msg_off[q]:P.msg_off[q] + Df * Df].reshape(Df, Df) - gq).max() < 1e-12
+    for (i, e), v in vals.items():
+        assert abs(full.value[i, e] - v) < 1e-12
+        kk = int(P.k[e])
+        assert abs(np.linalg.norm(th[kk][i, P.local_index[e]]) - norms[(i, e)]) < 1e-12
