@@ -90,6 +90,9 @@ extern "C" {
                                    selects the Hermitian 2x2-block layout (theta's upper triangle in
                                    shared memory, each stored entry rotated once per round) with that
                                    many threads per CTA; D lanes per region as in the lane-row layout */
+#define LRH_SHAPE_WARP16  8192  /* lrh_set_launch_shape, 4-site classes: LRH_SHAPE_WARP16 + 64 / 128 / 256
+                                   selects the 2x2-block layout with one warp per 16 x 16 region (each
+                                   lane one off-diagonal block and half a row of V) */
 #define LRH_SHAPE_CTA_FP32   1  /* lrh_set_launch_shape, classes of 6-7 sites: rho = W W^dagger on the FP32 cores */
 #define LRH_SHAPE_CTA_TENSOR 2  /* ... on the tensor cores (tcgen05, three TF32 products per term, FP32
                                    accumulate); 7-site (128 x 128) regions only */

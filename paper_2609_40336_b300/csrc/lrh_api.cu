@@ -323,16 +323,39 @@ int run_persistent(lrh_problem* p, int n) {
 // Classes of 3 and 4 sites whose launch shape selects the 2x2-block layout (bit k).
 int32_t blk_mask_of(const lrh_problem* p) {
     int32_t m = 0;
-    for (size_t c = 0; c < p->class_k.size(); ++c)
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
         if ((p->class_k[c] == 3 || p->class_k[c] == 4) && p->class_block[c] > LRH_SHAPE_BLOCKS) m |= 1 << p->class_k[c];
+        if (p->class_k[c] == 4 && p->class_block[c] > LRH_SHAPE_WARP16) m |= 1 << 5;
+    }
     return m;
 }
 
-// Plan of the persistent launch: classes in cost order (heaviest first), tiles of
-// persistent_tile_regions(k) regions, grid = min(tiles, resident CTAs).  Not available when a
-// class has more than 4 sites or the device lacks cooperative launches.
+// Tiles of the persistent / one-launch pass for the current launch shapes: classes in cost order
+// (heaviest first), persistent_tile_regions(k, layout) regions per tile, grid = min(tiles,
+// resident CTAs).  Called at creation and whenever a launch shape changes.
+void layout_plan(lrh_problem* p) {
+    if (p->persist_cap <= 0) return;
+    PersistPlan& L = p->plan;
+    L.blk_mask = blk_mask_of(p);
+    int64_t tiles = 0;
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
+        const int64_t per = persistent_tile_regions(p->class_k[c], L.blk_mask);
+        L.cls[c] = p->class_list[c];
+        L.count[c] = p->class_count[c];
+        L.k[c] = p->class_k[c];
+        L.tile0[c] = tiles;
+        tiles += ((int64_t)p->n_inst * p->class_count[c] + per - 1) / per;
+    }
+    L.tiles = tiles;
+    L.n_classes = (int32_t)p->class_k.size();
+    p->persist_grid = (int)std::min<int64_t>(tiles, p->persist_cap);
+}
+
+// The persistent launch's barrier word and resident-CTA capacity.  Not available when a class has
+// more than 4 sites or the device lacks cooperative launches.
 int plan_persistent(lrh_problem* p) {
     p->persist_grid = 0;
+    p->persist_cap = 0;
     const size_t nc = p->class_k.size();
     if (nc == 0 || nc > (size_t)kPersistClasses) return LRH_OK;
     int kmax = 2;
@@ -344,25 +367,13 @@ int plan_persistent(lrh_problem* p) {
     LRH_CK(persistent_prepare(kmax, &nb));
     if (nb <= 0) return LRH_OK;
     PersistPlan L{};
-    int64_t tiles = 0;
-    for (size_t c = 0; c < nc; ++c) {
-        const int64_t per = persistent_tile_regions(p->class_k[c]);
-        L.cls[c] = p->class_list[c];
-        L.count[c] = p->class_count[c];
-        L.k[c] = p->class_k[c];
-        L.tile0[c] = tiles;
-        tiles += ((int64_t)p->n_inst * p->class_count[c] + per - 1) / per;
-    }
-    L.tiles = tiles;
-    L.n_classes = (int32_t)nc;
     int rc;
     if ((rc = p->dalloc(&L.bar, 2))) return rc;
     LRH_CK(cudaMemset(L.bar, 0, 2 * sizeof(unsigned)));
-    L.blk_mask = blk_mask_of(p);
     p->plan = L;
     p->persist_kmax = kmax;
     p->persist_cap = (int64_t)nb * sms;
-    p->persist_grid = (int)std::min<int64_t>(tiles, p->persist_cap);
+    layout_plan(p);
     return LRH_OK;
 }
 
@@ -1277,10 +1288,11 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         if (!cache_lookup(cache, key, &blk)) {
             float best = 1e30f;
             for (int cand : {64, 128, 256, -64, -128, -256, LRH_SHAPE_BLOCKS + 64, LRH_SHAPE_BLOCKS + 128,
-                             LRH_SHAPE_BLOCKS + 256}) {
+                             LRH_SHAPE_BLOCKS + 256, LRH_SHAPE_WARP16 + 64, LRH_SHAPE_WARP16 + 128, LRH_SHAPE_WARP16 + 256}) {
                 if (cand > 0 && cand < LRH_SHAPE_BLOCKS && cand < (1 << k)) continue;
                 if (cand < 0 && k != 2) continue;   // thread-per-region layout: 4 x 4 regions
-                if (cand > LRH_SHAPE_BLOCKS && k != 3 && k != 4) continue;   // 2x2-block layout: 8 x 8, 16 x 16
+                if (cand > LRH_SHAPE_BLOCKS && cand < LRH_SHAPE_WARP16 && k != 3 && k != 4) continue;   // 8 x 8, 16 x 16
+                if (cand > LRH_SHAPE_WARP16 && k != 4) continue;   // one warp per 16 x 16 region
                 float ms = 0;
                 int rc = time_adaptive(p, 2.0f, [&]() -> int {
                     LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, cand));
@@ -1292,7 +1304,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
         }
         p->class_block[c] = blk;
     }
-    p->plan.blk_mask = blk_mask_of(p);
+    layout_plan(p);
     // Iteration driver: how the classes of a pass are launched (one after another, forked
     // streams, one launch) under the graph driver, and the persistent driver; each timed over
     // whole iterations on a saved copy of the multipliers and iteration scalars.
@@ -1386,6 +1398,9 @@ int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
     bool ok;
     if (k_sites >= 6) ok = block == LRH_SHAPE_CTA_FP32 || (block == LRH_SHAPE_CTA_TENSOR && k_sites == 7);
+    else if (block > LRH_SHAPE_WARP16)
+        ok = k_sites == 4 && (block - LRH_SHAPE_WARP16 == 64 || block - LRH_SHAPE_WARP16 == 128 ||
+                              block - LRH_SHAPE_WARP16 == 256);
     else if (block > LRH_SHAPE_BLOCKS)
         ok = (k_sites == 3 || k_sites == 4) && (block - LRH_SHAPE_BLOCKS == 64 || block - LRH_SHAPE_BLOCKS == 128 ||
                                                 block - LRH_SHAPE_BLOCKS == 256);
@@ -1399,7 +1414,7 @@ int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
                 const int bit = 1 << (k_sites - 6);
                 p->P.tc_backtransform = block == LRH_SHAPE_CTA_TENSOR ? (p->P.tc_backtransform | bit) : (p->P.tc_backtransform & ~bit);
             }
-            p->plan.blk_mask = blk_mask_of(p);
+            layout_plan(p);
             drop_graphs(p);
             return LRH_OK;
         }

@@ -14,7 +14,9 @@
 //      off-diagonal entry and the two new diagonal entries (exact: the block becomes diagonal);
 //   2. lanes update the D(D-2)/8 off-diagonal blocks, B' = J_k^H B J_l (two-sided, one pass);
 //   3. lane s applies the column rotation and the tournament permutation to row s of V
-//      (registers, compile-time indices, two register arrays used in turn).
+//      (registers, compile-time indices, two register arrays used in turn), one round late, so
+//      that step 1's dependent chain (computed by every lane, stored by lanes k < D/2) overlaps
+//      V's independent FMAs in one basic block.
 // The rotation parameters use the fast reciprocal / reciprocal square root (rot_fast).
 // Arithmetic per round: 12 FMA-type instructions per stored entry of theta and 6 per entry of V,
 // against 18 per row entry (both triangles of theta, plus V) in the lane-row layout.
@@ -31,6 +33,18 @@ namespace blk {
 
 using namespace dev;
 
+// Placement of the 16 x 16 layout in shared memory.  A buffer holds 72 units of 16 bytes (unit
+// u < 36: entries (0, 1) of block u; unit 36 + u: entries (2, 3)), spread over 144 unit slots
+// (the buffers share their space with the W / rho staging, which needs twice as much), and the
+// 28 off-diagonal blocks are dealt to the 32 (lane, j) positions of a region.  Both were chosen
+// by a search (paper_2609_40336_b300/blk16_layout.py) that minimises the shared-memory
+// wavefronts of a round: 64-bit stores are served per 16 lanes and 128-bit loads per 8, and two
+// lanes hitting the same bank at different addresses cost one more wavefront; the search cut the
+// modelled wavefronts of a round's block loads and stores from 43 to 31.
+static __constant__ unsigned char kPhys16[72] = {30, 39, 76, 102, 131, 141, 42, 7, 95, 80, 33, 132, 49, 29, 26, 108, 90, 109, 59, 93, 47, 9, 113, 97, 46, 107, 64, 110, 32, 15, 35, 0, 22, 122, 140, 37, 78, 127, 56, 135, 14, 98, 61, 50, 23, 1, 2, 100, 48, 53, 69, 18, 123, 3, 124, 74, 115, 8, 72, 4, 126, 118, 27, 63, 101, 103, 133, 62, 57, 17, 129, 12};
+// off-diagonal block (in (k, l) row order) of position j * 16 + lane; -1: repeats block 27
+static __constant__ signed char kAssign16[32] = {18, -1, 22, 23, 14, 21, 6, 27, 4, 5, 10, 17, 9, 3, 7, 2, 8, 26, 15, 0, 25, 1, 11, 13, -1, 16, 24, 12, -1, -1, 19, 20};
+
 template <int D>
 struct Blk {
     static constexpr int n = D / 2;                  // pairs per round
@@ -38,11 +52,13 @@ struct Blk {
     static constexpr int NOFF = n * (n - 1) / 2;     // off-diagonal blocks
     static constexpr int PER = (NOFF + D - 1) / D;   // off-diagonal blocks per lane
     static constexpr int LD = D + 2;                 // padded row stride of the W / rho staging
-    // one buffer = two halves of NB float4: entries (0, 1) of every block, then entries (2, 3)
-    static constexpr size_t buf_bytes = (size_t)2 * NB * 16;
+    static constexpr int SLOTS = D == 16 ? 144 : 2 * NB;   // 16-byte unit slots per buffer
+    // one buffer: unit u < NB = entries (0, 1) of block u, unit NB + u = entries (2, 3), placed
+    // at slot phys_unit<D>(u)
+    static constexpr size_t buf_bytes = (size_t)SLOTS * 16;
     static constexpr size_t stage_bytes = (size_t)2 * D * LD * sizeof(float2);
     static constexpr size_t union_bytes = 2 * buf_bytes > stage_bytes ? 2 * buf_bytes : stage_bytes;
-    static constexpr size_t per_group = union_bytes + n * sizeof(RotC<float>) + D * sizeof(float);
+    static constexpr size_t per_group = union_bytes + 2 * n * sizeof(RotC<float>) + D * sizeof(float);
 };
 
 template <int D, int BLOCK>
@@ -58,11 +74,34 @@ __host__ __device__ constexpr int rr_dst(int o, int D) {
 template <int D>
 __device__ __forceinline__ int bidx(int k, int l) { return k * (D / 2) - ((k * (k - 1)) >> 1) + (l - k); }
 
+// slot of unit u
+template <int D>
+__device__ __forceinline__ int phys_unit(int u) {
+    if constexpr (D == 16) return kPhys16[u];
+    else return u;
+}
+
 // float2 index (within one buffer) of entry (i, j), i <= j
 template <int D>
 __device__ __forceinline__ int eidx(int i, int j) {
     const int e = ((i & 1) << 1) | (j & 1);
-    return (e >> 1) * (2 * Blk<D>::NB) + bidx<D>(i >> 1, j >> 1) * 2 + (e & 1);
+    return phys_unit<D>((e >> 1) * Blk<D>::NB + bidx<D>(i >> 1, j >> 1)) * 2 + (e & 1);
+}
+
+// off-diagonal block of position (j, lane) (in (k, l) row order) and whether the position owns it
+// (positions without a block of their own repeat one: the same values to the same places)
+template <int D>
+__device__ __forceinline__ int assigned_block(int j, int lane, bool& own) {
+    constexpr int NOFF = Blk<D>::NOFF;
+    if constexpr (D == 16) {
+        const int m = kAssign16[j * 16 + lane];
+        own = m >= 0;
+        return m >= 0 ? m : NOFF - 1;
+    } else {
+        const int m = lane + D * j;
+        own = m < NOFF;
+        return own ? m : NOFF - 1;
+    }
 }
 
 // destination of entry (i, j), i <= j, after a round: its float2 index, negative (~index) when the
@@ -110,16 +149,16 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
                                                      const int32_t* __restrict__ cls, const int32_t count, const int k,
                                                      const int64_t tile) {
     using B = Blk<D>;
-    constexpr int n = B::n, NB = B::NB, NOFF = B::NOFF, PER = B::PER, LD = B::LD;
+    constexpr int n = B::n, NB = B::NB, PER = B::PER, LD = B::LD;
     constexpr int G = BLOCK / D;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int g = threadIdx.x / D;
     const int s = threadIdx.x % D;
     unsigned char* base = smem_raw + g * B::per_group;
     float2* bufA = reinterpret_cast<float2*>(base);
-    float2* bufB = bufA + 2 * NB * 2;
-    RotC<float>* prm = reinterpret_cast<RotC<float>*>(base + B::union_bytes);
-    float* pw = reinterpret_cast<float*>(prm + n);
+    float2* bufB = bufA + 2 * B::SLOTS;
+    RotC<float>* prm2 = reinterpret_cast<RotC<float>*>(base + B::union_bytes);   // [2][n] by round parity
+    float* pw = reinterpret_cast<float*>(prm2 + 2 * n);
     __shared__ unsigned long long blk_sweeps, blk_capped;
     if (threadIdx.x == 0) { blk_sweeps = 0ull; blk_capped = 0ull; }
 
@@ -149,19 +188,23 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     }
 
     // ---- blocks and destinations of every lane position (the same in every round and for every
-    //      region of the CTA): off-diagonal block j * D + s of lane s: byte offsets of the block
-    //      (first half) and of the rotations of its row and column pairs, the float2 indices of
-    //      its four entries' next positions, and +-1 for the entries stored conjugated
+    //      region of the CTA): for position (j, lane), byte offsets of its block's two halves and
+    //      of the rotations of the block's row and column pairs, the float2 indices of its four
+    //      entries' next positions, +-1 for the entries stored conjugated, and whether the
+    //      position owns the block
     __shared__ int4 tab_off[PER * D];
     __shared__ int4 tab_dst[PER * D];
     __shared__ float4 tab_sgn[PER * D];
+    __shared__ int tab_own[PER * D];
     if (threadIdx.x < PER * D) {
         const int j = threadIdx.x / D, ls = threadIdx.x % D;
-        int m = ls + D * j, kq = 0;
-        if (m >= NOFF) m = NOFF - 1;   // idle lane: a valid block, never stored
+        bool own;
+        int m = assigned_block<D>(j, ls, own), kq = 0;
         while (m >= n - 1 - kq) { m -= n - 1 - kq; ++kq; }
         const int lq = kq + 1 + m;
-        tab_off[threadIdx.x] = make_int4(16 * bidx<D>(kq, lq), 16 * kq, 16 * lq, 0);
+        const int bb = bidx<D>(kq, lq);
+        tab_off[threadIdx.x] = make_int4(16 * phys_unit<D>(bb), 16 * phys_unit<D>(NB + bb), 16 * kq, 16 * lq);
+        tab_own[threadIdx.x] = own ? 1 : 0;
         int d[4];
         float sg[4];
         for (int e = 0; e < 4; ++e) {
@@ -173,15 +216,21 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         tab_sgn[threadIdx.x] = make_float4(sg[0], sg[1], sg[2], sg[3]);
     }
     __syncthreads();
-    const int sd = s < n ? bidx<D>(s, s) : 0;
-    // next positions of the diagonal block's entries (never conjugated: 0 and 3 stay on the
+    // this lane's diagonal block: pair s mod (D/2) (lanes s >= D/2 compute a copy and store
+    // nothing), and the next positions of its entries (never conjugated: 0 and 3 stay on the
     // diagonal, and entry 1 is written as zero)
-    const int d0 = dest<D>(2 * s, 2 * s), d3 = dest<D>(2 * s + 1, 2 * s + 1);
-    const int d1x = dest<D>(2 * s, 2 * s + 1), d1 = d1x < 0 ? ~d1x : d1x;
+    const int pp = s & (n - 1);
+    const int sd0 = phys_unit<D>(bidx<D>(pp, pp)), sd1 = phys_unit<D>(NB + bidx<D>(pp, pp));
+    const int d0 = dest<D>(2 * pp, 2 * pp), d3 = dest<D>(2 * pp + 1, 2 * pp + 1);
+    const int d1x = dest<D>(2 * pp, 2 * pp + 1), d1 = d1x < 0 ? ~d1x : d1x;
 
+    // V takes each round's rotations one round late (so that their dependent chain overlaps V's
+    // independent FMAs); it starts as the identity with its columns in inverse tournament order,
+    // so that the first, rotation-free step (y[c] = x[rr_src(c)]) restores the identity
     float vr[D], vi[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { vr[c] = (c == s) ? 1.f : 0.f; vi[c] = 0.f; }
+    for (int c = 0; c < D; ++c) { vr[c] = (c == rr_src(s, D)) ? 1.f : 0.f; vi[c] = 0.f; }
+    if (s < 2 * n) prm2[s] = RotC<float>{1.f, 0.f, 0.f, 0.f};
     __syncwarp();
 
     // squared Frobenius norms: off-diagonal part (both triangles) and whole matrix
@@ -190,13 +239,13 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         float o = 0.f, dg = 0.f;
 #pragma unroll 1
         for (int j = 0; j < PER; ++j)
-            if (s + D * j < NOFF) {
-                const int b = tab_off[j * D + s].x >> 4;
-                const float4 h0 = c4[b], h1 = c4[NB + b];
+            if (tab_own[j * D + s]) {
+                const int4 of = tab_off[j * D + s];
+                const float4 h0 = c4[of.x >> 4], h1 = c4[of.y >> 4];
                 o += h0.x * h0.x + h0.y * h0.y + h0.z * h0.z + h0.w * h0.w + h1.x * h1.x + h1.y * h1.y + h1.z * h1.z + h1.w * h1.w;
             }
         if (s < n) {
-            const float4 h0 = c4[sd], h1 = c4[NB + sd];
+            const float4 h0 = c4[sd0], h1 = c4[sd1];
             o += h0.z * h0.z + h0.w * h0.w;
             dg = h0.x * h0.x + h1.z * h1.z;
         }
@@ -204,33 +253,51 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         all = off + group_sum<D>(dg);
     };
 
-    // one round: rotations from the diagonal blocks of `cur`, all blocks rotated into `nxt` at
-    // their next positions, row s of V (x) rotated and written permuted into y
-    auto round = [&](const float2* cur, float2* nxt, float (&xr)[D], float (&xi)[D], float (&yr)[D], float (&yi)[D]) {
+    // V step: the rotations `pr` on row s of V (x), then the tournament permutation into y
+    auto vstep = [&](const RotC<float>* pr, float (&xr)[D], float (&xi)[D], float (&yr)[D], float (&yi)[D]) {
+#pragma unroll
+        for (int q = 0; q < n; ++q) {
+            const RotC<float> Q = pr[q];
+            mix_cols(xr[2 * q], xi[2 * q], xr[2 * q + 1], xi[2 * q + 1], Q.c, Q.wr, Q.wi);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { yr[c] = xr[rr_src(c, D)]; yi[c] = xi[rr_src(c, D)]; }
+    };
+
+    // one round with parity par: rotations from the diagonal blocks of `cur` into prm2[par], the
+    // delayed V step with prm2[par ^ 1] (x into y), then every off-diagonal block into `nxt` at
+    // its next position
+    auto round = [&](const float2* cur, float2* nxt, int par, float (&xr)[D], float (&xi)[D], float (&yr)[D],
+                     float (&yi)[D]) {
         const float4* c4 = reinterpret_cast<const float4*>(cur);
         const unsigned char* cb = reinterpret_cast<const unsigned char*>(cur);
-        const unsigned char* pb = reinterpret_cast<const unsigned char*>(prm);
-        if (s < n) {
-            const float4 h0 = c4[sd], h1 = c4[NB + sd];
+        RotC<float>* pc = prm2 + n * par;
+        const unsigned char* pb = reinterpret_cast<const unsigned char*>(pc);
+        {
+            const float4 h0 = c4[sd0], h1 = c4[sd1];
             RotC<float> Rk;
             float2 dn;
             rot_fast(h0.x, h1.z, h0.z, h0.w, Rk, dn);
-            prm[s] = Rk;
-            nxt[d0] = make_float2(dn.x, 0.f);
-            nxt[d3] = make_float2(dn.y, 0.f);
-            nxt[d1] = make_float2(0.f, 0.f);
+            if (s < n) {
+                pc[s] = Rk;
+                nxt[d0] = make_float2(dn.x, 0.f);
+                nxt[d3] = make_float2(dn.y, 0.f);
+                nxt[d1] = make_float2(0.f, 0.f);
+            }
         }
+        vstep(prm2 + n * (par ^ 1), xr, xi, yr, yi);
         __syncwarp();
-#pragma unroll 1
+#pragma unroll
         for (int j = 0; j < PER; ++j) {
-            if (PER * D == NOFF || s + D * j < NOFF) {
+            {   // a lane without a j-th block repeats a valid block: the same values to the same
+                // places, and the round stays one basic block (loads of both blocks in flight)
                 const int4 of = tab_off[j * D + s];
                 const float4 h0 = *reinterpret_cast<const float4*>(cb + of.x);
-                const float4 h1 = *reinterpret_cast<const float4*>(cb + of.x + 16 * NB);   // c4[NB + block]
+                const float4 h1 = *reinterpret_cast<const float4*>(cb + of.y);
                 float2 b00 = make_float2(h0.x, h0.y), b01 = make_float2(h0.z, h0.w);
                 float2 b10 = make_float2(h1.x, h1.y), b11 = make_float2(h1.z, h1.w);
-                const RotC<float> K = *reinterpret_cast<const RotC<float>*>(pb + of.y);
-                const RotC<float> Lr = *reinterpret_cast<const RotC<float>*>(pb + of.z);
+                const RotC<float> K = *reinterpret_cast<const RotC<float>*>(pb + of.z);
+                const RotC<float> Lr = *reinterpret_cast<const RotC<float>*>(pb + of.w);
                 two_sided<float>(b00, b01, b10, b11, K, Lr);
                 const int4 dd = tab_dst[j * D + s];
                 const float4 sg = tab_sgn[j * D + s];
@@ -240,13 +307,6 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
                 nxt[dd.w] = make_float2(b11.x, sg.w * b11.y);
             }
         }
-#pragma unroll
-        for (int q = 0; q < n; ++q) {
-            const RotC<float> Q = prm[q];
-            mix_cols(xr[2 * q], xi[2 * q], xr[2 * q + 1], xi[2 * q + 1], Q.c, Q.wr, Q.wi);
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) { yr[c] = xr[rr_src(c, D)]; yi[c] = xi[rr_src(c, D)]; }
         __syncwarp();
     };
 
@@ -255,23 +315,28 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     float2* nxt = bufB;
     sums(cur, off2, norm2);
     const float thresh = 1e-12f * norm2;
-    int sweeps = 0;
+    int sweeps = 0, par = 0;
+    float ur[D], ui[D];
     for (;;) {
         if (sweeps > 0) sums(cur, off2, norm2);
         const bool done = (off2 <= thresh) || (sweeps >= max_sweeps);
         if (__all_sync(kFull, done)) break;
         ++sweeps;
-        float ur[D], ui[D];
 #pragma unroll 1
         for (int rd = 0; rd + 1 < D - 1; rd += 2) {
-            round(cur, nxt, vr, vi, ur, ui);
-            round(nxt, cur, ur, ui, vr, vi);
+            round(cur, nxt, par, vr, vi, ur, ui);
+            round(nxt, cur, par ^ 1, ur, ui, vr, vi);
         }
-        round(cur, nxt, vr, vi, ur, ui);   // D - 1 rounds per sweep is odd
+        round(cur, nxt, par, vr, vi, ur, ui);   // D - 1 rounds per sweep is odd
         { float2* t = cur; cur = nxt; nxt = t; }
+        par ^= 1;
 #pragma unroll
         for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
     }
+    // the last round's rotations (or, with no sweep, the initial permutation) complete V
+    vstep(prm2 + n * (par ^ 1), vr, vi, ur, ui);
+#pragma unroll
+    for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
     // the slots are back in natural order: lambda_s on the diagonal, row s of V in (vr, vi)
     const float lam = cur[eidx<D>(s, s)].x;
     const float lmin = group_min<D>(lam);
@@ -294,8 +359,7 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     float2* Wb = reinterpret_cast<float2*>(base);
     float2* Rb = Wb + D * LD;
     __syncwarp();
-    // W = V diag(sqrt(p)); rho = W W^dagger, row s per lane
-    float ur[D], ui[D];   // (the sweep loop's second V array is out of scope here)
+    // W = V diag(sqrt(p)); rho = W W^dagger, row s per lane (ur, ui reused)
 #pragma unroll
     for (int c = 0; c < D; ++c) { const float q = pw[c]; ur[c] = vr[c] * q; ui[c] = vi[c] * q; }
     {
@@ -354,6 +418,309 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     }
     __syncthreads();
     if (valid && s == 0) {
+        atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
+        if (off2 > thresh) atomicAdd(&blk_capped, 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_sweeps) atomicAdd(&P.sweeps[k], blk_sweeps);
+    if (threadIdx.x == 0 && blk_capped) atomicAdd(&P.capped[k], blk_capped);
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// One warp per 16 x 16 region (launch shape LRH_SHAPE_WARP16): the same block layout, rotations
+// and tournament as region_pass_blk_impl<16>, with the work spread over 32 lanes.
+//   * lane j < 28 owns off-diagonal block j for the whole eigensolve, so its source offset,
+//     destinations and signs stay in registers (lanes 28..31 repeat block 27: the same values
+//     to the same places, no divergence);
+//   * lane 2 r + h owns half h of row r of V (8 columns; the tournament moves one entry across
+//     the half-row boundary per round: one shuffle pair);
+//   * every lane computes the rotation of pair (lane mod 8) (lanes 0..7 store it), and V takes
+//     each round's rotations one round late, so the rotation's dependent chain overlaps V's
+//     independent FMAs in one basic block.  V starts as the identity with its columns in the
+//     inverse tournament order, so that the first (delayed) step, which only permutes, yields
+//     the identity; one more step after the last round applies the last rotations.
+// Rotations, block updates and V updates are those of region_pass_blk_impl<16> in the same
+// order; results agree with it to rounding (a few operations are ordered differently).
+struct W16 {
+    static constexpr int D = 16, n = 8, NB = 36, NOFF = 28, LD = D + 2;
+    static constexpr size_t union_bytes = Blk<16>::union_bytes;
+    static constexpr size_t per_group = union_bytes + 2 * n * sizeof(RotC<float>) + D * sizeof(float);
+};
+
+template <int BLOCK>
+struct W16Smem {
+    static constexpr size_t bytes = (BLOCK / 32) * W16::per_group + 16;
+};
+
+template <int BLOCK>
+__device__ __forceinline__ void region_pass_w16_impl(const DevProblem& P, const PassIO& io,
+                                                     const int32_t* __restrict__ cls, const int32_t count, const int k,
+                                                     const int64_t tile) {
+    constexpr int D = 16, n = 8, NB = 36, NOFF = 28, LD = W16::LD, H = D / 2;
+    constexpr int G = BLOCK / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int g = threadIdx.x >> 5;
+    const int L = threadIdx.x & 31;
+    const int s = L & (D - 1);            // row of theta / rho for lanes 0..15
+    unsigned char* base = smem_raw + g * W16::per_group;
+    float2* bufA = reinterpret_cast<float2*>(base);
+    float2* bufB = bufA + 2 * Blk<16>::SLOTS;
+    RotC<float>* prm2 = reinterpret_cast<RotC<float>*>(base + W16::union_bytes);   // [2][n] by round parity
+    float* pw = reinterpret_cast<float*>(prm2 + 2 * n);
+    __shared__ unsigned long long blk_sweeps, blk_capped;
+    if (threadIdx.x == 0) { blk_sweeps = 0ull; blk_capped = 0ull; }
+
+    const int64_t unit = tile * G + g;
+    const bool valid = unit < (int64_t)P.n_inst * count;
+    const int inst = valid ? (int)(unit / count) : 0;
+    const int r = valid ? cls[unit % count] : 0;
+    const bool nest = P.st->variant == 1;
+    const int max_sweeps = P.st->max_sweeps;
+    const Thetas T = pass_thetas(P, io);
+
+    // ---- assemble: lanes 0..15 build row s and store its upper part
+    const RegionInfo R = valid ? P.reg[r] : RegionInfo{-1, -1, 0, 0, 0, 0, 0};
+    if (L < D) {
+        float ar[D], ai[D];
+        if (valid) {
+            assemble_row_io<D>(P, R, inst, s, io, T, ar, ai);
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+            if (c >= s) bufA[eidx<D>(s, c)] = make_float2(ar[c], c == s ? 0.f : ai[c]);
+    }
+    if (L < 2 * n) prm2[L] = RotC<float>{1.f, 0.f, 0.f, 0.f};   // the "previous" rotations of round 0
+
+    // ---- this lane's off-diagonal block (the same in every round)
+    int boff, boff1, koff, loff, dd[4];
+    float sg[4];
+    {
+        int m = L < NOFF ? L : NOFF - 1, kq = 0;
+        while (m >= n - 1 - kq) { m -= n - 1 - kq; ++kq; }
+        const int lq = kq + 1 + m;
+        boff = 16 * phys_unit<D>(bidx<D>(kq, lq));
+        boff1 = 16 * phys_unit<D>(NB + bidx<D>(kq, lq));
+        koff = 16 * kq;
+        loff = 16 * lq;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int x = dest<D>(2 * kq + (e >> 1), 2 * lq + (e & 1));
+            dd[e] = x < 0 ? ~x : x;
+            sg[e] = x < 0 ? -1.f : 1.f;
+        }
+    }
+    // this lane's diagonal block (pair L mod 8) and the next positions of its entries
+    const int pp = L & (n - 1);
+    const int sd0 = phys_unit<D>(bidx<D>(pp, pp)), sd1 = phys_unit<D>(NB + bidx<D>(pp, pp));
+    const int d0 = dest<D>(2 * pp, 2 * pp), d3 = dest<D>(2 * pp + 1, 2 * pp + 1);
+    const int d1x = dest<D>(2 * pp, 2 * pp + 1), d1 = d1x < 0 ? ~d1x : d1x;
+    // V: lane L holds half hh of row vrow, columns 8 hh .. 8 hh + 7, starting as the identity with
+    // its columns in inverse tournament order (the first V step, y[c] = x[rr_src(c)], restores it)
+    const int vrow = L >> 1, hh = L & 1;
+    float vr[H], vi[H], ur[H], ui[H];
+#pragma unroll
+    for (int c = 0; c < H; ++c) { vr[c] = (H * hh + c == rr_src(vrow, D)) ? 1.f : 0.f; vi[c] = 0.f; }
+    __syncwarp();
+
+    auto sums = [&](const float2* cur, float& off, float& all) {
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(cur);
+        const float4* c4 = reinterpret_cast<const float4*>(cur);
+        float o = 0.f, dg = 0.f;
+        if (L < NOFF) {
+            const float4 h0 = *reinterpret_cast<const float4*>(cb + boff);
+            const float4 h1 = *reinterpret_cast<const float4*>(cb + boff1);
+            o = h0.x * h0.x + h0.y * h0.y + h0.z * h0.z + h0.w * h0.w + h1.x * h1.x + h1.y * h1.y + h1.z * h1.z + h1.w * h1.w;
+        }
+        if (L < n) {
+            const float4 h0 = c4[sd0], h1 = c4[sd1];
+            o += h0.z * h0.z + h0.w * h0.w;
+            dg = h0.x * h0.x + h1.z * h1.z;
+        }
+        off = 2.f * group_sum<32>(o);
+        all = off + group_sum<32>(dg);
+    };
+
+    // V step: the rotations `pr` on this lane's 4 column pairs, then the tournament permutation into
+    // (yr, yi); one complex entry crosses between the two halves of a row (half 0 sends column 6,
+    // half 1 sends column 9)
+    auto vstep = [&](const RotC<float>* pr, float (&xr)[H], float (&xi)[H], float (&yr)[H], float (&yi)[H]) {
+        const RotC<float>* ph = pr + 4 * hh;
+#pragma unroll
+        for (int q = 0; q < H / 2; ++q) {
+            const RotC<float> Q = ph[q];
+            mix_cols(xr[2 * q], xi[2 * q], xr[2 * q + 1], xi[2 * q + 1], Q.c, Q.wr, Q.wi);
+        }
+        const float sr = hh ? xr[1] : xr[6], si = hh ? xi[1] : xi[6];
+        const float rr = __shfl_xor_sync(kFull, sr, 1), ri = __shfl_xor_sync(kFull, si, 1);
+        // half 0: [x0, x3, x1, x5, x2, x7, x4, recv];  half 1: [recv, x3, x0, x5, x2, x7, x4, x6]
+        yr[0] = hh ? rr : xr[0];  yi[0] = hh ? ri : xi[0];
+        yr[1] = xr[3];            yi[1] = xi[3];
+        yr[2] = hh ? xr[0] : xr[1]; yi[2] = hh ? xi[0] : xi[1];
+        yr[3] = xr[5];            yi[3] = xi[5];
+        yr[4] = xr[2];            yi[4] = xi[2];
+        yr[5] = xr[7];            yi[5] = xi[7];
+        yr[6] = xr[4];            yi[6] = xi[4];
+        yr[7] = hh ? xr[6] : rr;  yi[7] = hh ? xi[6] : ri;
+    };
+
+    // one round with parity par: rotations from the diagonal blocks of `cur` into prm2[par], the
+    // delayed V step with prm2[par ^ 1], then every off-diagonal block into `nxt`
+    auto round = [&](const float2* cur, float2* nxt, int par, float (&xr)[H], float (&xi)[H], float (&yr)[H],
+                     float (&yi)[H]) {
+        const float4* c4 = reinterpret_cast<const float4*>(cur);
+        const unsigned char* cb = reinterpret_cast<const unsigned char*>(cur);
+        RotC<float>* pc = prm2 + n * par;
+        {
+            const float4 h0 = c4[sd0], h1 = c4[sd1];
+            RotC<float> Rk;
+            float2 dn;
+            rot_fast(h0.x, h1.z, h0.z, h0.w, Rk, dn);
+            if (L < n) {
+                pc[L] = Rk;
+                nxt[d0] = make_float2(dn.x, 0.f);
+                nxt[d3] = make_float2(dn.y, 0.f);
+                nxt[d1] = make_float2(0.f, 0.f);
+            }
+        }
+        vstep(prm2 + n * (par ^ 1), xr, xi, yr, yi);
+        __syncwarp();
+        {
+            const unsigned char* pb = reinterpret_cast<const unsigned char*>(pc);
+            const float4 h0 = *reinterpret_cast<const float4*>(cb + boff);
+            const float4 h1 = *reinterpret_cast<const float4*>(cb + boff1);
+            float2 b00 = make_float2(h0.x, h0.y), b01 = make_float2(h0.z, h0.w);
+            float2 b10 = make_float2(h1.x, h1.y), b11 = make_float2(h1.z, h1.w);
+            const RotC<float> K = *reinterpret_cast<const RotC<float>*>(pb + koff);
+            const RotC<float> Lr = *reinterpret_cast<const RotC<float>*>(pb + loff);
+            two_sided<float>(b00, b01, b10, b11, K, Lr);
+            nxt[dd[0]] = make_float2(b00.x, sg[0] * b00.y);
+            nxt[dd[1]] = make_float2(b01.x, sg[1] * b01.y);
+            nxt[dd[2]] = make_float2(b10.x, sg[2] * b10.y);
+            nxt[dd[3]] = make_float2(b11.x, sg[3] * b11.y);
+        }
+        __syncwarp();
+    };
+
+    float off2, norm2;
+    float2* cur = bufA;
+    float2* nxt = bufB;
+    sums(cur, off2, norm2);
+    const float thresh = 1e-12f * norm2;
+    int sweeps = 0, par = 0;
+    for (;;) {
+        if (sweeps > 0) sums(cur, off2, norm2);
+        const bool done = (off2 <= thresh) || (sweeps >= max_sweeps);
+        if (__all_sync(kFull, done)) break;
+        ++sweeps;
+#pragma unroll 1
+        for (int rd = 0; rd + 1 < D - 1; rd += 2) {
+            round(cur, nxt, par, vr, vi, ur, ui);
+            round(nxt, cur, par ^ 1, ur, ui, vr, vi);
+        }
+        round(cur, nxt, par, vr, vi, ur, ui);   // D - 1 rounds per sweep is odd
+        { float2* t = cur; cur = nxt; nxt = t; }
+        par ^= 1;
+#pragma unroll
+        for (int c = 0; c < H; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
+    }
+    // the last rounds' rotations (or, with no sweep, the initial permutation) complete V
+    vstep(prm2 + n * (par ^ 1), vr, vi, ur, ui);
+    // the slots are back in natural order: lambda_s on the diagonal, half hh of row vrow of V in (ur, ui)
+    const float lam = cur[eidx<D>(s, s)].x;
+    const float lmin = group_min<16>(lam);
+    float wgt, F;
+    if (nest) {
+        const float beta = (float)P.st->beta;
+        const float e = expf(-beta * (lam - lmin));
+        const float Z = group_sum<16>(e);
+        wgt = e / Z;
+        F = lmin - logf(Z) / beta;
+    } else {
+        const float tau = (float)P.st->degen_tol * fmaxf(1.0f, sqrtf(norm2));
+        const float in = (lam - lmin <= tau) ? 1.0f : 0.0f;
+        const float m = group_sum<16>(in);
+        wgt = in / m;
+        F = lmin;
+    }
+    __syncwarp();   // every lane has read its diagonal before the staging reuses the buffers
+    if (L < D) pw[s] = sqrtf(wgt);
+    float2* Wb = reinterpret_cast<float2*>(base);
+    float2* Rb = Wb + D * LD;
+    __syncwarp();
+    {   // W = V diag(sqrt(p)): this lane's half row
+        float4* wrow = reinterpret_cast<float4*>(Wb + vrow * LD + H * hh);
+#pragma unroll
+        for (int c = 0; c < H / 2; ++c) {
+            const float q0 = pw[H * hh + 2 * c], q1 = pw[H * hh + 2 * c + 1];
+            wrow[c] = make_float4(ur[2 * c] * q0, ui[2 * c] * q0, ur[2 * c + 1] * q1, ui[2 * c + 1] * q1);
+        }
+    }
+    __syncwarp();
+    if (L < D) {   // rho = W W^dagger, upper triangle of row s (lanes 0..15)
+        float wr_[D], wi_[D];
+        {
+            const float4* ws = reinterpret_cast<const float4*>(Wb + s * LD);
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c) {
+                const float4 x = ws[c];
+                wr_[2 * c] = x.x; wi_[2 * c] = x.y; wr_[2 * c + 1] = x.z; wi_[2 * c + 1] = x.w;
+            }
+        }
+        for (int j = s; j < D; ++j) {
+            const float4* wj = reinterpret_cast<const float4*>(Wb + j * LD);
+            float accr = 0.f, acci = 0.f;
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c) {
+                const float4 x = wj[c];
+                accr += wr_[2 * c] * x.x + wi_[2 * c] * x.y;
+                acci += wi_[2 * c] * x.x - wr_[2 * c] * x.y;
+                accr += wr_[2 * c + 1] * x.z + wi_[2 * c + 1] * x.w;
+                acci += wi_[2 * c + 1] * x.z - wr_[2 * c + 1] * x.w;
+            }
+            Rb[s * LD + j] = make_float2(accr, j == s ? 0.f : acci);
+            if (j > s) Rb[j * LD + s] = make_float2(accr, -acci);   // exactly Hermitian
+        }
+    }
+    __syncwarp();
+    if (valid && L < D) {
+        if (R.rho_off >= 0) {
+            float4* dst = reinterpret_cast<float4*>(io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off + (int64_t)s * D);
+            const float4* srcr = reinterpret_cast<const float4*>(Rb + s * LD);
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c) dst[c] = srcr[c];
+        }
+        float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask;
+            const int Mc = (D - 1) & ~M;
+            const int kf = pi.kf;
+            const int Df = 1 << kf;
+            const int nrest = D >> kf;
+            for (int idx = s; idx < Df * Df; idx += D) {
+                const int ra = pdep_bits(idx >> kf, M);
+                const int rb = pdep_bits(idx & (Df - 1), M);
+                float accr = 0.f, acci = 0.f;
+                for (int c = 0; c < nrest; ++c) {
+                    const int x = pdep_bits(c, Mc);
+                    const float2 v = Rb[(ra | x) * LD + (rb | x)];
+                    accr += v.x;
+                    acci += v.y;
+                }
+                trb[pi.off + idx] = make_float2(accr, acci);
+            }
+        }
+        if (s == 0) {
+            P.val[(int64_t)inst * P.n_regions + r] = (double)F;
+            if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+        }
+    }
+    __syncthreads();
+    if (valid && L == 0) {
         atomicAdd(&blk_sweeps, (unsigned long long)sweeps);
         if (off2 > thresh) atomicAdd(&blk_capped, 1ull);
     }

@@ -158,6 +158,10 @@ cudaError_t prepare_blk_kernels();   // lrh_block.cu (D = 8, 16, 2x2-block layou
 cudaError_t launch_region_pass_blk(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
                                    int32_t class_count, cudaStream_t s, int threads);
 constexpr int kShapeBlocks = 4096;   // LRH_SHAPE_BLOCKS
+constexpr int kShapeWarp16 = 8192;   // LRH_SHAPE_WARP16
+// D = 16 in the 2x2-block layout with one warp per region, `threads` per CTA (64, 128 or 256)
+cudaError_t launch_region_pass_w16(const DevProblem& P, const PassIO& io, const int32_t* class_regions,
+                                   int32_t class_count, cudaStream_t s, int threads);
 cudaError_t launch_region_pass_cta(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,
                                    int32_t class_count, cudaStream_t s);
 cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* class_regions, int32_t class_count,
@@ -202,11 +206,12 @@ struct PersistPlan {
     int32_t n;            // iterations
     int32_t nesterov;     // 1: fused Alg. 2 passes; 0: Alg. 1 iterations
     int32_t par0;         // Alg. 1: parity of the first iteration
-    int32_t blk_mask;     // bit k: class k (3 or 4 sites) runs in the 2x2-block layout
+    int32_t blk_mask;     // bit k: class k (3 or 4 sites) runs in the 2x2-block layout; bit 5: the
+                          // 4-site class in that layout with one warp per region
     unsigned* bar;        // device arrival counter of the grid barrier (zeroed by launch_persistent)
     unsigned expect;      // arrivals per barrier (the grid; set by launch_persistent)
 };
-int persistent_tile_regions(int k);
+int persistent_tile_regions(int k, int32_t blk_mask);
 cudaError_t persistent_prepare(int kmax, int* blocks_per_sm);
 // One region pass of every class of the plan in one ordinary launch (grid = plan tiles).
 cudaError_t launch_class_pass(const DevProblem& P, const PersistPlan& L, int kmax, const PassIO& io, cudaStream_t s);

@@ -776,7 +776,8 @@ __device__ __forceinline__ void plan_tile(const DevProblem& P, const PersistPlan
         }
     } else {
         if constexpr (KMAX >= 4) {
-            if ((L.blk_mask >> 4) & 1) blk::region_pass_blk_impl<16, kBlock>(P, io, cls, count, 4, lt);
+            if ((L.blk_mask >> 5) & 1) blk::region_pass_w16_impl<kBlock>(P, io, cls, count, 4, lt);
+            else if ((L.blk_mask >> 4) & 1) blk::region_pass_blk_impl<16, kBlock>(P, io, cls, count, 4, lt);
             else region_pass_impl<16, kBlock>(P, io, cls, count, 4, lt);
         }
     }
@@ -913,7 +914,8 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, const int32_t* cls, int32_t count,
                                cudaStream_t s, int block) {
     if (count <= 0) return cudaSuccess;
-    if (block > kShapeBlocks && (k == 3 || k == 4))
+    if (block > kShapeWarp16 && k == 4) return launch_region_pass_w16(P, io, cls, count, s, block - kShapeWarp16);
+    if (block > kShapeBlocks && block < kShapeWarp16 && (k == 3 || k == 4))
         return launch_region_pass_blk(P, io, k, cls, count, s, block - kShapeBlocks);
     if (block > 0 && block != 64 && block != 256) block = 128;
     if (block < 0 && k != 2) block = 128;   // the one-thread-per-region layout exists for 4 x 4 only
@@ -983,7 +985,10 @@ cudaError_t launch_advance(const DevProblem& P, int n, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int persistent_tile_regions(int k) { return k == 1 ? kBlock : kBlock >> k; }
+int persistent_tile_regions(int k, int32_t blk_mask) {
+    if (k == 4 && ((blk_mask >> 5) & 1)) return kBlock / 32;   // one warp per region
+    return k == 1 ? kBlock : kBlock >> k;
+}
 
 cudaError_t persistent_prepare(int kmax, int* blocks_per_sm) {
     switch (kmax) {

@@ -141,3 +141,74 @@ def test_tiny_and_decoupled_pairs_stay_finite(scale):
     nu30 = s2.messages("nu")
     assert np.all(np.isfinite(nu30))
     assert np.all(np.abs(s2.bound("certified") - dual.dual_value(P, h, nu30.astype(np.complex128))) / p.n_sites <= 1e-12)
+
+
+# ---------------------------------------------------------------- one warp per 16 x 16 region
+WARP16 = 8192
+CASES16 = {k: v for k, v in CASES.items() if v[1] == 4}
+
+
+def _solver_w16(p, threads, **kw):
+    s = Solver(p, **kw)
+    s.set_launch_shape(4, WARP16 + threads)
+    assert s.info()["class_block"][s.info()["class_sites"].index(4)] == WARP16 + threads
+    return s
+
+
+@pytest.mark.parametrize("name", sorted(CASES16))
+@pytest.mark.parametrize("beta", [1.0, 16.0, 1024.0])
+def test_warp16_smoothed_pass_parity(name, beta):
+    p = CASES16[name][0]()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    nu = random_traceless_messages(P, p.n_instances, seed=61, scale=0.7)
+    s = _solver_w16(p, 128, variant="nesterov", beta=beta)
+    s.set_messages("nu", nu)
+    s.restart()
+    s.evaluate()
+    ref = dual.region_pass(P, h, nu.astype(np.complex128), "smooth", beta=beta)
+    norms = region_norms(P, h, nu)
+    assert np.all(np.abs(s.region_values("last") - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    err, worst = check_grad(s.messages("grad"), ref.grad, grad_entry_tol(P, norms, beta / 2))
+    print(f"GRADERR warp16 {name} beta={beta:g} max_abs={err:.3e} of_tol={worst:.3f}")
+
+
+@pytest.mark.parametrize("name", sorted(CASES16))
+def test_warp16_subgradient_and_cta_sizes(name):
+    p = CASES16[name][0]()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    nu = random_traceless_messages(P, p.n_instances, seed=62, scale=0.7)
+    s = _solver_w16(p, 64, variant="subgradient", alpha=0.1, step_rule="const")
+    s.set_messages("nu", nu)
+    s.evaluate()
+    ref = dual.region_pass(P, h, nu.astype(np.complex128), "ground", tol=1e-5)
+    norms = region_norms(P, h, nu)
+    assert np.all(np.abs(s.region_values("last") - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    check_grad(s.messages("grad"), ref.grad, grad_entry_tol(P, norms, ground_sensitivity(P, h, nu, 1e-5)))
+    out = {}
+    for threads in (64, 128, 256):
+        t = _solver_w16(p, threads, variant="nesterov", beta=4.0)
+        t.set_messages("nu", nu)
+        t.restart()
+        t.step(5)
+        out[threads] = (t.messages("nu"), t.messages("zeta"), t.bound("certified"))
+    for threads in (64, 256):
+        for a, b in zip(out[threads], out[128]):
+            assert np.array_equal(a, b)
+    assert np.all(np.abs(out[128][2] - dual.dual_value(P, h, out[128][0].astype(np.complex128))) / p.n_sites <= 1e-12)
+
+
+def test_warp16_in_one_launch_and_persistent_drivers_is_bit_identical():
+    """The one-launch class mode and the persistent driver run the same per-region code (tiles
+    of 4 regions per 128 threads for this layout): bit-identical to the per-class launches."""
+    p = L.xxz_triangular(4, 3)
+    res = []
+    for loop, mode in (("graph", 1), ("graph", 2), ("persistent", 1)):
+        s = Solver(p, beta=4.0, loop=loop)
+        s.set_launch_shape(4, WARP16 + 128)
+        s.set_class_mode(mode)
+        s.step(9)
+        res.append((s.messages("nu"), s.messages("zeta")))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and np.array_equal(r[1], res[0][1])
