@@ -135,6 +135,14 @@ typedef struct {
     int64_t n_pairs;
     const int32_t* pair_parent;
     const int32_t* pair_child;
+    /* Optional explicit term placement: term t is embedded into region term_region[t], which
+     * must contain its sites (LRH_EPOSET otherwise).  NULL: the placement rule above.        */
+    const int32_t* term_region;
+    /* Optional ghost flags [n_regions] (nonzero = ghost) of one shard of a sharded lattice (see
+     * lrh_halo_set): a ghost region's pass runs on another shard; this problem neither
+     * computes it nor counts it in its bounds.  NULL: no ghosts.  Not every region may be a
+     * ghost.                                                                                 */
+    const uint8_t* region_ghost;
 } lrh_problem_desc;
 
 typedef struct {
@@ -399,6 +407,58 @@ int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_
 /* Static message for an error code, and the thread-local detail of the last failure. */
 const char* lrh_strerror(int code);
 const char* lrh_last_error(void);
+
+/* ---------------------------------------------------------------- sharding with halo exchange
+ * One lattice split into shards, one problem (and GPU) per shard; Alg. 2 only.  The paper's
+ * region and message loops are independent within an iteration (Alg. 1 and Alg. 2 mark them
+ * parallel), so a shard needs from the others, per iteration, only the two inputs of the
+ * gradient g_{e->f} = rho_f - Tr_{e\f} rho_e of the pairs its cut crosses.
+ *
+ * A shard's problem holds the regions it owns plus ghost regions (region_ghost), the other
+ * endpoints of its crossing pairs, in the unsharded problem's relative order, with the pairs
+ * that touch an owned region (explicit pairs) and the unsharded term placement (term_region)
+ * restricted to owned regions.  Per iteration:
+ *   lrh_halo_pass    region pass of the owned regions at the current (nu, zeta): Gibbs states
+ *                    and partial traces, per-region values (asynchronous)
+ *   lrh_halo_pack    copies the send items' pieces into the caller's device buffer
+ *   (the caller moves the buffers between shards: NCCL, gloo, or a device copy)
+ *   lrh_halo_unpack  stores the received pieces: ghost children's states, ghost parents' traces
+ *   lrh_halo_update  the Alg. 2 update of every message (crossing pairs on both shards, from the
+ *                    same inputs), theta recurrence
+ * With the same L_hat (lrh_options.lhat > 0, the unsharded problem's beta Lambda_G / 2) and
+ * launch shapes, every message of a shard is bit-identical to the same pair's message of the
+ * unsharded run (lrh_step).  lrh_bound returns the shard's share of the sum (ghost regions count
+ * zero); the caller adds the shards' shares.  lrh_step, lrh_evaluate, lrh_solve, lrh_vjp and
+ * lrh_autotune return LRH_EUNSUPPORTED for problems with ghost regions. */
+#define LRH_HALO_STATE 0   /* item id = region with a parent: its state rho (D x D complex)           */
+#define LRH_HALO_TRACE 1   /* item id = pair e->f: the partial trace Tr_{e\f} rho_e (D_f x D_f complex) */
+typedef struct {
+    int32_t kind;          /* LRH_HALO_STATE or LRH_HALO_TRACE */
+    int32_t id;            /* region or pair index of this problem */
+} lrh_halo_item;
+
+/* Host-only plan of a problem description (no device work; usable without a GPU): the pairs
+ * (pair order; arrays of pair_cap entries, each may be NULL), their number, each term's region
+ * (term_region[n_terms], may be NULL) and Lambda_G (may be NULL), exactly as lrh_create would
+ * build them.  LRH_EINVAL if pair_cap is below the number of pairs and a pair array is given. */
+int lrh_plan_poset(const lrh_problem_desc* desc, int64_t pair_cap, int32_t* pair_parent, int32_t* pair_child,
+                   int64_t* n_pairs, int32_t* term_region, double* lambda_G);
+
+/* Register the exchange of a problem with ghost regions: `send` lists the pieces this shard
+ * sends (states of owned regions with a parent, traces of pairs with an owned parent), `recv`
+ * the pieces it receives (states of ghost regions, traces of pairs with a ghost parent), each in
+ * buffer order.  Every ghost region with a parent must be received exactly once, and every pair
+ * with a ghost parent too (LRH_EINVAL otherwise, naming the item).  Returns the complex entries
+ * per instance of the send and receive buffers (buffers are [n_instances][elems] complex64).
+ * Synchronises. */
+int lrh_halo_set(lrh_problem* p, int32_t n_send, const lrh_halo_item* send, int32_t n_recv,
+                 const lrh_halo_item* recv, int64_t* send_elems, int64_t* recv_elems);
+int lrh_halo_pass(lrh_problem* p);
+/* send / recv: device buffers on the problem's device, 16-byte aligned, stream-ordered. */
+int lrh_halo_pack(lrh_problem* p, void* send);
+int lrh_halo_unpack(lrh_problem* p, const void* recv);
+/* LRH_EINVAL unless lrh_halo_pass ran since the last update. */
+int lrh_halo_update(lrh_problem* p);
 
 #ifdef __cplusplus
 }

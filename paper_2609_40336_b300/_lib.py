@@ -37,7 +37,17 @@ class ProblemDesc(C.Structure):
         ("n_pairs", C.c_int64),
         ("pair_parent", C.POINTER(C.c_int32)),
         ("pair_child", C.POINTER(C.c_int32)),
+        ("term_region", C.POINTER(C.c_int32)),
+        ("region_ghost", C.POINTER(C.c_uint8)),
     ]
+
+
+class HaloItem(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("id", C.c_int32)]
+
+
+HALO_STATE = 0
+HALO_TRACE = 1
 
 
 class Options(C.Structure):
@@ -134,6 +144,13 @@ SIGNATURES = {
     "lrh_theorem_parameters": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.POINTER(Params)]),
     "lrh_reset": (C.c_int, [C.c_void_p]),
     "lrh_solve": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lrh_plan_poset": (C.c_int, [C.POINTER(ProblemDesc), C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
+    "lrh_halo_set": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lrh_halo_pass": (C.c_int, [C.c_void_p]),
+    "lrh_halo_pack": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lrh_halo_unpack": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "lrh_halo_update": (C.c_int, [C.c_void_p]),
     "lrh_strerror": (C.c_char_p, [C.c_int]),
     "lrh_last_error": (C.c_char_p, []),
 }

@@ -113,6 +113,16 @@ struct lrh_problem {
     int persist_grid = 0;
     int64_t persist_cap = 0;
     int loop_auto = -1;
+    // sharding with halo exchange: ghost regions (pass run by another shard) and the exchange maps
+    // of lrh_halo_set (per 4-entry chunk of one instance's buffer: offset in the state arena, or
+    // ~offset in the partial-trace arena)
+    std::vector<uint8_t> ghost;
+    bool has_ghost = false;
+    int64_t* halo_send = nullptr;
+    int64_t* halo_recv = nullptr;
+    int64_t halo_send_chunks = 0, halo_recv_chunks = 0;
+    bool halo_ready = false;
+    bool halo_passed = false;   // lrh_halo_pass ran and lrh_halo_update has not yet
 
     template <typename T>
     int dalloc(T** ptr, int64_t count) {
@@ -124,6 +134,11 @@ struct lrh_problem {
         allocs.push_back(p);
         *ptr = static_cast<T*>(p);
         return LRH_OK;
+    }
+    void dfree(void* ptr) {
+        if (!ptr) return;
+        allocs.erase(std::remove(allocs.begin(), allocs.end(), ptr), allocs.end());
+        cudaFree(ptr);
     }
     ~lrh_problem() {
         for (auto& g : nest_graphs) cudaGraphExecDestroy(g.second);
@@ -479,44 +494,31 @@ int read_err(lrh_problem* p) {
     return LRH_OK;
 }
 
-}  // namespace
+// Host plan of a region family (no device work): validated regions, pairs (explicit, or the
+// covering relation of inclusion), term placement (explicit, or the smallest containing region
+// with the lowest index), and the constants Lambda_G, Gamma_G, kappa_G of the parameter rules.
+struct PosetPlan {
+    std::vector<std::vector<int32_t>> regs;
+    std::vector<std::vector<std::pair<int, int>>> kids;   // per parent: (child, index-bit mask), ascending child
+    int maxk = 0;
+    std::vector<int32_t> place;       // term -> region
+    std::vector<int32_t> term_mask;   // bits of the region's basis index that carry the term's sites
+    double lambda_G = 0, gamma_G = 0;
+    int32_t kappa = 0;
+    int64_t n_pairs = 0;
+};
 
-extern "C" {
-
-const char* lrh_strerror(int code) {
-    switch (code) {
-        case LRH_OK: return "ok";
-        case LRH_EINVAL: return "invalid argument";
-        case LRH_ENOTHERM: return "term matrix is not Hermitian";
-        case LRH_EPOSET: return "invalid region family";
-        case LRH_ENOMEM: return "out of memory";
-        case LRH_ECUDA: return "CUDA error";
-        case LRH_ETIMEOUT: return "device wait timed out";
-        case LRH_ENUMERIC: return "non-finite value";
-        case LRH_EUNSUPPORTED: return "unsupported region size";
-        case LRH_ENOCONV: return "certification eigensolve not converged (bound still valid)";
-        case LRH_EDEADLINE: return "deadline reached";
-        default: return "unknown error";
-    }
-}
-
-const char* lrh_last_error(void) { return g_last_error.c_str(); }
-
-int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream, lrh_problem** out) {
-    if (!out) return fail(LRH_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!d) return fail(LRH_EINVAL, "desc is NULL");
-    int rc = validate_options(opts);
-    if (rc) return rc;
+int plan_poset(const lrh_problem_desc* d, PosetPlan& pl) {
     if (d->n_sites <= 0 || d->n_regions <= 0 || d->n_instances <= 0 || d->n_terms < 0)
         return fail(LRH_EINVAL, "n_sites, n_regions, n_instances must be positive");
     if (!d->region_ptr || !d->region_sites) return fail(LRH_EINVAL, "region arrays are NULL");
-    if (d->n_terms > 0 && (!d->term_ptr || !d->term_sites || !d->term_mat_off || !d->term_mats))
+    if (d->n_terms > 0 && (!d->term_ptr || !d->term_sites || !d->term_mat_off))
         return fail(LRH_EINVAL, "term arrays are NULL");
-
-    // ---------------------------------------------------------------- regions
     const int R = d->n_regions;
-    std::vector<std::vector<int32_t>> regs(R);
+    auto& regs = pl.regs;
+    auto& kids = pl.kids;
+    regs.assign(R, {});
+    kids.assign(R, {});
     std::unordered_map<std::vector<int32_t>, int, VecHash> index;
     index.reserve((size_t)R * 2);
     int maxk = 0;
@@ -532,11 +534,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         if (!index.emplace(regs[e], e).second) return fail(LRH_EPOSET, "duplicate region " + std::to_string(e));
         maxk = std::max<int>(maxk, (int)k);
     }
-    if (maxk > kMaxKernelSites)
-        return fail(LRH_EUNSUPPORTED, "regions of " + std::to_string(maxk) + " sites have no region-pass kernel in this build (at most " +
-                                          std::to_string(kMaxKernelSites) + ")");
-
-    std::vector<std::vector<std::pair<int, int>>> kids(R);   // (child, index-bit mask)
+    pl.maxk = maxk;
     if (d->n_pairs < 0) return fail(LRH_EINVAL, "n_pairs < 0");
     if (d->n_pairs > 0) {
         // explicit pairs: the child's sites must be a proper subset of the parent's
@@ -580,6 +578,119 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         }
         std::sort(kids[e].begin(), kids[e].end());
     }
+    // Lambda_G, Gamma_G and kappa_G
+    std::vector<int64_t> n_par(R, 0);
+    pl.n_pairs = 0;
+    for (int e = 0; e < R; ++e) for (auto& f : kids[e]) { ++n_par[f.first]; ++pl.n_pairs; }
+    bool level1 = maxk <= 2;
+    for (int e = 0; e < R; ++e) for (auto& f : kids[e]) if (!(regs[e].size() == 2 && regs[f.first].size() == 1)) level1 = false;
+    if (level1) {
+        int64_t deg = 0;
+        for (int e = 0; e < R; ++e) deg = std::max(deg, n_par[e]);
+        pl.lambda_G = (double)deg + 2.0;
+    } else {
+        double best = 0;
+        for (int e = 0; e < R; ++e)
+            for (auto& f : kids[e]) {
+                const double me = (double)(n_par[e] + (int64_t)kids[e].size());
+                const double mf = (double)(n_par[f.first] + (int64_t)kids[f.first].size());
+                const double ratio = std::ldexp(1.0, (int)regs[e].size() - (int)regs[f.first].size());
+                best = std::max(best, mf + me * ratio);
+            }
+        pl.lambda_G = best;
+    }
+    pl.gamma_G = 0;
+    for (int e = 0; e < R; ++e) pl.gamma_G += (double)regs[e].size() * std::log(2.0);
+    {   // kappa_G = max over sites i of |{e->f : i in f}| (Thm 6)
+        std::vector<int32_t> cnt(d->n_sites, 0);
+        for (int e = 0; e < R; ++e) for (auto& f : kids[e]) for (int32_t site : regs[f.first]) ++cnt[site];
+        pl.kappa = cnt.empty() ? 0 : *std::max_element(cnt.begin(), cnt.end());
+    }
+    // term placement
+    std::vector<std::vector<int32_t>> by_site(d->n_sites);
+    for (int e = 0; e < R; ++e) for (int32_t s : regs[e]) by_site[s].push_back(e);
+    pl.place.assign(d->n_terms, -1);
+    pl.term_mask.assign(d->n_terms, 0);
+    for (int t = 0; t < d->n_terms; ++t) {
+        const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
+        if (en - b < 1 || en - b > kMaxSites) return fail(LRH_EINVAL, "term " + std::to_string(t) + " has a bad site count");
+        std::vector<int32_t> ts(d->term_sites + b, d->term_sites + en);
+        for (size_t i = 0; i < ts.size(); ++i) {
+            if (ts[i] < 0 || ts[i] >= d->n_sites) return fail(LRH_EINVAL, "term site out of range");
+            if (i && ts[i] <= ts[i - 1]) return fail(LRH_EINVAL, "term sites must be sorted and unique");
+        }
+        int bestr = -1;
+        if (d->term_region) {
+            bestr = d->term_region[t];
+            if (bestr < 0 || bestr >= R) return fail(LRH_EINVAL, "term_region out of range");
+            if (!std::includes(regs[bestr].begin(), regs[bestr].end(), ts.begin(), ts.end()))
+                return fail(LRH_EPOSET, "term " + std::to_string(t) + " does not fit in its term_region");
+        } else {
+            for (int32_t e : by_site[ts[0]]) {
+                if (!std::includes(regs[e].begin(), regs[e].end(), ts.begin(), ts.end())) continue;
+                if (bestr < 0 || regs[e].size() < regs[bestr].size() || (regs[e].size() == regs[bestr].size() && e < bestr)) bestr = e;
+            }
+            if (bestr < 0) return fail(LRH_EPOSET, "term " + std::to_string(t) + " fits in no region");
+        }
+        const int64_t Dt = (int64_t)1 << ts.size();
+        const int64_t off = d->term_mat_off[t];
+        if (off < 0 || off + Dt * Dt > d->term_mat_total) return fail(LRH_EINVAL, "term matrix offset out of range");
+        const int k = (int)regs[bestr].size();
+        int M = 0;
+        for (int32_t site : ts) {
+            const int pos = (int)(std::find(regs[bestr].begin(), regs[bestr].end(), site) - regs[bestr].begin());
+            M |= 1 << (k - 1 - pos);
+        }
+        pl.place[t] = bestr;
+        pl.term_mask[t] = M;
+    }
+    return LRH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lrh_strerror(int code) {
+    switch (code) {
+        case LRH_OK: return "ok";
+        case LRH_EINVAL: return "invalid argument";
+        case LRH_ENOTHERM: return "term matrix is not Hermitian";
+        case LRH_EPOSET: return "invalid region family";
+        case LRH_ENOMEM: return "out of memory";
+        case LRH_ECUDA: return "CUDA error";
+        case LRH_ETIMEOUT: return "device wait timed out";
+        case LRH_ENUMERIC: return "non-finite value";
+        case LRH_EUNSUPPORTED: return "unsupported region size";
+        case LRH_ENOCONV: return "certification eigensolve not converged (bound still valid)";
+        case LRH_EDEADLINE: return "deadline reached";
+        default: return "unknown error";
+    }
+}
+
+const char* lrh_last_error(void) { return g_last_error.c_str(); }
+
+int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream, lrh_problem** out) {
+    if (!out) return fail(LRH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(LRH_EINVAL, "desc is NULL");
+    int rc = validate_options(opts);
+    if (rc) return rc;
+    if (d->n_sites <= 0 || d->n_regions <= 0 || d->n_instances <= 0 || d->n_terms < 0)
+        return fail(LRH_EINVAL, "n_sites, n_regions, n_instances must be positive");
+    if (!d->region_ptr || !d->region_sites) return fail(LRH_EINVAL, "region arrays are NULL");
+    if (d->n_terms > 0 && (!d->term_ptr || !d->term_sites || !d->term_mat_off || !d->term_mats))
+        return fail(LRH_EINVAL, "term arrays are NULL");
+
+    PosetPlan pl;
+    if ((rc = plan_poset(d, pl))) return rc;
+    const int R = d->n_regions;
+    const auto& regs = pl.regs;
+    const auto& kids = pl.kids;
+    const int maxk = pl.maxk;
+    if (maxk > kMaxKernelSites)
+        return fail(LRH_EUNSUPPORTED, "regions of " + std::to_string(maxk) + " sites have no region-pass kernel in this build (at most " +
+                                          std::to_string(kMaxKernelSites) + ")");
     lrh_problem* p = new (std::nothrow) lrh_problem();
     if (!p) return fail(LRH_ENOMEM, "host allocation");
     std::unique_ptr<lrh_problem> guard(p);
@@ -589,6 +700,12 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     p->n_regions = R;
     p->max_k = maxk;
     cudaGetDevice(&p->device);
+    p->ghost.assign(R, 0);
+    if (d->region_ghost)
+        for (int e = 0; e < R; ++e) p->ghost[e] = d->region_ghost[e] ? 1 : 0;
+    p->has_ghost = std::find(p->ghost.begin(), p->ghost.end(), 1) != p->ghost.end();
+    if (std::find(p->ghost.begin(), p->ghost.end(), 0) == p->ghost.end())
+        return fail(LRH_EINVAL, "every region is a ghost region");
 
     std::vector<PairInfo> pairs;
     std::vector<std::vector<int32_t>> parent_of(R);
@@ -619,68 +736,20 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     p->n_pairs = (int32_t)pairs.size();
     p->msg_elems = moff;
     for (auto& pi : pairs) { p->pair_parent.push_back(pi.parent); p->pair_child.push_back(pi.child); p->pair_off.push_back(pi.off); }
-
-    // Lambda_G and Gamma_G
-    bool level1 = maxk <= 2;
-    for (auto& pi : pairs) if (!(regs[pi.parent].size() == 2 && pi.kf == 1)) level1 = false;
-    if (level1) {
-        size_t deg = 0;
-        for (int e = 0; e < R; ++e) deg = std::max(deg, parent_of[e].size());
-        p->lambda_G = (double)deg + 2.0;
-    } else {
-        double best = 0;
-        for (auto& pi : pairs) {
-            const double me = (double)(parent_of[pi.parent].size() + kids[pi.parent].size());
-            const double mf = (double)(parent_of[pi.child].size() + kids[pi.child].size());
-            const double ratio = std::ldexp(1.0, (int)regs[pi.parent].size() - pi.kf);
-            best = std::max(best, mf + me * ratio);
-        }
-        p->lambda_G = best;
-    }
-    p->gamma_G = 0;
-    for (int e = 0; e < R; ++e) p->gamma_G += (double)regs[e].size() * std::log(2.0);
-    {   // kappa_G = max over sites i of |{e->f : i in f}| (Thm 6)
-        std::vector<int32_t> cnt(d->n_sites, 0);
-        for (auto& pi : pairs) for (int32_t site : regs[pi.child]) ++cnt[site];
-        p->kappa = cnt.empty() ? 0 : *std::max_element(cnt.begin(), cnt.end());
-    }
+    p->lambda_G = pl.lambda_G;
+    p->gamma_G = pl.gamma_G;
+    p->kappa = pl.kappa;
 
     // ---------------------------------------------------------------- terms
-    std::vector<std::vector<int32_t>> by_site(d->n_sites);
-    for (int e = 0; e < R; ++e) for (int32_t s : regs[e]) by_site[s].push_back(e);
-    std::vector<int> place(d->n_terms, -1);
     std::vector<char> has_term(R, 0);
     p->n_terms = d->n_terms;
     p->term_total = d->term_mat_total;
     for (int t = 0; t < d->n_terms; ++t) {
-        const int64_t b = d->term_ptr[t], en = d->term_ptr[t + 1];
-        if (en - b < 1 || en - b > kMaxSites) return fail(LRH_EINVAL, "term " + std::to_string(t) + " has a bad site count");
-        std::vector<int32_t> ts(d->term_sites + b, d->term_sites + en);
-        for (size_t i = 0; i < ts.size(); ++i) {
-            if (ts[i] < 0 || ts[i] >= d->n_sites) return fail(LRH_EINVAL, "term site out of range");
-            if (i && ts[i] <= ts[i - 1]) return fail(LRH_EINVAL, "term sites must be sorted and unique");
-        }
-        int bestr = -1;
-        for (int32_t e : by_site[ts[0]]) {
-            if (!std::includes(regs[e].begin(), regs[e].end(), ts.begin(), ts.end())) continue;
-            if (bestr < 0 || regs[e].size() < regs[bestr].size() || (regs[e].size() == regs[bestr].size() && e < bestr)) bestr = e;
-        }
-        if (bestr < 0) return fail(LRH_EPOSET, "term " + std::to_string(t) + " fits in no region");
-        place[t] = bestr;
-        has_term[bestr] = 1;
-        const int64_t Dt = (int64_t)1 << ts.size();
-        const int64_t off = d->term_mat_off[t];
-        if (off < 0 || off + Dt * Dt > d->term_mat_total) return fail(LRH_EINVAL, "term matrix offset out of range");
-        const int k = (int)regs[bestr].size();
-        int M = 0;
-        for (int32_t site : ts) {
-            const int pos = (int)(std::find(regs[bestr].begin(), regs[bestr].end(), site) - regs[bestr].begin());
-            M |= 1 << (k - 1 - pos);
-        }
-        p->term_region.push_back(bestr);
-        p->term_mask.push_back(M);
-        p->term_kt.push_back((int32_t)ts.size());
-        p->term_off.push_back(off);
+        has_term[pl.place[t]] = 1;
+        p->term_region.push_back(pl.place[t]);
+        p->term_mask.push_back(pl.term_mask[t]);
+        p->term_kt.push_back((int32_t)(d->term_ptr[t + 1] - d->term_ptr[t]));
+        p->term_off.push_back(d->term_mat_off[t]);
     }
     if (d->n_terms > 0 && (rc = check_terms(p, d->term_ptr, d->term_mats))) return rc;
     int64_t hoff = 0, roff = 0, aoff = 0;
@@ -800,7 +869,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     P.class_uniform = 0;
     for (int k = 1; k <= kMaxSites; ++k) {
         std::vector<int32_t> lst;
-        for (int e = 0; e < R; ++e) if ((int)regs[e].size() == k) lst.push_back(e);
+        for (int e = 0; e < R; ++e) if ((int)regs[e].size() == k && !p->ghost[e]) lst.push_back(e);   // ghosts: no pass here
         if (lst.empty()) continue;
         int32_t* dl;
         if ((rc = p->dalloc(&dl, (int64_t)lst.size()))) return rc;
@@ -937,6 +1006,7 @@ int lrh_restart(lrh_problem* p) {
 
 int lrh_step(lrh_problem* p, int32_t n_iters) {
     if (!p || n_iters < 0) return fail(LRH_EINVAL, "bad arguments to lrh_step");
+    if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     DeviceGuard dg(p->device);
     int rc;
     if (p->opt.variant == LRH_NESTEROV) {
@@ -967,6 +1037,7 @@ int lrh_step(lrh_problem* p, int32_t n_iters) {
 
 int lrh_evaluate(lrh_problem* p) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     DeviceGuard dg(p->device);
     const int par = (int)(p->iteration & 1);
     int rc = launch_all_classes(p, plain_io(p));
@@ -1073,6 +1144,7 @@ int lrh_set_terms(lrh_problem* p, const double* term_mats) {
 int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_bar_is_device, void* nu_bar,
             void* term_bar, int32_t out_is_device) {
     if (!p || !q_bar) return fail(LRH_EINVAL, "NULL argument");
+    if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     if (p->opt.variant != LRH_NESTEROV) return fail(LRH_EINVAL, "lrh_vjp differentiates the smoothed objective (LRH_NESTEROV)");
     if (p->max_k > 5) return fail(LRH_EUNSUPPORTED, "the adjoint kernels handle regions of at most 5 sites");
     DeviceGuard dg(p->device);
@@ -1250,6 +1322,7 @@ extern "C" {
 
 int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     DeviceGuard dg(p->device);
     int sms = 0;
     LRH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -1500,6 +1573,7 @@ int lrh_reset(lrh_problem* p) {
 int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_bounds, int32_t* n_records,
               double* bound_out) {
     if (!p || !bound_out) return fail(LRH_EINVAL, "NULL argument");
+    if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     if (max_records < 0 || (max_records > 0 && (!rec || !rec_bounds))) return fail(LRH_EINVAL, "bad record buffers");
     DeviceGuard dg(p->device);
     const auto t0 = std::chrono::steady_clock::now();
@@ -1556,6 +1630,153 @@ int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_
     }
     if (stop) return fail(LRH_EDEADLINE, "lrh_solve reached its deadline");
     return status;
+}
+
+int lrh_plan_poset(const lrh_problem_desc* desc, int64_t pair_cap, int32_t* pair_parent, int32_t* pair_child,
+                   int64_t* n_pairs, int32_t* term_region, double* lambda_G) {
+    if (!desc) return fail(LRH_EINVAL, "desc is NULL");
+    PosetPlan pl;
+    int rc = plan_poset(desc, pl);
+    if (rc) return rc;
+    if (n_pairs) *n_pairs = pl.n_pairs;
+    if (lambda_G) *lambda_G = pl.lambda_G;
+    if (term_region) std::copy(pl.place.begin(), pl.place.end(), term_region);
+    if (pair_parent || pair_child) {
+        if (pair_cap < pl.n_pairs) return fail(LRH_EINVAL, "pair_cap is below the number of pairs");
+        int64_t q = 0;
+        for (int e = 0; e < desc->n_regions; ++e)
+            for (auto& f : pl.kids[e]) {
+                if (pair_parent) pair_parent[q] = e;
+                if (pair_child) pair_child[q] = f.first;
+                ++q;
+            }
+    }
+    return LRH_OK;
+}
+
+int lrh_halo_set(lrh_problem* p, int32_t n_send, const lrh_halo_item* send, int32_t n_recv, const lrh_halo_item* recv,
+                 int64_t* send_elems, int64_t* recv_elems) {
+    if (!p || n_send < 0 || n_recv < 0 || (n_send > 0 && !send) || (n_recv > 0 && !recv))
+        return fail(LRH_EINVAL, "bad arguments to lrh_halo_set");
+    if (!p->has_ghost) return fail(LRH_EINVAL, "lrh_halo_set: the problem has no ghost regions");
+    DeviceGuard dg(p->device);
+    // rho offset of every region with a parent (-1 otherwise), from the pair table
+    std::vector<int64_t> rho_off(p->n_regions, -1);
+    {
+        std::vector<RegionInfo> ri(p->n_regions);
+        LRH_CK(cudaMemcpy(ri.data(), p->P.reg, sizeof(RegionInfo) * ri.size(), cudaMemcpyDeviceToHost));
+        for (int e = 0; e < p->n_regions; ++e) rho_off[e] = ri[e].rho_off;
+    }
+    auto build = [&](const lrh_halo_item* it, int32_t n, bool incoming, std::vector<int64_t>& map) -> int {
+        map.clear();
+        for (int32_t i = 0; i < n; ++i) {
+            const int32_t id = it[i].id;
+            int64_t off, elems;
+            if (it[i].kind == LRH_HALO_STATE) {
+                if (id < 0 || id >= p->n_regions) return fail(LRH_EINVAL, "halo state item: region out of range");
+                if (rho_off[id] < 0) return fail(LRH_EINVAL, "halo state item: region " + std::to_string(id) + " is no pair's child");
+                if ((p->ghost[id] != 0) != incoming)
+                    return fail(LRH_EINVAL, std::string("halo state item: region ") + std::to_string(id) +
+                                                (incoming ? " is not a ghost (only ghost states are received)"
+                                                          : " is a ghost (only owned states are sent)"));
+                off = rho_off[id];
+                elems = (int64_t)1 << (2 * p->region_k[id]);
+            } else if (it[i].kind == LRH_HALO_TRACE) {
+                if (id < 0 || id >= p->n_pairs) return fail(LRH_EINVAL, "halo trace item: pair out of range");
+                const int par = p->pair_parent[id];
+                if ((p->ghost[par] != 0) != incoming)
+                    return fail(LRH_EINVAL, std::string("halo trace item: pair ") + std::to_string(id) +
+                                                (incoming ? " has an owned parent (only traces of ghost parents are received)"
+                                                          : " has a ghost parent (only traces of owned parents are sent)"));
+                off = ~p->pair_off[id];
+                elems = (int64_t)1 << (2 * p->region_k[p->pair_child[id]]);
+            } else {
+                return fail(LRH_EINVAL, "halo item of unknown kind");
+            }
+            for (int64_t c = 0; c < elems / 4; ++c) map.push_back(off >= 0 ? off + 4 * c : ~(~off + 4 * c));
+        }
+        return LRH_OK;
+    };
+    std::vector<int64_t> smap, rmap;
+    int rc;
+    if ((rc = build(send, n_send, false, smap)) || (rc = build(recv, n_recv, true, rmap))) return rc;
+    // every ghost state and every ghost-parent trace the update reads is received exactly once
+    {
+        std::vector<int32_t> got_state(p->n_regions, 0), got_trace(p->n_pairs, 0);
+        for (int32_t i = 0; i < n_recv; ++i) (recv[i].kind == LRH_HALO_STATE ? got_state[recv[i].id] : got_trace[recv[i].id])++;
+        for (int e = 0; e < p->n_regions; ++e)
+            if (p->ghost[e] && rho_off[e] >= 0 && got_state[e] != 1)
+                return fail(LRH_EINVAL, "ghost region " + std::to_string(e) + " state is received " + std::to_string(got_state[e]) +
+                                            " times (exactly once needed)");
+        for (int q = 0; q < p->n_pairs; ++q)
+            if (p->ghost[p->pair_parent[q]] && got_trace[q] != 1)
+                return fail(LRH_EINVAL, "pair " + std::to_string(q) + " (ghost parent) trace is received " +
+                                            std::to_string(got_trace[q]) + " times (exactly once needed)");
+    }
+    p->dfree(p->halo_send);
+    p->dfree(p->halo_recv);
+    p->halo_send = p->halo_recv = nullptr;
+    p->halo_ready = false;
+    if ((rc = p->dalloc(&p->halo_send, (int64_t)smap.size())) || (rc = p->dalloc(&p->halo_recv, (int64_t)rmap.size()))) return rc;
+    if (!smap.empty()) LRH_CK(cudaMemcpy(p->halo_send, smap.data(), sizeof(int64_t) * smap.size(), cudaMemcpyHostToDevice));
+    if (!rmap.empty()) LRH_CK(cudaMemcpy(p->halo_recv, rmap.data(), sizeof(int64_t) * rmap.size(), cudaMemcpyHostToDevice));
+    p->halo_send_chunks = (int64_t)smap.size();
+    p->halo_recv_chunks = (int64_t)rmap.size();
+    p->halo_ready = true;
+    if (send_elems) *send_elems = 4 * p->halo_send_chunks;
+    if (recv_elems) *recv_elems = 4 * p->halo_recv_chunks;
+    return LRH_OK;
+}
+
+int lrh_halo_pass(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (p->opt.variant != LRH_NESTEROV) return fail(LRH_EUNSUPPORTED, "sharded iterations run Alg. 2 (LRH_NESTEROV) only");
+    if (!p->halo_ready) return fail(LRH_EINVAL, "lrh_halo_set has not been called");
+    DeviceGuard dg(p->device);
+    // the first pass of lrh_step: canonical nu, zeta in; states and traces to the X arenas
+    PassIO io{};
+    io.rel = 0;
+    io.writer = 1;
+    io.pending = 0;
+    io.nu_in = p->P.nu;
+    io.zeta_in = p->P.zeta;
+    io.rho_out = p->P.rho;
+    io.tr_out = p->P.tr;
+    int rc = launch_all_classes(p, io);
+    if (rc) return rc;
+    p->halo_passed = true;
+    return LRH_OK;
+}
+
+int lrh_halo_pack(lrh_problem* p, void* send) {
+    if (!p || (!send && p->halo_send_chunks > 0)) return fail(LRH_EINVAL, "NULL argument");
+    if (!p->halo_ready) return fail(LRH_EINVAL, "lrh_halo_set has not been called");
+    if ((reinterpret_cast<uintptr_t>(send) & 15) != 0) return fail(LRH_EINVAL, "halo buffer must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    if (p->halo_send_chunks) LRH_CK(launch_halo_copy(p->P, p->halo_send, p->halo_send_chunks, static_cast<float2*>(send), 0, p->stream));
+    return LRH_OK;
+}
+
+int lrh_halo_unpack(lrh_problem* p, const void* recv) {
+    if (!p || (!recv && p->halo_recv_chunks > 0)) return fail(LRH_EINVAL, "NULL argument");
+    if (!p->halo_ready) return fail(LRH_EINVAL, "lrh_halo_set has not been called");
+    if ((reinterpret_cast<uintptr_t>(recv) & 15) != 0) return fail(LRH_EINVAL, "halo buffer must be 16-byte aligned");
+    DeviceGuard dg(p->device);
+    if (p->halo_recv_chunks)
+        LRH_CK(launch_halo_copy(p->P, p->halo_recv, p->halo_recv_chunks, const_cast<float2*>(static_cast<const float2*>(recv)), 1,
+                                p->stream));
+    return LRH_OK;
+}
+
+int lrh_halo_update(lrh_problem* p) {
+    if (!p) return fail(LRH_EINVAL, "NULL problem");
+    if (!p->halo_passed) return fail(LRH_EINVAL, "lrh_halo_update needs a preceding lrh_halo_pass");
+    DeviceGuard dg(p->device);
+    int rc = enqueue_nesterov_tail(p, 1);   // the Alg. 2 update of every message from the X arenas
+    if (rc) return rc;
+    p->halo_passed = false;
+    p->iteration += 1;
+    return LRH_OK;
 }
 
 }  // extern "C"

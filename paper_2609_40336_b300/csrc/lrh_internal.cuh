@@ -172,6 +172,11 @@ cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, con
                                int32_t class_count, cudaStream_t s, int block = 128);
 // Alg. 2: apply the pending update of iteration t0 + rel into the canonical nu, zeta.
 cudaError_t launch_finalize(const DevProblem& P, const PassIO& io, cudaStream_t s);
+// Halo exchange of a sharded iteration: copies, for every instance, the 4-entry chunks listed in
+// map (>= 0: complex offset in the state arena rho; < 0: ~offset in the partial-trace arena tr)
+// into (unpack = 0) or out of (unpack = 1) the packed buffer buf[n_inst][4 n_chunks].
+cudaError_t launch_halo_copy(const DevProblem& P, const int64_t* map, int64_t n_chunks, float2* buf, int unpack,
+                             cudaStream_t s);
 // Alg. 2: t0 += n.
 cudaError_t launch_advance(const DevProblem& P, int n, cudaStream_t s);
 cudaError_t launch_certify(const DevProblem& P, int k, const int32_t* class_regions,

@@ -607,6 +607,22 @@ __global__ void finalize_kernel(const DevProblem P, const PassIO io) {
     }
 }
 
+// Halo exchange of a sharded iteration (see launch_halo_copy): one thread per two complex entries
+// (16 bytes; chunk offsets are multiples of 4 entries, the buffer is 16-byte aligned).
+__global__ void halo_copy_kernel(const DevProblem P, const int64_t* __restrict__ map, const int64_t n_chunks,
+                                 float2* __restrict__ buf, const int unpack) {
+    const int64_t per = 2 * n_chunks;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)P.n_inst * per) return;
+    const int64_t inst = tid / per, u = tid % per;
+    const int64_t m = map[u >> 1];
+    const int64_t j = (u & 1) * 2;
+    float2* arena = m >= 0 ? P.rho + inst * P.rho_elems + m : P.tr + inst * P.msg_elems + ~m;
+    float4* a = reinterpret_cast<float4*>(arena + j);
+    float4* b = reinterpret_cast<float4*>(buf + inst * 4 * n_chunks + 2 * u);
+    if (unpack) *a = *b; else *b = *a;
+}
+
 __global__ void advance_kernel(IterState* st, int n) { st->t0 += n; }
 
 // Deterministic per-instance FP64 sum of per-region values (fixed strided partial sums and a
@@ -977,6 +993,14 @@ cudaError_t launch_finalize(const DevProblem& P, const PassIO& io, cudaStream_t 
     const int64_t n = (int64_t)P.n_inst * (P.msg_elems >> 1);
     if (n <= 0) return cudaSuccess;
     finalize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, io);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_copy(const DevProblem& P, const int64_t* map, int64_t n_chunks, float2* buf, int unpack,
+                             cudaStream_t s) {
+    const int64_t n = (int64_t)P.n_inst * 2 * n_chunks;
+    if (n <= 0) return cudaSuccess;
+    halo_copy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, map, n_chunks, buf, unpack);
     return cudaGetLastError();
 }
 

@@ -24,10 +24,13 @@ def _ptr(a: np.ndarray, ctype):
 
 
 def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence[Sequence[int]],
-            term_mats: Sequence[np.ndarray], pairs: Optional[Sequence[Sequence[int]]] = None):
+            term_mats: Sequence[np.ndarray], pairs: Optional[Sequence[Sequence[int]]] = None,
+            term_region: Optional[Sequence[int]] = None, ghost: Optional[Sequence[bool]] = None):
     """Flat host arrays of lrh_problem_desc.  term_mats[t] has shape
     (n_instances, 2^k, 2^k) or (2^k, 2^k); ``pairs`` optionally lists explicit (parent, child)
-    region pairs (default: the covering relation, derived by the library)."""
+    region pairs (default: the covering relation, derived by the library); ``term_region``
+    optionally places each term in a given region; ``ghost`` flags the ghost regions of one
+    shard of a sharded lattice."""
     region_ptr = np.zeros(len(regions) + 1, np.int64)
     region_ptr[1:] = np.cumsum([len(r) for r in regions])
     region_sites = np.ascontiguousarray([s for r in regions for s in r], np.int32)
@@ -49,17 +52,37 @@ def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence
         flat[:, o:o + m.shape[1] * m.shape[2]] = m.reshape(n_inst, -1)
     pp = np.ascontiguousarray([q[0] for q in pairs] if pairs else [0], np.int32)
     pc = np.ascontiguousarray([q[1] for q in pairs] if pairs else [0], np.int32)
+    tr = np.ascontiguousarray(term_region if term_region is not None else [0], np.int32)
+    gh = np.ascontiguousarray(np.asarray(ghost, bool) if ghost is not None else [0], np.uint8)
     keep = dict(region_ptr=region_ptr, region_sites=region_sites, term_ptr=term_ptr, term_sites=tsites,
                 term_mat_off=off, term_mats=np.ascontiguousarray(flat).view(np.float64),
-                pair_parent=pp, pair_child=pc)
+                pair_parent=pp, pair_child=pc, term_region=tr, ghost=gh)
     desc = L.ProblemDesc(n_sites=int(n_sites), n_regions=len(regions),
                          region_ptr=_ptr(region_ptr, C.c_int64), region_sites=_ptr(region_sites, C.c_int32),
                          n_terms=len(mats), term_ptr=_ptr(term_ptr, C.c_int64),
                          term_sites=_ptr(tsites, C.c_int32), term_mat_off=_ptr(off, C.c_int64),
                          term_mat_total=total, term_mats=_ptr(keep["term_mats"], C.c_double),
                          n_instances=int(n_inst), n_pairs=len(pairs) if pairs else 0,
-                         pair_parent=_ptr(pp, C.c_int32), pair_child=_ptr(pc, C.c_int32))
+                         pair_parent=_ptr(pp, C.c_int32), pair_child=_ptr(pc, C.c_int32),
+                         term_region=_ptr(tr, C.c_int32) if term_region is not None else None,
+                         region_ghost=_ptr(gh, C.c_uint8) if ghost is not None else None)
     return desc, keep
+
+
+def plan_poset(n_sites: int, regions, term_sites, term_mats, pairs=None):
+    """Host-only plan of a problem (lrh_plan_poset; no GPU needed): pair parents, pair
+    children (pair order), each term's region and Lambda_G, as lrh_create would build them."""
+    lib = L.load()
+    desc, keep = marshal(n_sites, regions, term_sites, term_mats, pairs)
+    n = C.c_int64(0)
+    lam = C.c_double(0.0)
+    L.check(lib.lrh_plan_poset(C.byref(desc), 0, None, None, C.byref(n), None, None), "lrh_plan_poset")
+    par = np.zeros(max(n.value, 1), np.int32)
+    chi = np.zeros(max(n.value, 1), np.int32)
+    treg = np.zeros(max(len(term_sites), 1), np.int32)
+    L.check(lib.lrh_plan_poset(C.byref(desc), n.value, par.ctypes.data, chi.ctypes.data, C.byref(n),
+                               treg.ctypes.data, C.byref(lam)), "lrh_plan_poset")
+    return par[:n.value], chi[:n.value], treg[:len(term_sites)], lam.value
 
 
 def _current_stream():
@@ -105,7 +128,8 @@ class Solver:
         self._lib = L.load()
         self._h = C.c_void_p(0)
         desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats,
-                                   getattr(problem, "pairs", None))
+                                   getattr(problem, "pairs", None), getattr(problem, "term_region", None),
+                                   getattr(problem, "ghost", None))
         self._opt = L.Options(variant=_VARIANTS[variant], step_rule=_RULES[step_rule], alpha=float(alpha),
                               beta=float(beta), lhat=float(lhat) if lhat else 0.0, degen_tol=float(degen_tol),
                               max_sweeps=int(max_sweeps), loop=_loop_code(loop, use_graph),

@@ -122,11 +122,13 @@ def test_autotune_chooses_a_driver_and_restores_the_multipliers():
     assert s.info()["iteration"] == it0
     for w, v in before.items():
         assert np.array_equal(s.messages(w), v), w
-    # and the tuned driver continues exactly like a fresh graph-driven copy (lane layouts are
-    # bit-identical; a one-thread-per-region 4 x 4 shape rotates in another order)
-    if tuned["loop"] == "graph" and min(tuned["class_block"]) < 0:
-        return
+    # and the tuned driver continues exactly like a fresh graph-driven copy with the same layouts:
+    # all lane-row shapes are bit-identical to one another, and so are all shapes of one 2x2-block
+    # or one-warp layout; the persistent driver runs a one-thread-per-region 4 x 4 class (negative
+    # shape) in the lane-row layout
     ref = Solver(p, beta=2.0, loop="graph")
+    for k, sh in zip(tuned["class_sites"], tuned["class_block"]):
+        ref.set_launch_shape(k, sh if (sh > 0 or tuned["loop"] == "graph") else 128)
     ref.set_messages("nu", nu)
     ref.restart()
     ref.step(5)
