@@ -93,7 +93,7 @@ extern "C" {
 #define LRH_SHAPE_WARP16  8192  /* lrh_set_launch_shape, 4-site classes: LRH_SHAPE_WARP16 + 64 / 128 / 256
                                    selects the 2x2-block layout with one warp per 16 x 16 region (each
                                    lane one off-diagonal block and half a row of V) */
-#define LRH_SHAPE_CTA_FP32   1  /* lrh_set_launch_shape, classes of 6-7 sites: rho = W W^dagger on the FP32 cores */
+#define LRH_SHAPE_CTA_FP32   1  /* lrh_set_launch_shape, classes of 6-8 sites: rho = W W^dagger on the FP32 cores */
 #define LRH_SHAPE_CTA_TENSOR 2  /* ... on the tensor cores (tcgen05, three TF32 products per term, FP32
                                    accumulate); 7-site (128 x 128) regions only */
 
@@ -118,7 +118,7 @@ typedef struct {
     int32_t n_sites;              /* sites 0 .. n_sites-1, all qubits                          */
     int32_t n_regions;            /* regions of the cluster family                             */
     const int64_t* region_ptr;    /* [n_regions + 1] CSR offsets into region_sites             */
-    const int32_t* region_sites;  /* sorted, unique site ids of each region (1..7 sites)       */
+    const int32_t* region_sites;  /* sorted, unique site ids of each region (1..8 sites)       */
     int32_t n_terms;              /* Hamiltonian terms                                          */
     const int64_t* term_ptr;      /* [n_terms + 1] CSR offsets into term_sites                 */
     const int32_t* term_sites;    /* sorted, unique sites of each term                          */
@@ -153,7 +153,8 @@ typedef struct {
     double  lhat;         /* Lipschitz estimate L_hat; <= 0 selects beta * Lambda_G / 2       */
     double  degen_tol;    /* ground space = eigenvalues within degen_tol * max(1,||theta||_F)
                              of lambda_min (subgradient); <= 0 selects 1e-5                   */
-    int32_t max_sweeps;   /* Jacobi sweep cap of the FP32 eigensolver; <= 0 selects 15        */
+    int32_t max_sweeps;   /* Jacobi sweep cap of the FP32 eigensolver; <= 0 selects 15 (regions
+                             of 8 sites: at most 16, the sweeps their rotation log holds)   */
     int32_t loop;         /* iteration driver of lrh_step: LRH_LOOP_EAGER (kernel launches),
                              LRH_LOOP_GRAPH (a captured CUDA graph of iterations),
                              LRH_LOOP_PERSISTENT (one cooperative launch running all the
@@ -194,7 +195,7 @@ typedef struct {
     uint64_t sweeps[8];           /* cumulative FP32 Jacobi sweeps x regions, per class        */
     int32_t class_block[8];       /* threads per CTA of each class's region pass (autotuned);
                                      negative: one thread per region (4 x 4 regions); classes of
-                                     6-7 sites: LRH_SHAPE_CTA_FP32 / LRH_SHAPE_CTA_TENSOR        */
+                                     6-8 sites: LRH_SHAPE_CTA_FP32 / LRH_SHAPE_CTA_TENSOR        */
     int32_t concurrent_classes;   /* region classes of one pass: 0 one after another, 1 on forked
                                      streams, 2 in one launch (classes of <= 4 sites; autotuned) */
     int32_t loop;                 /* driver lrh_step uses now (LRH_LOOP_EAGER/GRAPH/PERSISTENT)  */
@@ -324,7 +325,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
 /* Set the launch shape of one region class by hand (what lrh_autotune chooses): 64, 128 or
  * 256 threads per CTA with 2^k_sites lanes per region, or for 4 x 4 regions -64, -128, -256 for
  * one thread per region.  The lane layouts give bit-identical results; the one-thread layout
- * rotates in another order and agrees to rounding.  For classes of 6 or 7 sites (one CTA per
+ * rotates in another order and agrees to rounding.  For classes of 6 to 8 sites (one CTA per
  * region) the shape selects the back-transform: LRH_SHAPE_CTA_FP32, or for 7 sites also
  * LRH_SHAPE_CTA_TENSOR (results agree to FP32 rounding). */
 int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block);

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "liblrh.so")
 LRH_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOTHERM", -3: "EPOSET", -4: "ENOMEM", -5: "ECUDA",
           -6: "ETIMEOUT", -7: "ENUMERIC", -8: "EUNSUPPORTED", -9: "ENOCONV", -10: "EDEADLINE"}
+EINVAL, ENOTHERM, EPOSET, ENOMEM, ECUDA, ETIMEOUT, ENUMERIC, EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7, -8
 ENOCONV, EDEADLINE = -9, -10
 SUBGRADIENT, NESTEROV = 0, 1
 STEP_CONST, STEP_INV_SQRT = 0, 1

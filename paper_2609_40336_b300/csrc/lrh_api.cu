@@ -44,8 +44,9 @@ struct VecHash {
     }
 };
 
-constexpr int kMaxSites = 7;     // region size limit of the data layout (D <= 128)
-constexpr int kMaxKernelSites = 7;  // sizes with a region-pass kernel in this build (D <= 128)
+constexpr int kMaxSites = 8;     // region size limit of the data layout (D <= 256)
+constexpr int kMaxKernelSites = 8;  // sizes with a region-pass kernel in this build (D <= 256)
+constexpr int kBigLogSweeps = 16;   // FP32 sweep cap of 8-site regions (their rotation log holds 16 sweeps)
 constexpr int kGraphChunk = 8;   // iterations per captured graph (even: parity returns to 0)
 
 struct DeviceGuard {
@@ -194,7 +195,7 @@ int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
 // Hermitian part of every term matrix (exactly: (m + m^dagger)/2) embedded into the dense
 // region terms h_e in FP64, instance-major, at the offsets of region_h_off.
 void embed_terms(const lrh_problem* p, const double* term_mats, std::vector<double>& h64) {
-    auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 7; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
+    auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 8; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
     h64.assign((size_t)(2 * p->n_inst * std::max<int64_t>(p->h_elems, 1)), 0.0);
     for (int t = 0; t < p->n_terms; ++t) {
         const int e = p->term_region[t];
@@ -525,7 +526,7 @@ int plan_poset(const lrh_problem_desc* d, PosetPlan& pl) {
     for (int e = 0; e < R; ++e) {
         const int64_t b = d->region_ptr[e], en = d->region_ptr[e + 1];
         const int64_t k = en - b;
-        if (k < 1 || k > kMaxSites) return fail(LRH_EINVAL, "region " + std::to_string(e) + " has " + std::to_string(k) + " sites (1..7 allowed)");
+        if (k < 1 || k > kMaxSites) return fail(LRH_EINVAL, "region " + std::to_string(e) + " has " + std::to_string(k) + " sites (1..8 allowed)");
         regs[e].assign(d->region_sites + b, d->region_sites + en);
         for (int64_t i = 0; i < k; ++i) {
             if (regs[e][i] < 0 || regs[e][i] >= d->n_sites) return fail(LRH_EINVAL, "region site out of range");
@@ -914,6 +915,15 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         if (p->class_k[c] == 3 || p->class_k[c] == 4) p->class_block[c] = LRH_SHAPE_BLOCKS + 128;   // 2x2-block layout
     }
     p->P.tc_backtransform = 0;
+    if (maxk == 8) {   // scratch slots of the D = 256 pass (theta overflow, V, rho, rotation log)
+        int slots = 0;
+        LRH_CK(big_launch_slots(&slots));
+        const int64_t slot = big_slot_elems(kBigLogSweeps);
+        if ((rc = p->dalloc(&P.big, (int64_t)slots * slot))) return rc;
+        P.big_slot = slot;
+        P.big_slots = slots;
+        P.big_log_sweeps = kBigLogSweeps;
+    }
     if ((rc = plan_persistent(p))) return rc;
     LRH_CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
     for (size_t c = 1; c < p->class_k.size(); ++c) {

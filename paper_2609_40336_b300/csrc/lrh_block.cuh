@@ -223,6 +223,11 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     const int sd0 = phys_unit<D>(bidx<D>(pp, pp)), sd1 = phys_unit<D>(NB + bidx<D>(pp, pp));
     const int d0 = dest<D>(2 * pp, 2 * pp), d3 = dest<D>(2 * pp + 1, 2 * pp + 1);
     const int d1x = dest<D>(2 * pp, 2 * pp + 1), d1 = d1x < 0 ? ~d1x : d1x;
+    const float sg1 = d1x < 0 ? -1.f : 1.f;
+    // Each region stops at its own test; while other regions of the warp still sweep, a stopped
+    // region runs identity rotations (every value kept exactly, only the tournament permutation
+    // applied, which whole sweeps undo), so its result does not depend on its warp neighbours.
+    bool active = true;
 
     // V takes each round's rotations one round late (so that their dependent chain overlaps V's
     // independent FMAs); it starts as the identity with its columns in inverse tournament order,
@@ -278,11 +283,17 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
             RotC<float> Rk;
             float2 dn;
             rot_fast(h0.x, h1.z, h0.z, h0.w, Rk, dn);
+            float2 b1 = make_float2(0.f, 0.f);
+            if (!active) {
+                Rk = RotC<float>{1.f, 0.f, 0.f, 0.f};
+                dn = make_float2(h0.x, h1.z);
+                b1 = make_float2(h0.z, sg1 * h0.w);
+            }
             if (s < n) {
                 pc[s] = Rk;
                 nxt[d0] = make_float2(dn.x, 0.f);
                 nxt[d3] = make_float2(dn.y, 0.f);
-                nxt[d1] = make_float2(0.f, 0.f);
+                nxt[d1] = b1;
             }
         }
         vstep(prm2 + n * (par ^ 1), xr, xi, yr, yi);
@@ -317,11 +328,15 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     const float thresh = 1e-12f * norm2;
     int sweeps = 0, par = 0;
     float ur[D], ui[D];
-    for (;;) {
-        if (sweeps > 0) sums(cur, off2, norm2);
-        const bool done = (off2 <= thresh) || (sweeps >= max_sweeps);
-        if (__all_sync(kFull, done)) break;
-        ++sweeps;
+    for (bool first = true;; first = false) {
+        if (!first) {
+            float o2, a2;
+            sums(cur, o2, a2);
+            if (active) { off2 = o2; norm2 = a2; }
+        }
+        if (active) active = !((off2 <= thresh) || (sweeps >= max_sweeps));
+        if (!__any_sync(kFull, active)) break;
+        if (active) ++sweeps;
 #pragma unroll 1
         for (int rd = 0; rd + 1 < D - 1; rd += 2) {
             round(cur, nxt, par, vr, vi, ur, ui);

@@ -20,6 +20,7 @@
 #include "lrh_device.cuh"
 #include "lrh_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -36,18 +37,18 @@ __host__ __device__ constexpr int rr_src_c(int s, int D) {
     return s == 0 ? 0 : (s == 2 ? 1 : ((s & 1) == 0 ? s - 2 : (s == D - 1 ? D - 2 : s + 2)));
 }
 
-__device__ __forceinline__ int pext7(int x, int m) {
+__device__ __forceinline__ int pext8(int x, int m) {
     int r = 0, k = 0;
 #pragma unroll
-    for (int b = 0; b < 7; ++b)
+    for (int b = 0; b < 8; ++b)
         if ((m >> b) & 1) { r |= ((x >> b) & 1) << k; ++k; }
     return r;
 }
 
-__device__ __forceinline__ int pdep7(int x, int m) {
+__device__ __forceinline__ int pdep8(int x, int m) {
     int r = 0, k = 0;
 #pragma unroll
-    for (int b = 0; b < 7; ++b)
+    for (int b = 0; b < 8; ++b)
         if ((m >> b) & 1) { r |= ((x >> k) & 1) << b; ++k; }
     return r;
 }
@@ -136,6 +137,43 @@ struct Full {
     }
 };
 
+// Hermitian matrix too large for shared memory (D = 256): a packed upper triangle whose first NS
+// entries live in shared memory and the rest in a global-memory scratch slot of this CTA (held in
+// L2 while the CTA runs).  Positions are the logical indices (sig = identity), as for Packed.
+// Global entries are read and written with plain loads and stores; the CTA barriers between
+// Jacobi phases make them visible to the other threads of the CTA.
+template <typename T>
+struct Split {
+    using C2 = typename V2<T>::t;
+    using Real = T;
+    C2* s;     // entries [0, NS)
+    C2* g;     // entries [NS, D (D + 1) / 2)
+    int NS;
+    int D;
+    __device__ __forceinline__ int sig(int j) const { return j; }
+    __device__ __forceinline__ C2& at(int x) const { return x < NS ? s[x] : g[x - NS]; }
+    __device__ __forceinline__ C2 get(int i, int j) const {
+        if (i <= j) return at(tri(i, j, D));
+        C2 v = at(tri(j, i, D));
+        v.y = -v.y;
+        return v;
+    }
+    __device__ __forceinline__ void set(int i, int j, C2 v) const {
+        if (i <= j) { at(tri(i, j, D)) = v; } else { v.y = -v.y; at(tri(j, i, D)) = v; }
+    }
+    __device__ __forceinline__ C2 dget(int i) const { return at(tri(i, i, D)); }
+    __device__ __forceinline__ void dset(int i, C2 v) const { at(tri(i, i, D)) = v; }
+    template <int NT>
+    __device__ __forceinline__ void sums(T& offd, T& diag) const {
+        offd = T(0); diag = T(0);
+        for (int e = threadIdx.x; e < D * D; e += NT) {
+            const int i = e / D, j = e - (e / D) * D;
+            if (i < j) { const C2 v = at(tri(i, j, D)); offd += v.x * v.x + v.y * v.y; }
+        }
+        for (int i = threadIdx.x; i < D; i += NT) { const C2 v = at(tri(i, i, D)); diag += v.x * v.x + v.y * v.y; }
+    }
+};
+
 // V rows in registers: a warp holds 8 rows x 4 column chunks, lane = 8 chunk + (row mod 8).
 // The 8 lanes of a quarter-warp share one chunk, so the rotation parameters they read are one
 // shared-memory address (a broadcast), and the neighbour chunk of the same row is 8 lanes away.
@@ -163,6 +201,7 @@ __device__ __forceinline__ int prm_at(int k) { return k + k / (D / 8); }
 template <int D> struct CtaCfg;
 template <> struct CtaCfg<64> { static constexpr int NT = 256; static constexpr int TR = 4, TC = 4; };
 template <> struct CtaCfg<128> { static constexpr int NT = 512; static constexpr int TR = 4, TC = 8; };
+template <> struct CtaCfg<256> { static constexpr int NT = 1024; };
 
 template <int D, typename T>
 struct CtaSmem {
@@ -195,10 +234,12 @@ struct CtaSmem {
 // (Computing the next round's rotations inside the block updates, to save the first barrier,
 // measured slower: the 64 parameter computations then fall on many warps, each of which runs
 // the divisions and square roots for one lane, instead of two warps running them for all.)
-template <int D, typename T, bool WANT_V, typename Acc>
+// LOG (instead of V): every round's rotations are appended to `log` (n records per round, the
+// pair's two positions packed into the pad word), for V to be formed afterwards.
+template <int D, typename T, bool WANT_V, typename Acc, bool LOG = false>
 __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
                           T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out,
-                          T& off_out) {
+                          T& off_out, RotC<T>* log = nullptr) {
     using C2 = typename V2<T>::t;
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
@@ -235,6 +276,11 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
                 const auto b = A.get(pq.x, pq.y);
                 C2 unused;
                 rot_params_d<T>(A.dget(pq.x).x, A.dget(pq.y).x, b.x, b.y, prm[prm_at<D>(t)], unused);
+                if constexpr (LOG) {
+                    RotC<T> e = prm[prm_at<D>(t)];
+                    e.pad = __int_as_float(pq.x | (pq.y << 16));
+                    log[((size_t)(sweeps - 1) * (D - 1) + r) * n + t] = e;
+                }
             }
             __syncthreads();
             if (t < D) ixn[t] = ix[rr_src_c(t, D)];
@@ -313,8 +359,8 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
 
 // theta entries (i <= j) into the packed triangle: h_e - sum_children 1 (x) m + sum_parents m,
 // m = (1 - th) nu + th zeta (zeta == nullptr: m = nu).  FP64 path reads h64.
-template <int D, typename T>
-__device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int inst, Packed<T> A,
+template <int D, typename T, typename Acc>
+__device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int inst, Acc A,
                                 const float2* __restrict__ nu, const float2* __restrict__ zeta, float th, bool use_h64) {
     constexpr int NT = CtaCfg<D>::NT;
     const int64_t mbase = (int64_t)inst * P.msg_elems;
@@ -336,7 +382,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
             const PairInfo pi = P.child_info[q];
             if (((i ^ j) & ~pi.mask) != 0) continue;
             const int Df = 1 << pi.kf;
-            const int64_t o = mbase + pi.off + (int64_t)pext7(i, pi.mask) * Df + pext7(j, pi.mask);
+            const int64_t o = mbase + pi.off + (int64_t)pext8(i, pi.mask) * Df + pext8(j, pi.mask);
             float2 m = nu[o];
             if (zeta) { const float2 z = zeta[o]; m.x = om * m.x + th * z.x; m.y = om * m.y + th * z.y; }
             re -= T(m.x); im -= T(m.y);
@@ -350,14 +396,14 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
         }
         if (i == j) im = T(0);
         typename V2<T>::t v; v.x = re; v.y = im;
-        A.a[tri(i, j, D)] = v;
+        A.set(i, j, v);
     }
 }
 
 // FP32 pass version: message entries from pass_entry (pending Alg. 2 update applied); the
 // region owns its parent messages and also stores their conjugate (lower-triangle) entries.
-template <int D>
-__device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Full<float> A, const PassIO& io,
+template <int D, typename Acc>
+__device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int inst, Acc A, const PassIO& io,
                                    const dev::Thetas& T) {
     constexpr int NT = CtaCfg<D>::NT;
     const int64_t mbase = (int64_t)inst * P.msg_elems;
@@ -375,7 +421,7 @@ __device__ void assemble_packed_io(const DevProblem& P, const RegionInfo& R, int
             const PairInfo pi = P.child_info[q];
             if (((i ^ j) & ~pi.mask) != 0) continue;
             const int Df = 1 << pi.kf;
-            const int64_t x = (int64_t)pext7(i, pi.mask) * Df + pext7(j, pi.mask);
+            const int64_t x = (int64_t)pext8(i, pi.mask) * Df + pext8(j, pi.mask);
             const float2 m = dev::pass_entry(io, T, mbase + pi.off + x, rbase + pi.child_rho + x, false);
             re -= m.x; im -= m.y;
         }
@@ -717,10 +763,10 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
                 const PairInfo pi = P.child_info[q];
                 const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
                 for (int o = t; o < Df * Df; o += NT) {
-                    const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
+                    const int ra = pdep8(o >> kf, M), rbb = pdep8(o & (Df - 1), M);
                     float sr = 0.f, si = 0.f;
                     for (int c = 0; c < nrest; ++c) {
-                        const int x = pdep7(c, Mc);
+                        const int x = pdep8(c, Mc);
                         const float2 v = rho_at(ra | x, rbb | x);
                         sr += v.x; si += v.y;
                     }
@@ -786,10 +832,10 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
             const PairInfo pi = P.child_info[q];
             const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
             for (int o = t; o < Df * Df; o += NT) {
-                const int ra = pdep7(o >> kf, M), rbb = pdep7(o & (Df - 1), M);
+                const int ra = pdep8(o >> kf, M), rbb = pdep8(o & (Df - 1), M);
                 float sr = 0.f, si = 0.f;
                 for (int c = 0; c < nrest; ++c) {
-                    const int x = pdep7(c, Mc);
+                    const int x = pdep8(c, Mc);
                     const float2 v = buf[(ra | x) * D + (rbb | x)];
                     sr += v.x; si += v.y;
                 }
@@ -840,6 +886,274 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// D = 256 (regions of 8 sites).  theta's packed upper triangle (32,896 complex entries: 263 KB in
+// FP32, 526 KB in FP64) exceeds one CTA's shared memory: its first entries stay there and the
+// rest lives in this CTA's global scratch slot (kept in L2 while the CTA runs; Split accessor).
+// V (512 KB) fits neither registers nor shared memory during the sweeps, so the sweeps append
+// their rotations to a log in the slot (16 bytes per pair and round), and V is formed afterwards
+// by replaying the log on 64 rows at a time in shared memory: rows of V are independent (each is
+// a row of the identity times J_1 J_2 ...), so each warp owns two rows and needs only a warp
+// barrier between rounds.  rho = W W^dagger (W = V diag(sqrt p)) is formed tile by tile into the
+// slot and traced onto the children.  One 1024-thread CTA per SM, each looping over the regions
+// of the launch.
+constexpr int kBigD = 256;
+constexpr int kBigN = kBigD / 2;
+constexpr int kBigTri = kBigD * (kBigD + 1) / 2;   // 32,896 entries
+constexpr int kBigNOFF = kBigN * (kBigN - 1) / 2;   // 8,128 off-diagonal 2x2 blocks
+constexpr int kBigRB = 64;                          // V rows per batch (two per warp)
+constexpr int kBigT = 64;                           // rho tile edge
+
+struct BigSmem {
+    static constexpr size_t prm_bytes = sizeof(RotC<double>) * (kBigN + 8);
+    static constexpr size_t idx_bytes = sizeof(int) * 2 * kBigD;
+    static constexpr size_t tab_bytes = (sizeof(unsigned short) * kBigNOFF + 15) / 16 * 16;
+    static constexpr size_t lam_bytes = sizeof(double) * 2 * kBigD;
+    static constexpr size_t red_bytes = sizeof(double) * 32;
+    static constexpr size_t fixed = prm_bytes + idx_bytes + tab_bytes + lam_bytes + red_bytes;
+    static constexpr size_t total = 227 * 1024;   // opt-in shared memory of one CTA
+    static constexpr size_t tri_bytes = (total - fixed) / 16 * 16;
+    static constexpr int ns32 = (int)(tri_bytes / sizeof(float2));
+    static constexpr int ns64 = (int)(tri_bytes / sizeof(double2));
+    static constexpr size_t off_prm = tri_bytes;
+    static constexpr size_t off_idx = off_prm + prm_bytes;
+    static constexpr size_t off_tab = off_idx + idx_bytes;
+    static constexpr size_t off_lam = off_tab + tab_bytes;
+    static constexpr size_t off_red = off_lam + lam_bytes;
+    static constexpr size_t bytes = off_red + red_bytes;
+    static_assert(bytes <= total, "D = 256 shared-memory layout");
+    static_assert(sizeof(float2) * kBigRB * kBigD <= tri_bytes, "V batch");
+    static_assert(sizeof(float2) * 2 * kBigT * (kBigT + 1) <= tri_bytes, "rho tiles");
+};
+
+// scratch slot (complex64 units): theta overflow | V (W after scaling) | rho | rotation log
+constexpr int64_t kBigTriG = ((int64_t)(kBigTri - BigSmem::ns32) + 1) / 2 * 2;
+constexpr int64_t kBigOffV = kBigTriG;
+constexpr int64_t kBigOffR = kBigOffV + (int64_t)kBigD * kBigD;
+constexpr int64_t kBigOffLog = kBigOffR + (int64_t)kBigD * kBigD;
+static_assert(2 * (int64_t)(kBigTri - BigSmem::ns64) <= kBigOffLog, "FP64 overflow fits the slot");
+
+__device__ __forceinline__ void rot_pair(float2& p, float2& q, const RotC<float>& R) {
+    const float npr = R.c * p.x + (R.wr * q.x + R.wi * q.y);
+    const float npi = R.c * p.y + (R.wr * q.y - R.wi * q.x);
+    const float nqr = R.c * q.x - (R.wr * p.x - R.wi * p.y);
+    const float nqi = R.c * q.y - (R.wr * p.y + R.wi * p.x);
+    p = make_float2(npr, npi);
+    q = make_float2(nqr, nqi);
+}
+
+__global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevProblem P, const PassIO io,
+                                                                     const int32_t* __restrict__ cls,
+                                                                     const int32_t count, const int k) {
+    using S = BigSmem;
+    constexpr int D = kBigD, n = kBigN, NT = 1024;
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2* tri_s = reinterpret_cast<float2*>(sm);
+    RotC<float>* prm = reinterpret_cast<RotC<float>*>(sm + S::off_prm);
+    int* idx0 = reinterpret_cast<int*>(sm + S::off_idx);
+    int* idx1 = idx0 + D;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(sm + S::off_tab);
+    float* lam = reinterpret_cast<float*>(sm + S::off_lam);
+    float* pw = lam + D;
+    float* red = reinterpret_cast<float*>(sm + S::off_red);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    float2* slot = P.big + (int64_t)blockIdx.x * P.big_slot;
+    float2* Wg = slot + kBigOffV;
+    float2* Rg = slot + kBigOffR;
+    RotC<float>* logp = reinterpret_cast<RotC<float>*>(slot + kBigOffLog);
+    const bool nest = P.st->variant == 1;
+    const dev::Thetas Th = dev::pass_thetas(P, io);
+    if (io.writer && blockIdx.x == 0 && t == 0) dev::advance_theta(P, io);
+    build_table<D, float>(tab);
+    const int max_sw = min(P.st->max_sweeps, P.big_log_sweeps);
+    const int total = P.n_inst * count;
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int inst = b / count;
+        const int r = cls[b % count];
+        const RegionInfo R = P.reg[r];
+        Split<float> A{tri_s, slot, S::ns32, D};
+        __syncthreads();   // the previous region's reads of shared memory and of the slot are done
+        if (t < D) idx0[t] = t;
+        assemble_packed_io<D>(P, R, inst, A, io, Th);
+        __syncthreads();
+        float vr[D / 4], vi[D / 4];   // not used: V comes from the log
+        float norm2, off2;
+        const int sweeps = jacobi_cta<D, float, false, Split<float>, true>(A, prm, idx0, idx1, tab, red, vr, vi, max_sw,
+                                                                         1e-12f, norm2, off2, logp);
+        if (t < D) lam[t] = A.dget(t).x;   // positions: theta's diagonal holds the eigenvalues
+        __syncthreads();
+        float lmin = lam[0];
+        for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
+        float F, Z = 0.f;
+        if (nest) {
+            const float beta = (float)P.st->beta;
+            for (int i = 0; i < D; ++i) Z += expf(-beta * (lam[i] - lmin));
+            F = lmin - logf(Z) / beta;
+            if (t < D) pw[t] = sqrtf(expf(-beta * (lam[t] - lmin)) / Z);
+        } else {
+            const float tau = (float)P.st->degen_tol * fmaxf(1.0f, sqrtf(norm2));
+            for (int i = 0; i < D; ++i) Z += (lam[i] - lmin <= tau) ? 1.f : 0.f;
+            F = lmin;
+            if (t < D) pw[t] = (lam[t] - lmin <= tau) ? sqrtf(1.0f / Z) : 0.f;
+        }
+        __syncthreads();
+        // V from the log, kBigRB rows at a time (theta's shared part is free now); W = V diag(sqrt p)
+        const int nrounds = sweeps * (D - 1);
+        float2* Vs = tri_s;
+        for (int row0 = 0; row0 < D; row0 += kBigRB) {
+            for (int e = t; e < kBigRB * D; e += NT) Vs[e] = make_float2((row0 + e / D == e % D) ? 1.f : 0.f, 0.f);
+            __syncthreads();
+            float2* v0 = Vs + (2 * warp) * D;
+            float2* v1 = v0 + D;
+            for (int rd = 0; rd < nrounds; ++rd) {
+                const RotC<float>* lg = logp + (size_t)rd * n;
+#pragma unroll
+                for (int m = 0; m < n / 32; ++m) {
+                    const RotC<float> Rk = lg[lane + 32 * m];
+                    const int pq = __float_as_int(Rk.pad);
+                    const int p = pq & 0xffff, q = pq >> 16;
+                    rot_pair(v0[p], v0[q], Rk);
+                    rot_pair(v1[p], v1[q], Rk);
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int e = t; e < kBigRB * D; e += NT) {
+                const float2 v = Vs[e];
+                const float q = pw[e % D];
+                Wg[(int64_t)row0 * D + e] = make_float2(v.x * q, v.y * q);
+            }
+            __syncthreads();
+        }
+        // rho = W W^dagger, upper tiles (ti <= tj) of kBigT x kBigT: rho[i][j] = sum_c W[i][c] conj(W[j][c]);
+        // thread (ty, tx) = (warp, lane) owns rows 2 ty, 2 ty + 1 and columns tx, tx + 32 of the tile
+        {
+            constexpr int T = kBigT, LD = T + 1;
+            float2* Wa = tri_s;            // [T][LD]: rows of the tile's row block, c in the chunk
+            float2* Wb = tri_s + T * LD;   // [T][LD]: transposed, Wb[c][j]
+            for (int ti = 0; ti < D / T; ++ti)
+                for (int tj = ti; tj < D / T; ++tj) {
+                    float2 acc[2][2];
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb) acc[a][bb] = make_float2(0.f, 0.f);
+                    for (int c0 = 0; c0 < D; c0 += T) {
+                        for (int e = t; e < T * T; e += NT) {
+                            const int i = e / T, c = e % T;
+                            Wa[i * LD + c] = Wg[(int64_t)(ti * T + i) * D + c0 + c];
+                            Wb[c * LD + i] = Wg[(int64_t)(tj * T + i) * D + c0 + c];
+                        }
+                        __syncthreads();
+                        for (int c = 0; c < T; ++c) {
+                            const float2 a0 = Wa[(2 * warp) * LD + c], a1 = Wa[(2 * warp + 1) * LD + c];
+                            const float2 b0 = Wb[c * LD + lane], b1 = Wb[c * LD + lane + 32];
+                            const float2 av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int bb = 0; bb < 2; ++bb) {
+                                    acc[a][bb].x += av[a].x * bv[bb].x + av[a].y * bv[bb].y;
+                                    acc[a][bb].y += av[a].y * bv[bb].x - av[a].x * bv[bb].y;
+                                }
+                        }
+                        __syncthreads();
+                    }
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 2; ++bb)
+                            Rg[(int64_t)(ti * T + 2 * warp + a) * D + tj * T + lane + 32 * bb] = acc[a][bb];
+                }
+        }
+        __syncthreads();
+        // exact Hermitian symmetry: lower triangle := conj(upper), real diagonal
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            if (i > j) { const float2 u = Rg[j * D + i]; Rg[e] = make_float2(u.x, -u.y); }
+            else if (i == j) Rg[e].y = 0.f;
+        }
+        __syncthreads();
+        if (R.rho_off >= 0) {
+            float2* dst = io.rho_out + (int64_t)inst * P.rho_elems + R.rho_off;
+            for (int e = t; e < D * D; e += NT) dst[e] = Rg[e];
+        }
+        float2* trb = io.tr_out + (int64_t)inst * P.msg_elems;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
+            for (int o = t; o < Df * Df; o += NT) {
+                const int ra = pdep8(o >> kf, M), rbb = pdep8(o & (Df - 1), M);
+                float sr = 0.f, si = 0.f;
+                for (int c = 0; c < nrest; ++c) {
+                    const int x = pdep8(c, Mc);
+                    const float2 v = Rg[(ra | x) * D + (rbb | x)];
+                    sr += v.x; si += v.y;
+                }
+                trb[pi.off + o] = make_float2(sr, si);
+            }
+        }
+        if (t == 0) {
+            P.val[(int64_t)inst * P.n_regions + r] = (double)F;
+            if (!isfinite(F)) atomicOr(P.err, DEV_ERR_NUMERIC);
+            atomicAdd(&P.sweeps[k], (unsigned long long)sweeps);
+            if (off2 > 1e-12f * norm2) atomicAdd(&P.capped[k], 1ull);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) certify_cta256_kernel(const DevProblem P, const int32_t* __restrict__ cls,
+                                                                 const int32_t count, const float2* __restrict__ msg) {
+    using S = BigSmem;
+    constexpr int D = kBigD;
+    extern __shared__ __align__(16) unsigned char sm[];
+    double2* tri_s = reinterpret_cast<double2*>(sm);
+    RotC<double>* prm = reinterpret_cast<RotC<double>*>(sm + S::off_prm);
+    int* idx0 = reinterpret_cast<int*>(sm + S::off_idx);
+    int* idx1 = idx0 + D;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(sm + S::off_tab);
+    double* red = reinterpret_cast<double*>(sm + S::off_red);
+    const int t = threadIdx.x;
+    double2* slot = reinterpret_cast<double2*>(P.big + (int64_t)blockIdx.x * P.big_slot);
+    build_table<D, double>(tab);
+    const int total = P.n_inst * count;
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int inst = b / count;
+        const int r = cls[b % count];
+        const RegionInfo R = P.reg[r];
+        Split<double> A{tri_s, slot, S::ns64, D};
+        __syncthreads();
+        if (t < D) idx0[t] = t;
+        assemble_packed<D, double>(P, R, inst, A, msg, nullptr, 0.0f, true);
+        __syncthreads();
+        double vr[D / 4], vi[D / 4];
+        double norm2, off2;
+        jacobi_cta<D, double, false>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->cert_sweeps, 1e-28, norm2, off2);
+        double lmin = A.dget(0).x;
+        for (int i = 1; i < D; ++i) lmin = fmin(lmin, A.dget(i).x);
+        lmin -= sqrt(off2);   // Weyl: a lower bound on lambda_min also when the sweep cap stopped it
+        if (t == 0) {
+            P.val64[(int64_t)inst * P.n_regions + r] = lmin;
+            if (!isfinite(lmin)) atomicOr(P.err, DEV_ERR_NUMERIC);
+            if (off2 > 1e-28 * norm2) atomicOr(P.err, DEV_ERR_NOCONV);
+        }
+    }
+}
+
+cudaError_t pass_cta256(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k, cudaStream_t s) {
+    if (!P.big || P.big_slots <= 0) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((int64_t)P.n_inst * count, P.big_slots);
+    region_pass_cta256_kernel<<<(unsigned)blocks, 1024, BigSmem::bytes, s>>>(P, io, cls, count, k);
+    return cudaGetLastError();
+}
+
+cudaError_t cert_cta256(const DevProblem& P, const int32_t* cls, int32_t count, const float2* msg, cudaStream_t s) {
+    if (!P.big || P.big_slots <= 0) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((int64_t)P.n_inst * count, P.big_slots);
+    certify_cta256_kernel<<<(unsigned)blocks, 1024, BigSmem::bytes, s>>>(P, cls, count, msg);
+    return cudaGetLastError();
+}
+
 template <int D>
 cudaError_t pass_cta(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k, cudaStream_t s) {
     const int64_t blocks = (int64_t)P.n_inst * count;
@@ -862,6 +1176,10 @@ cudaError_t prepare_cta_kernels() {
                                   (int)CtaSmem<64, float>::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(region_pass_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CtaSmem<128, float>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(region_pass_cta256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)BigSmem::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(certify_cta256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)BigSmem::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(certify_cta_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CtaSmem<64, double>::bytes)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(certify_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -873,6 +1191,7 @@ cudaError_t launch_region_pass_cta(const DevProblem& P, const PassIO& io, int k,
     if (count <= 0) return cudaSuccess;
     if (k == 6) return pass_cta<64>(P, io, cls, count, k, s);
     if (k == 7) return pass_cta<128>(P, io, cls, count, k, s);
+    if (k == 8) return pass_cta256(P, io, cls, count, k, s);
     return cudaErrorInvalidValue;
 }
 
@@ -881,7 +1200,23 @@ cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* cls, i
     if (count <= 0) return cudaSuccess;
     if (k == 6) return cert_cta<64>(P, cls, count, msg, s);
     if (k == 7) return cert_cta<128>(P, cls, count, msg, s);
+    if (k == 8) return cert_cta256(P, cls, count, msg, s);
     return cudaErrorInvalidValue;
+}
+
+int64_t big_slot_elems(int log_sweeps) {
+    return kBigOffLog + 2 * (int64_t)log_sweeps * (kBigD - 1) * kBigN;   // a RotC<float> is two complex64
+}
+
+cudaError_t big_launch_slots(int* slots) {
+    int dev = 0, sms = 0, occ_p = 0, occ_c = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_p, region_pass_cta256_kernel, 1024, BigSmem::bytes)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, certify_cta256_kernel, 1024, BigSmem::bytes)) != cudaSuccess) return e;
+    *slots = sms * std::max(1, std::max(occ_p, occ_c));
+    return cudaSuccess;
 }
 
 }  // namespace lrh

@@ -183,16 +183,23 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
     n2 = group_sum<D>(n2);
     norm2 = n2;
     const T thresh = tol2 * n2;
+    // Each group (region) stops at its own test; while other groups of the warp still sweep, a
+    // stopped group runs identity rotations (c = 1, w = 0: every value is kept exactly and only
+    // the tournament permutation moves it, which whole sweeps undo), so a region's result does
+    // not depend on the regions that share its warp.
     int sweeps = 0;
+    bool active = true;
     for (;;) {
         T off = T(0);
 #pragma unroll
         for (int c = 0; c < D; ++c) off += (c == s) ? T(0) : (ar[c] * ar[c] + ai[c] * ai[c]);
         off = group_sum<D>(off);
-        off2 = off;
-        const bool done = (off <= thresh) || (sweeps >= max_sweeps);
-        if (__all_sync(kFull, done)) break;
-        ++sweeps;
+        if (active) {
+            off2 = off;
+            active = !((off <= thresh) || (sweeps >= max_sweeps));
+        }
+        if (!__any_sync(kFull, active)) break;
+        if (active) ++sweeps;
         // One round of the tournament: pair parameters from (xr, xi), column rotations of
         // (xr, xi) and of V (ur, ui) in place, the row rotation with the tournament permutation
         // into (yr, yi) and V's column permutation into (wr_, wi_).  Rounds alternate between
@@ -214,6 +221,7 @@ __device__ __forceinline__ int jacobi_lanes(T (&ar)[D], T (&ai)[D], T (&vr)[D], 
             const T aqq = odd ? mydiag : pdiag;
             T c, wr, wi;
             rot_params(app, aqq, br, bi, c, wr, wi);
+            if (!active) { c = T(1); wr = T(0); wi = T(0); }
             if (!odd) prm[s >> 1] = Rot<T>{c, wr, wi, T(0)};
             __syncwarp();
             // (2) column rotations of A and V (all pairs)

@@ -144,6 +144,12 @@ struct DevProblem {
     float2* thb;           // [n_inst][all_elems] theta_bar of every region
     float2* gbar;          // [n_inst][msg_elems] cotangent of the gradient output
     double* qbar;          // [n_inst] cotangent of Q_beta
+    // regions of 8 sites (D = 256): one global scratch slot per CTA of their launch (theta
+    // entries beyond shared memory, V, rho and the rotation log), allocated at creation
+    float2* big;
+    int64_t big_slot;        // complex entries per slot
+    int32_t big_slots;       // slots (= CTAs of a D = 256 launch)
+    int32_t big_log_sweeps;  // sweeps the rotation log of a slot holds (the D = 256 sweep cap)
 };
 
 // Record `msg` as the thread-local detail returned by lrh_last_error; returns `code`.
@@ -152,7 +158,11 @@ int set_last_error(int code, const std::string& msg);
 // Kernel attributes (dynamic shared memory limits) for the current device; called once per
 // problem creation, outside any stream capture.
 cudaError_t prepare_kernels();
-cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128)
+cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128, 256)
+// Global scratch of the D = 256 pass and certification: complex entries per CTA slot for a
+// rotation log of `log_sweeps` sweeps, and the CTAs a launch uses on this device.
+int64_t big_slot_elems(int log_sweeps);
+cudaError_t big_launch_slots(int* slots);
 cudaError_t prepare_blk_kernels();   // lrh_block.cu (D = 8, 16, 2x2-block layout)
 // D = 8, 16 in the Hermitian 2x2-block layout, `threads` per CTA (64, 128 or 256)
 cudaError_t launch_region_pass_blk(const DevProblem& P, const PassIO& io, int k, const int32_t* class_regions,

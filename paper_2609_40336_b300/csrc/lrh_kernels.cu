@@ -958,7 +958,8 @@ cudaError_t launch_region_pass(const DevProblem& P, const PassIO& io, int k, con
         case 4: return launch_pass_D<16>(P, io, cls, count, k, s, block);
         case 5: return launch_pass_D<32>(P, io, cls, count, k, s, block);
         case 6:
-        case 7: return launch_region_pass_cta(P, io, k, cls, count, s);
+        case 7:
+        case 8: return launch_region_pass_cta(P, io, k, cls, count, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -977,7 +978,8 @@ cudaError_t launch_certify(const DevProblem& P, int k, const int32_t* cls, int32
         case 4: return launch_cert_D<16>(P, cls, count, msg, s);
         case 5: return launch_cert_D<32>(P, cls, count, msg, s);
         case 6:
-        case 7: return launch_certify_cta(P, k, cls, count, msg, s);
+        case 7:
+        case 8: return launch_certify_cta(P, k, cls, count, msg, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -59,8 +59,8 @@ def _code(p):
     return ei.value.code
 
 
-def test_region_beyond_seven_sites_is_rejected():
-    p = g.Problem(8, [tuple(range(8))], [(0, 1)], [g.lattices.ZZ[None]])
+def test_region_beyond_eight_sites_is_rejected():
+    p = g.Problem(9, [tuple(range(9))], [(0, 1)], [g.lattices.ZZ[None]])
     assert _code(p) == -1
 
 
