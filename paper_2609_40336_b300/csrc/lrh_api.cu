@@ -98,6 +98,8 @@ struct lrh_problem {
     int64_t all_elems = 0;
     float2* vjp_nubar = nullptr;    // adjoint outputs staged on the device
     float2* vjp_termbar = nullptr;
+    float2* vjp_scratch = nullptr;  // CTA adjoint (6-7 sites): one slot of 2 D^2 complex per CTA
+    int vjp_slots = 0;
     // region classes after the first run on forked streams (joined before the update)
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> ev_join;
@@ -837,7 +839,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     }
     if ((rc = p->dalloc(&P.val, NI * R)) || (rc = p->dalloc(&P.val64, NI * R)) || (rc = p->dalloc(&P.q_sum, NI)) ||
         (rc = p->dalloc(&P.q_best, NI)) || (rc = p->dalloc(&P.best_flag, NI)) || (rc = p->dalloc(&P.st, 1)) ||
-        (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, 8)) || (rc = p->dalloc(&P.capped, 8)))
+        (rc = p->dalloc(&P.err, 1)) || (rc = p->dalloc(&P.sweeps, kClassSlots)) || (rc = p->dalloc(&P.capped, kClassSlots)))
         return rc;
     P.reg = dreg; P.pair = dpair; P.child_pairs = dcp; P.parent_pairs = dpp; P.h32 = h32; P.h64 = dh64;
     P.all_elems = p->all_elems;
@@ -856,8 +858,8 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     LRH_CK(cudaMemset(P.grad, 0, sizeof(float2) * std::max<int64_t>(NI * moff, 1)));
     LRH_CK(cudaMemset(P.best_flag, 0, sizeof(int32_t) * NI));
     LRH_CK(cudaMemset(P.err, 0, sizeof(int32_t)));
-    LRH_CK(cudaMemset(P.sweeps, 0, sizeof(unsigned long long) * 8));
-    LRH_CK(cudaMemset(P.capped, 0, sizeof(unsigned long long) * 8));
+    LRH_CK(cudaMemset(P.sweeps, 0, sizeof(unsigned long long) * kClassSlots));
+    LRH_CK(cudaMemset(P.capped, 0, sizeof(unsigned long long) * kClassSlots));
     LRH_CK(cudaMemset(P.val64, 0, sizeof(double) * NI * R));
     LRH_CK(cudaMemset(P.val, 0, sizeof(double) * NI * R));
     LRH_CK(cudaMemset(P.st, 0, sizeof(IterState)));
@@ -866,7 +868,7 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         LRH_CK(cudaMemcpy(P.q_best, ninf.data(), sizeof(double) * NI, cudaMemcpyHostToDevice));
     }
     // size classes
-    for (int k = 0; k < 8; ++k) P.class_base[k] = -1;
+    for (int k = 0; k < kClassSlots; ++k) P.class_base[k] = -1;
     P.class_uniform = 0;
     for (int k = 1; k <= kMaxSites; ++k) {
         std::vector<int32_t> lst;
@@ -962,7 +964,7 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
     info->gamma_G = p->gamma_G;
     info->iteration = p->iteration;
     info->n_classes = (int32_t)p->class_k.size();
-    unsigned long long sw[8] = {0}, cap[8] = {0};
+    unsigned long long sw[kClassSlots] = {0}, cap[kClassSlots] = {0};
     LRH_CK(cudaMemcpyAsync(sw, p->P.sweeps, sizeof(sw), cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaMemcpyAsync(cap, p->P.capped, sizeof(cap), cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
@@ -1156,7 +1158,7 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
     if (!p || !q_bar) return fail(LRH_EINVAL, "NULL argument");
     if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     if (p->opt.variant != LRH_NESTEROV) return fail(LRH_EINVAL, "lrh_vjp differentiates the smoothed objective (LRH_NESTEROV)");
-    if (p->max_k > 5) return fail(LRH_EUNSUPPORTED, "the adjoint kernels handle regions of at most 5 sites");
+    if (p->max_k > 7) return fail(LRH_EUNSUPPORTED, "the adjoint kernels handle regions of at most 7 sites");
     DeviceGuard dg(p->device);
     const int64_t NI = p->n_inst;
     DevProblem& P = p->P;
@@ -1186,8 +1188,25 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
         if (g_bar) LRH_CK(cudaMemcpyAsync(P.gbar, g_bar, mbytes, g_bar_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream));
         else LRH_CK(cudaMemsetAsync(P.gbar, 0, mbytes, p->stream));
     }
-    for (size_t c = 0; c < p->class_k.size(); ++c)
-        LRH_CK(launch_vjp_region(P, p->class_k[c], p->class_list[c], p->class_count[c], p->stream));
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
+        const int k = p->class_k[c];
+        if (k >= 6) {
+            if (!p->vjp_scratch) {   // scratch slots of the CTA adjoint: 2 D^2 complex per CTA of the launch
+                int slots = 0;
+                LRH_CK(vjp_cta_slots(p->max_k >= 7 ? 7 : 6, &slots));
+                const int64_t D = (int64_t)1 << std::min(p->max_k, 7);
+                int rc;
+                if ((rc = p->dalloc(&p->vjp_scratch, (int64_t)slots * 2 * D * D))) return rc;
+                p->vjp_slots = slots;
+            }
+            int slots = 0;
+            LRH_CK(vjp_cta_slots(k, &slots));
+            LRH_CK(launch_vjp_cta(P, k, p->class_list[c], p->class_count[c], p->vjp_scratch, std::min(slots, p->vjp_slots),
+                                  p->stream));
+        } else {
+            LRH_CK(launch_vjp_region(P, k, p->class_list[c], p->class_count[c], p->stream));
+        }
+    }
     LRH_CK(launch_vjp_outputs(P, p->vjp_nubar, p->vjp_termbar, p->stream));
     const cudaMemcpyKind kind = out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (nu_bar && mbytes) LRH_CK(cudaMemcpyAsync(nu_bar, p->vjp_nubar, mbytes, kind, p->stream));

@@ -31,6 +31,7 @@ namespace {
 using dev::RotC;
 using dev::rot_params_d;
 using dev::two_sided;
+using dev::kdd;
 constexpr unsigned kFull = 0xffffffffu;
 
 __host__ __device__ constexpr int rr_src_c(int s, int D) {
@@ -396,7 +397,7 @@ __device__ void assemble_packed(const DevProblem& P, const RegionInfo& R, int in
         }
         if (i == j) im = T(0);
         typename V2<T>::t v; v.x = re; v.y = im;
-        A.set(i, j, v);
+        A.set(A.sig(i), A.sig(j), v);
     }
 }
 
@@ -1154,6 +1155,171 @@ cudaError_t cert_cta256(const DevProblem& P, const int32_t* cls, int32_t count, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Adjoint of the smoothed pass for D = 64 and 128 (see lrh_vjp.cu for the formulas): the
+// eigenbasis is recomputed by the CTA Jacobi at the same point eta, then
+//   Y = rho_bar V,  M = V^dagger Y,  X = M o K + (beta <rho_bar, rho> + q_bar) diag(p),
+//   Z = V X,  theta_bar = Z V^dagger,
+// four complex D x D products in TR x TC register tiles.  One D x D operand lives in shared
+// memory (rho_bar, then M / X, then theta_bar) and V, Y / Z in the CTA's global scratch slot
+// (2 D^2 complex, L2-resident while the CTA runs).  CTAs loop over the regions of the launch.
+template <int D, typename FA, typename FB, typename FS>
+__device__ __forceinline__ void cmm_tile(FA A, FB B, FS store) {
+    constexpr int NT = CtaCfg<D>::NT, TR = CtaCfg<D>::TR, TC = CtaCfg<D>::TC, CS = D / TC;
+    const int t = threadIdx.x;
+    const int i0 = (t / CS) * TR, cb = t % CS;
+    static_assert((D / TR) * CS == NT, "tile cover");
+    float accr[TR][TC], acci[TR][TC];
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) { accr[a][b] = 0.f; acci[a][b] = 0.f; }
+    for (int k = 0; k < D; ++k) {
+        float2 av[TR], bv[TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a) av[a] = A(i0 + a, k);
+#pragma unroll
+        for (int b = 0; b < TC; ++b) bv[b] = B(k, cb + CS * b);
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) {
+                accr[a][b] += av[a].x * bv[b].x - av[a].y * bv[b].y;
+                acci[a][b] += av[a].x * bv[b].y + av[a].y * bv[b].x;
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) store(i0 + a, cb + CS * b, make_float2(accr[a][b], acci[a][b]));
+}
+
+template <int D>
+__global__ void __launch_bounds__(CtaCfg<D>::NT) vjp_cta_kernel(const DevProblem P, const int32_t* __restrict__ cls,
+                                                                const int32_t count, float2* __restrict__ scratch) {
+    using S = CtaSmem<D, float>;
+    constexpr int NT = CtaCfg<D>::NT;
+    constexpr int W = D / 4;
+    constexpr int LD = D + 1;
+    extern __shared__ __align__(16) unsigned char sm[];
+    float2* buf = reinterpret_cast<float2*>(sm);
+    RotC<float>* prm = reinterpret_cast<RotC<float>*>(sm + S::off_prm);
+    int* idx0 = reinterpret_cast<int*>(sm + S::off_idx);
+    int* idx1 = idx0 + D;
+    unsigned short* tab = reinterpret_cast<unsigned short*>(sm + S::off_tab);
+    float* lam = reinterpret_cast<float*>(sm + S::off_lam);
+    float* pp = lam + D;
+    float* red = reinterpret_cast<float*>(sm + S::off_red);
+    const int t = threadIdx.x;
+    float2* Vg = scratch + (int64_t)blockIdx.x * 2 * D * D;
+    float2* Yg = Vg + D * D;
+    const float th = (float)P.st->th3[P.st->t0 % 3];
+    const float beta = (float)P.st->beta;
+    build_table<D, float>(tab);
+    const int total = P.n_inst * count;
+    for (int b = blockIdx.x; b < total; b += gridDim.x) {
+        const int inst = b / count;
+        const int r = cls[b % count];
+        const RegionInfo R = P.reg[r];
+        Full<float> A{buf, D};
+        __syncthreads();
+        if (t < D) idx0[t] = A.sig(t);
+        assemble_packed<D, float>(P, R, inst, A, P.nu, P.zeta, th, false);
+        __syncthreads();
+        const int row = vrow_of(t), chunk = vchunk_of(t);
+        float vr[W], vi[W];
+#pragma unroll
+        for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
+        float norm2, off2;
+        jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2, off2);
+        if (t < D) lam[t] = A.dget(A.sig(t)).x;
+        __syncthreads();
+        float lmin = lam[0];
+        for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
+        float Z = 0.f;
+        for (int i = 0; i < D; ++i) Z += expf(-beta * (lam[i] - lmin));
+        if (t < D) pp[t] = expf(-beta * (lam[t] - lmin)) / Z;
+#pragma unroll
+        for (int m = 0; m < W; ++m) Vg[row * D + chunk * W + m] = make_float2(vr[m], vi[m]);
+        __syncthreads();
+        // rho_bar (general D x D): the gather of theta with h = 0 applied to g_bar
+        const int64_t mbase = (int64_t)inst * P.msg_elems;
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            float re = 0.f, im = 0.f;
+            for (int q = R.child_begin; q < R.child_end; ++q) {
+                const PairInfo pi = P.child_info[q];
+                if (((i ^ j) & ~pi.mask) != 0) continue;
+                const int Df = 1 << pi.kf;
+                const float2 m = P.gbar[mbase + pi.off + (int64_t)pext8(i, pi.mask) * Df + pext8(j, pi.mask)];
+                re -= m.x; im -= m.y;
+            }
+            for (int q = R.parent_begin; q < R.parent_end; ++q) {
+                const float2 m = P.gbar[mbase + P.parent_info[q].off + e];
+                re += m.x; im += m.y;
+            }
+            buf[i * LD + j] = make_float2(re, im);
+        }
+        __syncthreads();
+        // (1) Y = rho_bar V
+        cmm_tile<D>([&](int i, int k) { return buf[i * LD + k]; }, [&](int k, int j) { return Vg[k * D + j]; },
+                    [&](int i, int j, float2 v) { Yg[i * D + j] = v; });
+        __syncthreads();
+        // (2) M = V^dagger Y (into shared memory; rho_bar is no longer needed)
+        cmm_tile<D>([&](int i, int k) { const float2 v = Vg[k * D + i]; return make_float2(v.x, -v.y); },
+                    [&](int k, int j) { return Yg[k * D + j]; }, [&](int i, int j, float2 v) { buf[i * LD + j] = v; });
+        __syncthreads();
+        // <rho_bar, rho> = sum_k p_k Re M_kk;  X = M o K + (beta <rho_bar, rho> + q_bar) diag(p)
+        float part = 0.f;
+        for (int k = t; k < D; k += NT) part += pp[k] * buf[k * LD + k].x;
+        const float inner = block_sum<NT>(part, red);
+        const float coef = beta * inner + (float)P.qbar[inst];
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            const float kv = kdd(lam[i], lam[j], pp[i], pp[j], beta);
+            float2 x = buf[i * LD + j];
+            x.x *= kv; x.y *= kv;
+            if (i == j) x.x += coef * pp[i];
+            buf[i * LD + j] = x;
+        }
+        __syncthreads();
+        // (3) Z = V X (into the slot; Y is no longer needed)
+        cmm_tile<D>([&](int i, int k) { return Vg[i * D + k]; }, [&](int k, int j) { return buf[k * LD + j]; },
+                    [&](int i, int j, float2 v) { Yg[i * D + j] = v; });
+        __syncthreads();
+        // (4) theta_bar = Z V^dagger
+        cmm_tile<D>([&](int i, int k) { return Yg[i * D + k]; },
+                    [&](int k, int j) { const float2 v = Vg[j * D + k]; return make_float2(v.x, -v.y); },
+                    [&](int i, int j, float2 v) { buf[i * LD + j] = v; });
+        __syncthreads();
+        // exactly Hermitian (upper triangle as computed), out to theta_bar and onto the children
+        float2* dst = P.thb + (int64_t)inst * P.all_elems + R.all_off;
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            float2 v = i <= j ? buf[i * LD + j] : buf[j * LD + i];
+            if (i > j) v.y = -v.y;
+            if (i == j) v.y = 0.f;
+            dst[e] = v;
+        }
+        __syncthreads();
+        float2* trb = P.tr + (int64_t)inst * P.msg_elems;
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask, Mc = (D - 1) & ~M, kf = pi.kf, Df = 1 << kf, nrest = D >> kf;
+            for (int o = t; o < Df * Df; o += NT) {
+                const int ra = pdep8(o >> kf, M), rbb = pdep8(o & (Df - 1), M);
+                float sr = 0.f, si = 0.f;
+                for (int c = 0; c < nrest; ++c) {
+                    const int x = pdep8(c, Mc);
+                    const float2 v = dst[(ra | x) * D + (rbb | x)];
+                    sr += v.x; si += v.y;
+                }
+                trb[pi.off + o] = make_float2(sr, si);
+            }
+        }
+    }
+}
+
 template <int D>
 cudaError_t pass_cta(const DevProblem& P, const PassIO& io, const int32_t* cls, int32_t count, int k, cudaStream_t s) {
     const int64_t blocks = (int64_t)P.n_inst * count;
@@ -1175,6 +1341,10 @@ cudaError_t prepare_cta_kernels() {
     if ((e = cudaFuncSetAttribute(region_pass_cta_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CtaSmem<64, float>::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(region_pass_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CtaSmem<128, float>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(vjp_cta_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CtaSmem<64, float>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(vjp_cta_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CtaSmem<128, float>::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(region_pass_cta256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)BigSmem::bytes)) != cudaSuccess) return e;
@@ -1202,6 +1372,28 @@ cudaError_t launch_certify_cta(const DevProblem& P, int k, const int32_t* cls, i
     if (k == 7) return cert_cta<128>(P, cls, count, msg, s);
     if (k == 8) return cert_cta256(P, cls, count, msg, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t vjp_cta_slots(int k, int* slots) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (k == 6) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vjp_cta_kernel<64>, CtaCfg<64>::NT, CtaSmem<64, float>::bytes);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vjp_cta_kernel<128>, CtaCfg<128>::NT, CtaSmem<128, float>::bytes);
+    if (e != cudaSuccess) return e;
+    *slots = sms * std::max(1, occ);
+    return cudaSuccess;
+}
+
+cudaError_t launch_vjp_cta(const DevProblem& P, int k, const int32_t* cls, int32_t count, float2* scratch, int slots,
+                           cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((int64_t)P.n_inst * count, slots);
+    if (k == 6) vjp_cta_kernel<64><<<(unsigned)blocks, CtaCfg<64>::NT, CtaSmem<64, float>::bytes, s>>>(P, cls, count, scratch);
+    else if (k == 7) vjp_cta_kernel<128><<<(unsigned)blocks, CtaCfg<128>::NT, CtaSmem<128, float>::bytes, s>>>(P, cls, count, scratch);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 int64_t big_slot_elems(int log_sweeps) {

@@ -21,7 +21,7 @@ __host__ __device__ constexpr int rr_src(int s, int D) {
 __device__ __forceinline__ int pext_bits(int x, int m) {
     int r = 0, k = 0;
 #pragma unroll
-    for (int b = 0; b < 7; ++b) {
+    for (int b = 0; b < 8; ++b) {
         if ((m >> b) & 1) { r |= ((x >> b) & 1) << k; ++k; }
     }
     return r;
@@ -30,7 +30,7 @@ __device__ __forceinline__ int pext_bits(int x, int m) {
 __device__ __forceinline__ int pdep_bits(int x, int m) {
     int r = 0, k = 0;
 #pragma unroll
-    for (int b = 0; b < 7; ++b) {
+    for (int b = 0; b < 8; ++b) {
         if ((m >> b) & 1) { r |= ((x >> k) & 1) << b; ++k; }
     }
     return r;
@@ -332,6 +332,17 @@ __device__ __forceinline__ void assemble_row(const DevProblem& P, const RegionIn
             ar[2 * c] += T(m.x); ai[2 * c] += T(m.y); ar[2 * c + 1] += T(m.z); ai[2 * c + 1] += T(m.w);
         }
     }
+}
+
+// K_kl of the eigendecomposition's adjoint for lambda_k, lambda_l with Gibbs weights p_k, p_l:
+// the divided difference (p_k - p_l) / (lambda_k - lambda_l) of the normalised e^{-beta x},
+// evaluated stably as p_lo expm1(-beta |d|) / |d| (p_lo = weight of the smaller eigenvalue),
+// with the limit -beta p at coinciding eigenvalues.
+__device__ __forceinline__ float kdd(float lk, float ll, float pk, float pl, float beta) {
+    const float d = fabsf(lk - ll);
+    const float plo = lk <= ll ? pk : pl;
+    if (d * beta < 1e-6f) return -beta * plo;
+    return plo * expm1f(-beta * d) / d;
 }
 
 // ------------------------------------------------------------------ fused Alg. 2 passes

@@ -91,6 +91,9 @@ __host__ __device__ inline RegionInfo uniform_region(const RegionInfo& f, int64_
 // lower bound: the Weyl correction below covers the remaining off-diagonal part).
 enum : int32_t { DEV_ERR_NUMERIC = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_NOCONV = 4 };
 
+// Arrays indexed by a region's site count k (0 .. 8, regions of up to 8 sites).
+constexpr int kClassSlots = 9;
+
 struct DevProblem {
     int32_t n_inst;
     int32_t n_regions;
@@ -107,12 +110,12 @@ struct DevProblem {
     const int64_t* chunk_rho;    // [msg_elems / 4] child-state offset minus message offset of that pair
     const PairInfo* child_info;  // PairInfo in child CSR order (child_pairs[q] resolved)
     const PairInfo* parent_info; // PairInfo in parent CSR order
-    int32_t class_base[8];       // [k]: first region id when the class of k sites is a contiguous id range, else -1
+    int32_t class_base[kClassSlots];   // [k]: first region id when the class of k sites is a contiguous id range, else -1
     // [k]: record of the class's first region when every region r = class_base[k] + i of the class
     // has the record of the first shifted by i (child / parent ranges by their lengths, term and
     // state offsets by D^2 where present); lets the small-region passes build the record without
     // a dependent load.  class_uniform bit k marks such classes.
-    RegionInfo class_first[8];
+    RegionInfo class_first[kClassSlots];
     int32_t class_uniform;
     const float2* h32;     // [n_inst][h_elems]
     const double2* h64;    // [n_inst][h_elems]
@@ -133,8 +136,8 @@ struct DevProblem {
     int32_t* best_flag;    // [n_inst]
     IterState* st;
     int32_t* err;
-    unsigned long long* sweeps;   // [8] per size class (indexed by k)
-    unsigned long long* capped;   // [8] per size class: FP32 eigensolves stopped by the sweep cap
+    unsigned long long* sweeps;   // [kClassSlots] per size class (indexed by k)
+    unsigned long long* capped;   // [kClassSlots] per size class: FP32 eigensolves stopped by the sweep cap
     // adjoint (allocated on the first lrh_vjp call)
     int64_t all_elems;     // complex entries of the every-region arena per instance
     int32_t n_terms;
@@ -162,6 +165,11 @@ cudaError_t prepare_cta_kernels();   // lrh_cta.cu (D = 64, 128, 256)
 // Global scratch of the D = 256 pass and certification: complex entries per CTA slot for a
 // rotation log of `log_sweeps` sweeps, and the CTAs a launch uses on this device.
 int64_t big_slot_elems(int log_sweeps);
+// Adjoint of the 6- and 7-site classes (lrh_cta.cu): CTAs of one launch (scratch slots of
+// 2 D^2 complex each) and the launch.
+cudaError_t vjp_cta_slots(int k, int* slots);
+cudaError_t launch_vjp_cta(const DevProblem& P, int k, const int32_t* cls, int32_t count, float2* scratch, int slots,
+                           cudaStream_t s);
 cudaError_t big_launch_slots(int* slots);
 cudaError_t prepare_blk_kernels();   // lrh_block.cu (D = 8, 16, 2x2-block layout)
 // D = 8, 16 in the Hermitian 2x2-block layout, `threads` per CTA (64, 128 or 256)

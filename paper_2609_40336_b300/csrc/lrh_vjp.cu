@@ -34,16 +34,6 @@ struct VjpSmem {
     static constexpr size_t bytes = G * ((per_group + 15) / 16 * 16) + 16;
 };
 
-// K_kl for lambda_k, lambda_l with weights p_k, p_l: stable divided difference of the
-// normalised e^{-beta x}: p_lo expm1(-beta |d|) / |d| (p_lo = weight of the smaller eigenvalue),
-// limit -beta p at coinciding eigenvalues.
-__device__ __forceinline__ float kdd(float lk, float ll, float pk, float pl, float beta) {
-    const float d = fabsf(lk - ll);
-    const float plo = lk <= ll ? pk : pl;
-    if (d * beta < 1e-6f) return -beta * plo;
-    return plo * expm1f(-beta * d) / d;
-}
-
 template <int D>
 __global__ void __launch_bounds__(kVB) vjp_region_kernel(const DevProblem P, const int32_t* __restrict__ cls,
                                                          const int32_t count) {
