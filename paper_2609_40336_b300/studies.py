@@ -14,8 +14,15 @@ Models (Pauli matrices, open chains): Heisenberg J = 1, XYZ (Jx, Jy, Jz) = (2, -
 TFIM J = h = 1, Heisenberg with a transverse field h = 0.5 on every site, and a random
 chain (dense Hermitian nearest-neighbour terms, seeded).
 
+* ``bound_vs_L`` (Sec. 3.3, Thm 3: for weakly perturbed separable chains the interval
+  hierarchy's bound approaches E_0 exponentially fast in the interval length L; its cost per
+  iteration is O(sum_e D_e^3), Sec. 4.2): the certified bound per site of the n-site
+  perturbed chain (H = sum Z_i + delta sum X_i X_{i+1} + delta sum g_i X_i) for every L,
+  after the same beta-continuation schedule, with the wall time of the solve.
+
     python -m paper_2609_40336_b300.studies norms --n 8 16 32 64
     python -m paper_2609_40336_b300.studies eps --n 32 --eps 0.02 0.01 0.005
+    python -m paper_2609_40336_b300.studies levels --n 4096 --L 4 5 6 7 8 --iters 10
 """
 from __future__ import annotations
 
@@ -123,6 +130,30 @@ def iterations_vs_eps(models: Sequence[str], n: int, eps_list: Sequence[float], 
     return out
 
 
+def bound_vs_L(Ls: Sequence[int], n: int = 4096, delta: float = 0.1, iters_per_stage: int = 10,
+               betas: Sequence[float] = tuple(2.0 ** s for s in range(11)), seed: int = 1003) -> List[Dict]:
+    import time
+
+    import lrh_gen as g
+    out = []
+    for L in Ls:
+        p = g.lattices.perturbed_chain(n, L=L, delta=delta, seed=seed)
+        s = Solver(p, variant="nesterov", betas=betas, iters_per_stage=iters_per_stage)
+        s.synchronize()
+        t0 = time.perf_counter()
+        res = s.solve(max_records=0)
+        wall = time.perf_counter() - t0
+        inf = s.info()
+        top = inf["class_sites"].index(L)
+        out.append({"L": L, "n": n, "delta": delta, "iterations": iters_per_stage * len(betas),
+                    "bound_per_site": float(res["bound"][0] / n), "solve_s": wall,
+                    "top_regions": inf["class_regions"][top], "top_D": 2 ** L,
+                    "top_sweeps_per_eigensolve": inf["sweeps"][top] / max(1, inf["class_regions"][top] * iters_per_stage * len(betas)),
+                    "top_sweep_capped": int(inf["sweep_capped"][top])})
+        s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -134,8 +165,14 @@ def main():
     b.add_argument("--n", type=int, default=32)
     b.add_argument("--eps", nargs="+", type=float, default=[0.02, 0.01, 0.005, 0.0025])
     b.add_argument("--check", type=int, default=10)
+    c = sub.add_parser("levels")
+    c.add_argument("--n", type=int, default=4096)
+    c.add_argument("--L", nargs="+", type=int, default=[4, 5, 6, 7, 8])
+    c.add_argument("--iters", type=int, default=10)
     args = ap.parse_args()
-    if args.cmd == "norms":
+    if args.cmd == "levels":
+        res = bound_vs_L(args.L, args.n, iters_per_stage=args.iters)
+    elif args.cmd == "norms":
         res = multiplier_norms(args.models, args.n)
     else:
         res = iterations_vs_eps(args.models, args.n, args.eps, args.check)

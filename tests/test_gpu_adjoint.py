@@ -51,8 +51,9 @@ def test_vjp_matches_oracle(name):
     flat_T = np.concatenate([t.reshape(p.n_instances, -1) for t in r_T], axis=1)
     e_nu, e_T = rel(nu_bar.astype(np.complex128), r_nu), rel(term_bar.astype(np.complex128), flat_T)
     print(f"VJPERR {name} beta={beta:g} nu_bar={e_nu:.2e} term_bar={e_T:.2e}")
-    assert e_nu <= 1e-4
-    assert e_T <= 1e-4
+    tol = 1e-5 if beta >= 256 else 1e-4   # beta = 256 (the J1-J2 workload's): within 1e-5
+    assert e_nu <= tol
+    assert e_T <= tol
 
 
 def test_vjp_envelope_equals_gradient():
