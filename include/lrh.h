@@ -175,6 +175,15 @@ typedef struct {
     double deadline_s;           /* lrh_solve stops at the first record after this many
                                     seconds of wall time (<= 0: no deadline)                  */
     const char* tune_cache;      /* cache file lrh_autotune uses when called with NULL (copied) */
+    /* Target-driven solve (lrh_solve with certify_every > 0): */
+    const double* target;        /* [n_instances] or NULL (copied): lrh_solve stops at the first
+                                    checkpoint whose certified bound is >= target[i] on every
+                                    instance i with a finite target                            */
+    double screen_tol;           /* > 0 (with target): before certifying a checkpoint, estimate
+                                    Q(nu) = sum_e lambda_min(theta_e) in FP32 (one region pass)
+                                    and certify (FP64) only if the estimate is >= target[i] -
+                                    screen_tol on every targeted instance; the run's last
+                                    checkpoint is always certified.  0: certify every checkpoint */
 } lrh_options;
 
 typedef struct lrh_problem lrh_problem;
@@ -224,7 +233,8 @@ typedef struct {
     int64_t T_nesterov, T_subgradient;
 } lrh_params;
 
-/* One record of lrh_solve: the certified bound after `iteration` iterations of the run. */
+/* One record of lrh_solve: the certified bound after `iteration` iterations of the run (with
+ * screening, only the checkpoints that were certified are recorded). */
 typedef struct {
     int64_t iteration;   /* iterations since the start of this lrh_solve call               */
     double seconds;      /* host wall time since the start of the call, after the bound was read */

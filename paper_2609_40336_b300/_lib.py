@@ -68,6 +68,8 @@ class Options(C.Structure):
         ("certify_every", C.c_int32),
         ("deadline_s", C.c_double),
         ("tune_cache", C.c_char_p),
+        ("target", C.POINTER(C.c_double)),
+        ("screen_tol", C.c_double),
     ]
 
 

@@ -68,6 +68,7 @@ struct lrh_problem {
     lrh_options opt{};
     std::vector<double> beta_sched;   // owned copies of the options' host arrays
     std::string tune_cache;
+    std::vector<double> target;
     int32_t n_sites = 0, kappa = 0;
     double lhat_eff = 1.0;
     int32_t n_inst = 1, n_regions = 0, n_pairs = 0, max_k = 0;
@@ -165,6 +166,7 @@ int validate_options(const lrh_options* o) {
         if (!(o->beta_sched[i] > 0.0) || !std::isfinite(o->beta_sched[i])) return fail(LRH_EINVAL, "beta_sched entries must be finite and > 0");
     if (o->iters_per_stage < 0 || o->certify_every < 0) return fail(LRH_EINVAL, "iters_per_stage and certify_every must be >= 0");
     if (!std::isfinite(o->deadline_s)) return fail(LRH_EINVAL, "non-finite deadline_s");
+    if (!(o->screen_tol >= 0.0) || !std::isfinite(o->screen_tol)) return fail(LRH_EINVAL, "screen_tol must be finite and >= 0");
     if (o->variant != LRH_SUBGRADIENT && o->variant != LRH_NESTEROV) return fail(LRH_EINVAL, "unknown variant");
     if (o->step_rule != LRH_STEP_CONST && o->step_rule != LRH_STEP_INV_SQRT) return fail(LRH_EINVAL, "unknown step rule");
     if (o->variant == LRH_SUBGRADIENT && !(o->alpha > 0.0)) return fail(LRH_EINVAL, "alpha must be > 0");
@@ -174,13 +176,16 @@ int validate_options(const lrh_options* o) {
     return LRH_OK;
 }
 
-// Options with their host arrays copied into the problem (the caller's may go away).
+// Options with their host arrays copied into the problem (the caller's may go away);
+// p->n_inst must be set (the length of `target`).
 void copy_options(lrh_problem* p, const lrh_options* o) {
     p->opt = *o;
     p->beta_sched.assign(o->beta_sched, o->beta_sched + (o->n_beta > 0 ? o->n_beta : 0));
     p->opt.beta_sched = p->beta_sched.empty() ? nullptr : p->beta_sched.data();
     p->tune_cache = o->tune_cache ? o->tune_cache : "";
     p->opt.tune_cache = o->tune_cache ? p->tune_cache.c_str() : nullptr;
+    if (o->target) p->target.assign(o->target, o->target + p->n_inst); else p->target.clear();
+    p->opt.target = p->target.empty() ? nullptr : p->target.data();
 }
 
 int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
@@ -697,9 +702,9 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     lrh_problem* p = new (std::nothrow) lrh_problem();
     if (!p) return fail(LRH_ENOMEM, "host allocation");
     std::unique_ptr<lrh_problem> guard(p);
-    copy_options(p, opts);
     p->n_sites = d->n_sites;
     p->n_inst = d->n_instances;
+    copy_options(p, opts);
     p->n_regions = R;
     p->max_k = maxk;
     cudaGetDevice(&p->device);
@@ -1599,6 +1604,32 @@ int lrh_reset(lrh_problem* p) {
     return LRH_OK;
 }
 
+namespace {
+// FP32 estimate of Q(nu) = sum_e lambda_min(theta_e(nu)) per instance: one region pass in the
+// ground-state mode at nu (no update; the pass's states and traces are rewritten by the next
+// iteration's first pass), FP64 sums.  Restores the iteration scalars' mode afterwards.
+int estimate_q32(lrh_problem* p, double* out) {
+    const lrh_options& o = p->opt;
+    const double degen = o.degen_tol > 0.0 ? o.degen_tol : 1e-5;
+    const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
+    const int cert = o.cert_sweeps > 0 ? o.cert_sweeps : 40;
+    LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), 0.0, 0.0, 0, o.beta, 1.0 / p->lhat_eff, o.alpha, degen,
+                            LRH_SUBGRADIENT, o.step_rule, sweeps, cert, p->stream));
+    PassIO io{};
+    io.nu_in = p->P.nu;
+    io.rho_out = p->P.rho;
+    io.tr_out = p->P.tr;
+    int rc = launch_all_classes(p, io);
+    if (rc) return rc;
+    LRH_CK(launch_reduce(p->P, p->P.val, 0, p->stream));
+    LRH_CK(cudaMemcpyAsync(p->h_pinned, p->P.q_sum, sizeof(double) * p->n_inst, cudaMemcpyDeviceToHost, p->stream));
+    if ((rc = push_state(p, false, 0.0, 0.0))) return rc;
+    if ((rc = read_err(p))) return rc;
+    std::copy(p->h_pinned, p->h_pinned + p->n_inst, out);
+    return LRH_OK;
+}
+}  // namespace
+
 int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_bounds, int32_t* n_records,
               double* bound_out) {
     if (!p || !bound_out) return fail(LRH_EINVAL, "NULL argument");
@@ -1611,9 +1642,17 @@ int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_
     int32_t nrec = 0;
     int64_t done = 0;
     int status = LRH_OK;
-    bool stop = false;
+    bool stop = false, reached = false;
     if (n_records) *n_records = 0;
-    auto record = [&](double beta) -> int {
+    const bool targeted = !p->target.empty() && p->opt.certify_every > 0;
+    std::vector<double> est((size_t)NI);
+    auto record = [&](double beta, bool last) -> int {
+        if (targeted && p->opt.screen_tol > 0.0 && !last) {   // FP32 screen before the FP64 certificate
+            int r = estimate_q32(p, est.data());
+            if (r) return r;
+            for (int64_t i = 0; i < NI; ++i)
+                if (std::isfinite(p->target[i]) && est[i] < p->target[i] - p->opt.screen_tol) return LRH_OK;
+        }
         int r = lrh_bound(p, LRH_BOUND_CERTIFIED, cur.data());
         if (r && r != LRH_ENOCONV) return r;
         if (r == LRH_ENOCONV) status = LRH_ENOCONV;
@@ -1626,6 +1665,12 @@ int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_
         }
         std::copy(cur.begin(), cur.end(), bound_out);
         if (p->opt.deadline_s > 0.0 && secs > p->opt.deadline_s) stop = true;
+        if (targeted) {
+            bool all = true;
+            for (int64_t i = 0; i < NI; ++i)
+                if (std::isfinite(p->target[i]) && !(cur[i] >= p->target[i])) all = false;
+            if (all) reached = true;
+        }
         return LRH_OK;
     };
     const int per = p->opt.iters_per_stage;
@@ -1634,28 +1679,29 @@ int lrh_solve(lrh_problem* p, int32_t max_records, lrh_record* rec, double* rec_
     if (p->opt.variant == LRH_NESTEROV) {
         std::vector<double> stages = p->beta_sched;
         if (stages.empty()) stages.push_back(p->opt.beta);
-        for (size_t si = 0; si < stages.size() && !stop; ++si) {
+        for (size_t si = 0; si < stages.size() && !stop && !reached; ++si) {
             p->opt.beta = stages[si];        // L_hat follows: lhat if set, else beta Lambda_G / 2
             if ((rc = lrh_restart(p))) return rc;
-            for (int it = 0; it < per && !stop;) {
+            for (int it = 0; it < per && !stop && !reached;) {
                 const int n = std::min(every, per - it);
                 if ((rc = lrh_step(p, n))) return rc;
                 it += n;
                 done += n;
-                if (p->opt.certify_every > 0 && (rc = record(stages[si]))) return rc;
+                const bool last = si + 1 == stages.size() && it >= per;
+                if (p->opt.certify_every > 0 && (rc = record(stages[si], last))) return rc;
             }
         }
-        if (p->opt.certify_every <= 0 && (rc = record(p->opt.beta))) return rc;
+        if (p->opt.certify_every <= 0 && (rc = record(p->opt.beta, true))) return rc;
     } else {
         if ((rc = lrh_restart(p))) return rc;
-        for (int it = 0; it < per && !stop;) {
+        for (int it = 0; it < per && !stop && !reached;) {
             const int n = std::min(every, per - it);
             if ((rc = lrh_step(p, n))) return rc;
             it += n;
             done += n;
-            if (p->opt.certify_every > 0 && (rc = record(0.0))) return rc;
+            if (p->opt.certify_every > 0 && (rc = record(0.0, it >= per))) return rc;
         }
-        if (p->opt.certify_every <= 0 && (rc = record(0.0))) return rc;
+        if (p->opt.certify_every <= 0 && (rc = record(0.0, true))) return rc;
     }
     if (stop) return fail(LRH_EDEADLINE, "lrh_solve reached its deadline");
     return status;

@@ -124,7 +124,8 @@ class Solver:
                  alpha: float = 1.0, step_rule: str = "inv_sqrt", degen_tol: float = 1e-5,
                  max_sweeps: int = 15, use_graph: Optional[bool] = None, loop: str = "auto", stream=None,
                  cert_sweeps: int = 0, betas: Optional[Sequence[float]] = None, iters_per_stage: int = 0,
-                 certify_every: int = 0, deadline_s: float = 0.0, tune_cache: Optional[str] = None):
+                 certify_every: int = 0, deadline_s: float = 0.0, tune_cache: Optional[str] = None,
+                 targets: Optional[Sequence[float]] = None, screen_tol: float = 0.0):
         self._lib = L.load()
         self._h = C.c_void_p(0)
         desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats,
@@ -136,6 +137,9 @@ class Solver:
                               cert_sweeps=int(cert_sweeps), iters_per_stage=int(iters_per_stage),
                               certify_every=int(certify_every), deadline_s=float(deadline_s))
         self._set_betas(betas)
+        self.n_instances = int(desc.n_instances)
+        self._set_targets(targets)
+        self._opt.screen_tol = float(screen_tol)
         self._tune = tune_cache.encode() if tune_cache else None
         self._opt.tune_cache = self._tune
         st = _current_stream() if stream is None else C.c_void_p(int(stream))
@@ -189,6 +193,18 @@ class Solver:
         return par, chi, off
 
     # ------------------------------------------------------------ control
+    def _set_targets(self, targets) -> None:
+        """Per-instance targets of lrh_solve (NaN: no target for that instance; None: none)."""
+        if targets is None:
+            self._targets = None
+            self._opt.target = None
+            return
+        self._targets = np.ascontiguousarray(np.asarray(targets, np.float64).reshape(-1))
+        n = getattr(self, "n_instances", None)
+        if n is not None and self._targets.size != n:
+            raise ValueError(f"targets needs {n} entries")
+        self._opt.target = _ptr(self._targets, C.c_double)
+
     def _set_betas(self, betas) -> None:
         self._betas = np.ascontiguousarray(betas if betas is not None else [1.0], np.float64)
         self._opt.n_beta = len(betas) if betas is not None else 0
@@ -197,6 +213,8 @@ class Solver:
     def set_options(self, **kw) -> None:
         o = self._opt
         if "betas" in kw: self._set_betas(kw.pop("betas"))
+        if "targets" in kw: self._set_targets(kw.pop("targets"))
+        if "screen_tol" in kw: o.screen_tol = float(kw.pop("screen_tol"))
         for k in ("cert_sweeps", "iters_per_stage", "certify_every"):
             if k in kw: setattr(o, k, int(kw.pop(k)))
         if "deadline_s" in kw: o.deadline_s = float(kw.pop("deadline_s"))

@@ -221,3 +221,32 @@ def test_thm6_constant_step_subgradient_on_intervals_matches_oracle():
         dual.subgradient_step(P, h, st, "const", prm["alpha"], tol=1e-5)
     assert np.all(np.abs(s.messages("nu").astype(np.complex128) - st.nu) <= 3 * prm["alpha"] * 1e-4 + 1e-6)
     assert abs(s.bound("best")[0] - st.q_best[0]) <= 1e-5 * abs(st.q_best[0])
+
+
+def test_solve_stops_at_the_first_certified_checkpoint_reaching_the_target():
+    """lrh_options.target: the run stops at the first checkpoint whose certified bound reaches
+    every finite target (same trajectory as the untargeted run); with screen_tol the FP32
+    estimate skips FP64 certifications far from the target but not the stopping checkpoint."""
+    p = L.xxz_triangular(4, 3)
+    s = Solver(p, variant="nesterov", betas=[1.0, 4.0, 16.0], iters_per_stage=40, certify_every=10)
+    full = s.solve(max_records=20)
+    recs = full["records"]
+    assert len(recs) == 12
+    targets = recs[7]["bound"].copy()
+    targets[1] = np.nan
+    first = next(i for i, r in enumerate(recs) if np.all(r["bound"][[0, 2]] >= targets[[0, 2]]))
+    for screen in (0.0, 0.05 * p.n_sites):
+        s.set_options(targets=targets, screen_tol=screen)
+        s.reset()
+        out = s.solve(max_records=20)
+        last = out["records"][-1]
+        assert last["iteration"] == recs[first]["iteration"]
+        assert np.array_equal(last["bound"], recs[first]["bound"])
+        assert np.array_equal(out["bound"], recs[first]["bound"])
+        if screen == 0.0:
+            assert len(out["records"]) == first + 1
+        else:
+            assert 1 <= len(out["records"]) <= first + 1
+    s.set_options(targets=None, screen_tol=0.0)
+    with pytest.raises(ValueError):
+        s.set_options(targets=[1.0])
