@@ -152,26 +152,34 @@ struct Split {
     int NS;
     int D;
     __device__ __forceinline__ int sig(int j) const { return j; }
-    __device__ __forceinline__ C2& at(int x) const { return x < NS ? s[x] : g[x - NS]; }
+    // separate shared and global accesses (a reference into either would force generic addressing)
+    __device__ __forceinline__ C2 ld(int x) const {
+        if (x < NS) return s[x];
+        return g[x - NS];
+    }
+    __device__ __forceinline__ void st(int x, C2 v) const {
+        if (x < NS) s[x] = v;
+        else g[x - NS] = v;
+    }
     __device__ __forceinline__ C2 get(int i, int j) const {
-        if (i <= j) return at(tri(i, j, D));
-        C2 v = at(tri(j, i, D));
+        if (i <= j) return ld(tri(i, j, D));
+        C2 v = ld(tri(j, i, D));
         v.y = -v.y;
         return v;
     }
     __device__ __forceinline__ void set(int i, int j, C2 v) const {
-        if (i <= j) { at(tri(i, j, D)) = v; } else { v.y = -v.y; at(tri(j, i, D)) = v; }
+        if (i <= j) { st(tri(i, j, D), v); } else { v.y = -v.y; st(tri(j, i, D), v); }
     }
-    __device__ __forceinline__ C2 dget(int i) const { return at(tri(i, i, D)); }
-    __device__ __forceinline__ void dset(int i, C2 v) const { at(tri(i, i, D)) = v; }
+    __device__ __forceinline__ C2 dget(int i) const { return ld(tri(i, i, D)); }
+    __device__ __forceinline__ void dset(int i, C2 v) const { st(tri(i, i, D), v); }
     template <int NT>
     __device__ __forceinline__ void sums(T& offd, T& diag) const {
         offd = T(0); diag = T(0);
         for (int e = threadIdx.x; e < D * D; e += NT) {
             const int i = e / D, j = e - (e / D) * D;
-            if (i < j) { const C2 v = at(tri(i, j, D)); offd += v.x * v.x + v.y * v.y; }
+            if (i < j) { const C2 v = ld(tri(i, j, D)); offd += v.x * v.x + v.y * v.y; }
         }
-        for (int i = threadIdx.x; i < D; i += NT) { const C2 v = at(tri(i, i, D)); diag += v.x * v.x + v.y * v.y; }
+        for (int i = threadIdx.x; i < D; i += NT) { const C2 v = ld(tri(i, i, D)); diag += v.x * v.x + v.y * v.y; }
     }
 };
 
@@ -1006,15 +1014,27 @@ __global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevPr
             __syncthreads();
             float2* v0 = Vs + (2 * warp) * D;
             float2* v1 = v0 + D;
+            // the next round's log records are loaded while this round's rotations run
+            RotC<float> nxt[n / 32];
+            if (nrounds > 0) {
+#pragma unroll
+                for (int m = 0; m < n / 32; ++m) nxt[m] = logp[lane + 32 * m];
+            }
             for (int rd = 0; rd < nrounds; ++rd) {
-                const RotC<float>* lg = logp + (size_t)rd * n;
+                RotC<float> cur[n / 32];
+#pragma unroll
+                for (int m = 0; m < n / 32; ++m) cur[m] = nxt[m];
+                if (rd + 1 < nrounds) {
+                    const RotC<float>* lg = logp + (size_t)(rd + 1) * n;
+#pragma unroll
+                    for (int m = 0; m < n / 32; ++m) nxt[m] = lg[lane + 32 * m];
+                }
 #pragma unroll
                 for (int m = 0; m < n / 32; ++m) {
-                    const RotC<float> Rk = lg[lane + 32 * m];
-                    const int pq = __float_as_int(Rk.pad);
+                    const int pq = __float_as_int(cur[m].pad);
                     const int p = pq & 0xffff, q = pq >> 16;
-                    rot_pair(v0[p], v0[q], Rk);
-                    rot_pair(v1[p], v1[q], Rk);
+                    rot_pair(v0[p], v0[q], cur[m]);
+                    rot_pair(v1[p], v1[q], cur[m]);
                 }
                 __syncwarp();
             }
