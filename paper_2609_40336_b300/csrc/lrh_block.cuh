@@ -216,6 +216,19 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         tab_sgn[threadIdx.x] = make_float4(sg[0], sg[1], sg[2], sg[3]);
     }
     __syncthreads();
+    // the same table in registers, packed (a round reads it without shared-memory traffic):
+    // pk0 = unit slots of the block's two halves (bits 0-7, 8-15) and the byte offsets of its
+    // row and column rotations (16-23, 24-31); pk1 / pk2 = float2 indices of the next positions
+    // of entries 0, 1 / 2, 3 (bits 0-14, 16-30), bits 15 / 31 set when the entry is stored
+    // conjugated
+    uint32_t pk1[PER], pk2[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int4 dd = tab_dst[j * D + s];
+        const float4 sg = tab_sgn[j * D + s];
+        pk1[j] = (uint32_t)dd.x | (sg.x < 0.f ? 0x8000u : 0u) | ((uint32_t)dd.y << 16) | (sg.y < 0.f ? 0x80000000u : 0u);
+        pk2[j] = (uint32_t)dd.z | (sg.z < 0.f ? 0x8000u : 0u) | ((uint32_t)dd.w << 16) | (sg.w < 0.f ? 0x80000000u : 0u);
+    }
     // this lane's diagonal block: pair s mod (D/2) (lanes s >= D/2 compute a copy and store
     // nothing), and the next positions of its entries (never conjugated: 0 and 3 stay on the
     // diagonal, and entry 1 is written as zero)
@@ -302,6 +315,7 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         for (int j = 0; j < PER; ++j) {
             {   // a lane without a j-th block repeats a valid block: the same values to the same
                 // places, and the round stays one basic block (loads of both blocks in flight)
+                const uint32_t w1 = pk1[j], w2 = pk2[j];
                 const int4 of = tab_off[j * D + s];
                 const float4 h0 = *reinterpret_cast<const float4*>(cb + of.x);
                 const float4 h1 = *reinterpret_cast<const float4*>(cb + of.y);
@@ -310,12 +324,12 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
                 const RotC<float> K = *reinterpret_cast<const RotC<float>*>(pb + of.z);
                 const RotC<float> Lr = *reinterpret_cast<const RotC<float>*>(pb + of.w);
                 two_sided<float>(b00, b01, b10, b11, K, Lr);
-                const int4 dd = tab_dst[j * D + s];
-                const float4 sg = tab_sgn[j * D + s];
-                nxt[dd.x] = make_float2(b00.x, sg.x * b00.y);
-                nxt[dd.y] = make_float2(b01.x, sg.y * b01.y);
-                nxt[dd.z] = make_float2(b10.x, sg.z * b10.y);
-                nxt[dd.w] = make_float2(b11.x, sg.w * b11.y);
+                // conjugation: flip the sign bit of the imaginary part
+                auto cj = [](float y, uint32_t bit31) { return __int_as_float(__float_as_int(y) ^ (int)(bit31 & 0x80000000u)); };
+                nxt[w1 & 0x7fffu] = make_float2(b00.x, cj(b00.y, w1 << 16));
+                nxt[(w1 >> 16) & 0x7fffu] = make_float2(b01.x, cj(b01.y, w1));
+                nxt[w2 & 0x7fffu] = make_float2(b10.x, cj(b10.y, w2 << 16));
+                nxt[(w2 >> 16) & 0x7fffu] = make_float2(b11.x, cj(b11.y, w2));
             }
         }
         __syncwarp();

@@ -901,8 +901,8 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
 // rest lives in this CTA's global scratch slot (kept in L2 while the CTA runs; Split accessor).
 // V (512 KB) fits neither registers nor shared memory during the sweeps, so the sweeps append
 // their rotations to a log in the slot (16 bytes per pair and round), and V is formed afterwards
-// by replaying the log on 64 rows at a time in shared memory: rows of V are independent (each is
-// a row of the identity times J_1 J_2 ...), so each warp owns two rows and needs only a warp
+// by replaying the log on 96 rows at a time in shared memory: rows of V are independent (each is
+// a row of the identity times J_1 J_2 ...), so each warp owns three rows and needs only a warp
 // barrier between rounds.  rho = W W^dagger (W = V diag(sqrt p)) is formed tile by tile into the
 // slot and traced onto the children.  One 1024-thread CTA per SM, each looping over the regions
 // of the launch.
@@ -910,7 +910,7 @@ constexpr int kBigD = 256;
 constexpr int kBigN = kBigD / 2;
 constexpr int kBigTri = kBigD * (kBigD + 1) / 2;   // 32,896 entries
 constexpr int kBigNOFF = kBigN * (kBigN - 1) / 2;   // 8,128 off-diagonal 2x2 blocks
-constexpr int kBigRB = 64;                          // V rows per batch (two per warp)
+constexpr int kBigRB = 96;                          // V rows per batch (three per warp)
 constexpr int kBigT = 64;                           // rho tile edge
 
 struct BigSmem {
@@ -1010,10 +1010,13 @@ __global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevPr
         const int nrounds = sweeps * (D - 1);
         float2* Vs = tri_s;
         for (int row0 = 0; row0 < D; row0 += kBigRB) {
-            for (int e = t; e < kBigRB * D; e += NT) Vs[e] = make_float2((row0 + e / D == e % D) ? 1.f : 0.f, 0.f);
+            const int rows = min(kBigRB, D - row0);
+            for (int e = t; e < rows * D; e += NT) Vs[e] = make_float2((row0 + e / D == e % D) ? 1.f : 0.f, 0.f);
             __syncthreads();
-            float2* v0 = Vs + (2 * warp) * D;
-            float2* v1 = v0 + D;
+            // warp w owns rows 3w .. 3w + 2 of the batch (those below `rows`)
+            constexpr int RPW = kBigRB / 32;
+            const int nr = max(0, min(RPW, rows - RPW * warp));
+            float2* v0 = Vs + (RPW * warp) * D;
             // the next round's log records are loaded while this round's rotations run
             RotC<float> nxt[n / 32];
             if (nrounds > 0) {
@@ -1033,13 +1036,14 @@ __global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevPr
                 for (int m = 0; m < n / 32; ++m) {
                     const int pq = __float_as_int(cur[m].pad);
                     const int p = pq & 0xffff, q = pq >> 16;
-                    rot_pair(v0[p], v0[q], cur[m]);
-                    rot_pair(v1[p], v1[q], cur[m]);
+#pragma unroll
+                    for (int rr = 0; rr < RPW; ++rr)
+                        if (rr < nr) rot_pair(v0[rr * D + p], v0[rr * D + q], cur[m]);
                 }
                 __syncwarp();
             }
             __syncthreads();
-            for (int e = t; e < kBigRB * D; e += NT) {
+            for (int e = t; e < rows * D; e += NT) {
                 const float2 v = Vs[e];
                 const float q = pw[e % D];
                 Wg[(int64_t)row0 * D + e] = make_float2(v.x * q, v.y * q);
