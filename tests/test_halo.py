@@ -154,3 +154,46 @@ def test_two_gloo_ranks_exchange_halos_bit_identically(name):
         merged = np.where(np.isnan(out[0][w]), out[1][w], out[0][w])
         assert not np.any(np.isnan(merged))
         assert np.array_equal(merged, ref[w]), w
+
+
+def test_a_dropped_halo_item_breaks_bit_identity():
+    """Planted mistake: shard 0's first received item zeroed after every exchange must break
+    the bit-identity that the correct exchange gives."""
+    p = PROBLEMS["chain_L4"]()
+    ref, _ = _run(p, 1, BETAS, ITERS)
+    shards, (par, chi) = halo.plan_shards(p, 2)
+    goff = halo.msg_offsets(p.regions, list(zip(par, chi)))
+    drivers = [halo.HaloDriver(sh, OracleShardEngine(sh, BETAS[0])) for sh in shards]
+    for b in BETAS:
+        for d in drivers:
+            d.engine.set_beta(b)
+            d.restart()
+        for _ in range(ITERS):
+            halo.run_local(drivers, 1)
+    good = np.full(ref["nu"].shape, np.nan, np.complex128)
+    for d in drivers:
+        d.scatter_into(good, goff, "nu")
+    assert np.array_equal(good, ref["nu"])
+    # the same run with shard 0's first received item zeroed after every exchange
+    drivers = [halo.HaloDriver(sh, OracleShardEngine(sh, BETAS[0])) for sh in shards]
+    a, b_ = next(iter(drivers[0].recv_seg.values()))
+    first = drivers[0].shard.item_elems(*drivers[0].recv_items[0])
+    for b in BETAS:
+        for d in drivers:
+            d.engine.set_beta(b)
+            d.restart()
+        for _ in range(ITERS):
+            for d in drivers:
+                d.begin()
+            for d in drivers:
+                for peer, (lo, hi) in d.recv_seg.items():
+                    src = drivers[peer]
+                    sa, sb = src.send_seg[d.shard.part]
+                    d.recv[:, 2 * lo:2 * hi] = src.send[:, 2 * sa:2 * sb]
+            drivers[0].recv[:, 2 * a:2 * (a + first)] = 0
+            for d in drivers:
+                d.finish()
+    bad = np.full(ref["nu"].shape, np.nan, np.complex128)
+    for d in drivers:
+        d.scatter_into(bad, goff, "nu")
+    assert not np.array_equal(bad, ref["nu"])
