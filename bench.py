@@ -581,8 +581,9 @@ def run_lrh(args, ws, rank, dev, stream):
     import torch
     import torch.distributed as dist
     p = WL.problem(rank, ws)
-    tune = os.path.join(ROOT, "gpurun_out", f"tune_{WL_KEY}_rank{rank}.jsonl") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    # the autotuner's choices for this run (read back by the end-to-end leg's fresh solver)
+    import tempfile
+    tune = os.path.join(tempfile.gettempdir(), f"lrh_tune_{WL_KEY}_rank{rank}_{os.getpid()}.jsonl")
     s = make_solver(p, stream)
     n_units = s.n_regions * s.n_instances
     iters = WL.n_iterations()
