@@ -250,3 +250,20 @@ def test_solve_stops_at_the_first_certified_checkpoint_reaching_the_target():
     s.set_options(targets=None, screen_tol=0.0)
     with pytest.raises(ValueError):
         s.set_options(targets=[1.0])
+
+
+def test_problem_without_terms_stays_at_zero():
+    """No Hamiltonian terms: theta_e = 0 at nu = 0, every Gibbs state is the maximally mixed
+    state, every gradient vanishes (rho_f = Tr_{e\\f} rho_e = I / D_f; in FP32 to the rounding
+    of sqrt(1/D) squared), so Alg. 2 stays at nu = 0 and the certified bound is 0 (= E_0 of the
+    zero Hamiltonian) to that rounding."""
+    p = g.Problem(6, L.interval_regions(6, 3), [], [])
+    s = Solver(p, variant="nesterov", beta=4.0)
+    s.evaluate()
+    assert np.max(np.abs(s.messages("grad"))) <= 1e-7
+    s.step(7)
+    assert np.max(np.abs(s.messages("nu"))) <= 1e-6
+    assert abs(s.bound("certified")[0]) <= 1e-5
+    P = Poset(p.regions)
+    ref = dual.region_pass(P, dual.local_terms(p, P), dual.zeros_messages(P, 1), "smooth", beta=4.0)
+    assert np.allclose(s.region_values("last")[0], ref.value[0], atol=1e-6)
