@@ -243,12 +243,10 @@ struct CtaSmem {
 // (Computing the next round's rotations inside the block updates, to save the first barrier,
 // measured slower: the 64 parameter computations then fall on many warps, each of which runs
 // the divisions and square roots for one lane, instead of two warps running them for all.)
-// LOG (instead of V): every round's rotations are appended to `log` (n records per round, the
-// pair's two positions packed into the pad word), for V to be formed afterwards.
-template <int D, typename T, bool WANT_V, typename Acc, bool LOG = false>
+template <int D, typename T, bool WANT_V, typename Acc>
 __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsigned short* tab,
                           T* red, T (&vr)[D / 4], T (&vi)[D / 4], int max_sweeps, T tol2, T& norm2_out,
-                          T& off_out, RotC<T>* log = nullptr) {
+                          T& off_out) {
     using C2 = typename V2<T>::t;
     constexpr int NT = CtaCfg<D>::NT;
     constexpr int n = D / 2;
@@ -285,11 +283,6 @@ __device__ int jacobi_cta(Acc A, RotC<T>* prm, int* idx0, int* idx1, const unsig
                 const auto b = A.get(pq.x, pq.y);
                 C2 unused;
                 rot_params_d<T>(A.dget(pq.x).x, A.dget(pq.y).x, b.x, b.y, prm[prm_at<D>(t)], unused);
-                if constexpr (LOG) {
-                    RotC<T> e = prm[prm_at<D>(t)];
-                    e.pad = __int_as_float(pq.x | (pq.y << 16));
-                    log[((size_t)(sweeps - 1) * (D - 1) + r) * n + t] = e;
-                }
             }
             __syncthreads();
             if (t < D) ixn[t] = ix[rr_src_c(t, D)];
@@ -897,15 +890,16 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) certify_cta_kernel(const DevPro
 
 // ---------------------------------------------------------------------------------------------
 // D = 256 (regions of 8 sites).  theta's packed upper triangle (32,896 complex entries: 263 KB in
-// FP32, 526 KB in FP64) exceeds one CTA's shared memory: its first entries stay there and the
-// rest lives in this CTA's global scratch slot (kept in L2 while the CTA runs; Split accessor).
-// V (512 KB) fits neither registers nor shared memory during the sweeps, so the sweeps append
-// their rotations to a log in the slot (16 bytes per pair and round), and V is formed afterwards
-// by replaying the log on 96 rows at a time in shared memory: rows of V are independent (each is
-// a row of the identity times J_1 J_2 ...), so each warp owns three rows and needs only a warp
-// barrier between rounds.  rho = W W^dagger (W = V diag(sqrt p)) is formed tile by tile into the
-// slot and traced onto the children.  One 1024-thread CTA per SM, each looping over the regions
-// of the launch.
+// FP32, 526 KB in FP64) and V (512 KB) exceed one SM's shared memory and registers.  The FP32
+// Jacobi keeps theta in slot order in two packed triangles of this CTA's global scratch slot
+// (L2-resident while the CTA runs), ping-ponged every round (jacobi256_slots); the FP64
+// certification keeps the first part of its triangle in shared memory and the rest in the slot
+// (Split accessor).  V is not carried through the sweeps: they append their rotations to a log in
+// the slot (16 bytes per pair and round), and V is formed afterwards by replaying the log on 96
+// rows at a time in shared memory: rows of V are independent (each is a row of the identity times
+// J_1 J_2 ...), so each warp owns three rows and needs only a warp barrier between rounds.
+// rho = W W^dagger (W = V diag(sqrt p)) is formed tile by tile into the slot and traced onto the
+// children.  One 1024-thread CTA per SM, each looping over the regions of the launch.
 constexpr int kBigD = 256;
 constexpr int kBigN = kBigD / 2;
 constexpr int kBigTri = kBigD * (kBigD + 1) / 2;   // 32,896 entries
@@ -922,7 +916,6 @@ struct BigSmem {
     static constexpr size_t fixed = prm_bytes + idx_bytes + tab_bytes + lam_bytes + red_bytes;
     static constexpr size_t total = 227 * 1024;   // opt-in shared memory of one CTA
     static constexpr size_t tri_bytes = (total - fixed) / 16 * 16;
-    static constexpr int ns32 = (int)(tri_bytes / sizeof(float2));
     static constexpr int ns64 = (int)(tri_bytes / sizeof(double2));
     static constexpr size_t off_prm = tri_bytes;
     static constexpr size_t off_idx = off_prm + prm_bytes;
@@ -935,9 +928,11 @@ struct BigSmem {
     static_assert(sizeof(float2) * 2 * kBigT * (kBigT + 1) <= tri_bytes, "rho tiles");
 };
 
-// scratch slot (complex64 units): theta overflow | V (W after scaling) | rho | rotation log
-constexpr int64_t kBigTriG = ((int64_t)(kBigTri - BigSmem::ns32) + 1) / 2 * 2;
-constexpr int64_t kBigOffV = kBigTriG;
+// scratch slot (complex64 units): the two theta buffers of the FP32 Jacobi (packed upper
+// triangles in slot order; the FP64 certification uses the same space for its overflow) | V (W
+// after scaling) | rho | rotation log
+constexpr int64_t kBigTriPad = ((int64_t)kBigTri + 1) / 2 * 2;
+constexpr int64_t kBigOffV = 2 * kBigTriPad;
 constexpr int64_t kBigOffR = kBigOffV + (int64_t)kBigD * kBigD;
 constexpr int64_t kBigOffLog = kBigOffR + (int64_t)kBigD * kBigD;
 static_assert(2 * (int64_t)(kBigTri - BigSmem::ns64) <= kBigOffLog, "FP64 overflow fits the slot");
@@ -949,6 +944,93 @@ __device__ __forceinline__ void rot_pair(float2& p, float2& q, const RotC<float>
     const float nqi = R.c * q.y - (R.wr * p.y + R.wi * p.x);
     p = make_float2(npr, npi);
     q = make_float2(nqr, nqi);
+}
+
+// next slot of the entries in slot o (inverse of rr_src_c)
+__host__ __device__ constexpr int rr_dst_c(int o, int D) {
+    return o == 0 ? 0 : (o == 1 ? 2 : ((o & 1) ? o - 2 : (o == D - 2 ? D - 1 : o + 2)));
+}
+
+// Cyclic Jacobi of the D = 256 pass with theta in slot order, ping-ponged between two packed
+// upper triangles in the CTA's global slot (L2-resident): a round reads every off-diagonal 2x2
+// block (k, l) of the slot pairs (2k, 2k+1), (2l, 2l+1) at fixed addresses and writes each rotated
+// entry at its next slots (rr_dst_c of its row and of its column; conjugated when that lands
+// below the diagonal) in the other buffer; the diagonal block of pair k becomes exactly diagonal
+// (the two entries of rot_params_d).  The rotations are those of jacobi_cta in the same order;
+// the slot -> position map (which basis vector each slot holds) is tracked for the rotation log,
+// from which V is formed afterwards.  After whole sweeps every entry is back in its own slot, so
+// slot t's diagonal entry is the eigenvalue of V's column t.  Returns the sweeps run and the
+// buffer holding the result.
+__device__ int jacobi256_slots(float2* bufA, float2* bufB, RotC<float>* prm, int* idx0, int* idx1,
+                               const unsigned short* tab, float* red, int max_sweeps, float tol2, float& norm2_out,
+                               float& off_out, RotC<float>* log, float2*& result) {
+    constexpr int D = kBigD, n = kBigN, NT = 1024, NOFF = kBigNOFF;
+    const int t = threadIdx.x;
+    float2* cur = bufA;
+    float2* nxt = bufB;
+    auto put = [&](float2* buf, int I, int J, float2 v) {
+        const int a = rr_dst_c(I, D), b = rr_dst_c(J, D);
+        if (a <= b) buf[tri(a, b, D)] = v;
+        else buf[tri(b, a, D)] = make_float2(v.x, -v.y);
+    };
+    auto sums = [&](const float2* a, float& offd, float& dg) {
+        offd = 0.f;
+        dg = 0.f;
+        for (int e = t; e < D * D; e += NT) {
+            const int i = e / D, j = e % D;
+            if (i < j) { const float2 v = a[tri(i, j, D)]; offd += v.x * v.x + v.y * v.y; }
+        }
+        for (int i = t; i < D; i += NT) { const float2 v = a[tri(i, i, D)]; dg += v.x * v.x + v.y * v.y; }
+    };
+    float up, dg;
+    sums(cur, up, dg);
+    const float norm2 = 2.f * block_sum<NT>(up, red) + block_sum<NT>(dg, red);
+    norm2_out = norm2;
+    const float thresh = tol2 * norm2;
+    int* ix = idx0;
+    int* ixn = idx1;
+    int sweeps = 0;
+    for (;;) {
+        sums(cur, up, dg);
+        const float off = 2.f * block_sum<NT>(up, red);
+        off_out = off;
+        if (off <= thresh || sweeps >= max_sweeps) break;
+        ++sweeps;
+        for (int r = 0; r < D - 1; ++r) {
+            if (t < n) {
+                const int p = 2 * t, q = 2 * t + 1;
+                const float2 b = cur[tri(p, q, D)];
+                float2 dnew;
+                RotC<float> R;
+                rot_params_d<float>(cur[tri(p, p, D)].x, cur[tri(q, q, D)].x, b.x, b.y, R, dnew);
+                prm[t] = R;
+                R.pad = __int_as_float(ix[p] | (ix[q] << 16));
+                log[((size_t)(sweeps - 1) * (D - 1) + r) * n + t] = R;
+                put(nxt, p, p, make_float2(dnew.x, 0.f));
+                put(nxt, q, q, make_float2(dnew.y, 0.f));
+                put(nxt, p, q, make_float2(0.f, 0.f));
+            }
+            __syncthreads();
+            if (t < D) ixn[t] = ix[rr_src_c(t, D)];
+            for (int v = t; v < NOFF; v += NT) {
+                const int kl = tab[v];
+                const int kk = kl >> 8, ll = kl & 255;
+                const int i0 = 2 * kk, j0 = 2 * ll;
+                const int r0 = tri(i0, j0, D), r1 = tri(i0 + 1, j0, D);
+                float2 b00 = cur[r0], b01 = cur[r0 + 1], b10 = cur[r1], b11 = cur[r1 + 1];
+                two_sided<float>(b00, b01, b10, b11, prm[kk], prm[ll]);
+                put(nxt, i0, j0, b00);
+                put(nxt, i0, j0 + 1, b01);
+                put(nxt, i0 + 1, j0, b10);
+                put(nxt, i0 + 1, j0 + 1, b11);
+            }
+            __syncthreads();
+            float2* tb = cur; cur = nxt; nxt = tb;
+            int* ti = ix; ix = ixn; ixn = ti;
+        }
+    }
+    result = cur;
+    return sweeps;
 }
 
 __global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevProblem P, const PassIO io,
@@ -980,16 +1062,17 @@ __global__ void __launch_bounds__(1024, 1) region_pass_cta256_kernel(const DevPr
         const int inst = b / count;
         const int r = cls[b % count];
         const RegionInfo R = P.reg[r];
-        Split<float> A{tri_s, slot, S::ns32, D};
+        float2* thA = slot;
+        float2* thB = slot + kBigTriPad;
+        Split<float> A{tri_s, thA, 0, D};   // every entry in the slot's first buffer
         __syncthreads();   // the previous region's reads of shared memory and of the slot are done
         if (t < D) idx0[t] = t;
         assemble_packed_io<D>(P, R, inst, A, io, Th);
         __syncthreads();
-        float vr[D / 4], vi[D / 4];   // not used: V comes from the log
         float norm2, off2;
-        const int sweeps = jacobi_cta<D, float, false, Split<float>, true>(A, prm, idx0, idx1, tab, red, vr, vi, max_sw,
-                                                                         1e-12f, norm2, off2, logp);
-        if (t < D) lam[t] = A.dget(t).x;   // positions: theta's diagonal holds the eigenvalues
+        float2* th = thA;
+        const int sweeps = jacobi256_slots(thA, thB, prm, idx0, idx1, tab, red, max_sw, 1e-12f, norm2, off2, logp, th);
+        if (t < D) lam[t] = th[tri(t, t, D)].x;   // whole sweeps: slot t holds eigenvalue t
         __syncthreads();
         float lmin = lam[0];
         for (int i = 1; i < D; ++i) lmin = fminf(lmin, lam[i]);
