@@ -92,6 +92,9 @@ def workloads():
                             lambda: L.j1j2_square(48), "nesterov", [256.0], 200, dominant_k=4,
                             golden="j1j2_48_fstar.json"),
     }
+    w["chain40_L8"] = Workload("perturbed_chain_n40_delta0.1_intervals_L8_nesterov_beta1-1024",
+                               lambda: L.perturbed_chain(40, L=8, delta=0.1, seed=1003), "nesterov", BETAS11, 10,
+                               dominant_k=8, note="33 regions of 256x256 (profiling size)")
     for Lint in (4, 5, 6, 7, 8):
         ips = 200 if Lint <= 5 else (20 if Lint <= 7 else 10)
         w[f"chain4096_L{Lint}"] = Workload(
@@ -404,7 +407,7 @@ def cpu_problems():
     key = WL_KEY
     if key.startswith("chain4096_L"):
         Lint = int(key[-1])
-        n = {4: 1024, 5: 256, 6: 32, 7: 12}[Lint]
+        n = {4: 1024, 5: 256, 6: 32, 7: 12, 8: 10}[Lint]
         return (lambda i: L.perturbed_chain(n, L=Lint, delta=0.1, seed=1003)), f"same family with n={n} sites"
     if key in ("xxz_tri32_x256", "xxz_tri32_x32"):
         def one(i):
