@@ -243,12 +243,11 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     bool active = true;
 
     // V takes each round's rotations one round late (so that their dependent chain overlaps V's
-    // independent FMAs).  Its columns stay in index order: in round r of a sweep the slots
-    // (2q, 2q+1) hold the indices rr_sigma(r, 2q), rr_sigma(r, 2q+1), compile-time constants in
-    // the unrolled sweep, so the tournament permutation costs V no register moves.
+    // independent FMAs); it starts as the identity with its columns in inverse tournament order,
+    // so that the first, rotation-free step (y[c] = x[rr_src(c)]) restores the identity
     float vr[D], vi[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { vr[c] = (c == s) ? 1.f : 0.f; vi[c] = 0.f; }
+    for (int c = 0; c < D; ++c) { vr[c] = (c == rr_src(s, D)) ? 1.f : 0.f; vi[c] = 0.f; }
     if (s < 2 * n) prm2[s] = RotC<float>{1.f, 0.f, 0.f, 0.f};
     __syncwarp();
 
@@ -272,20 +271,22 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         all = off + group_sum<D>(dg);
     };
 
-    // V step: the rotations `pr` of round r of a sweep on row s of V
-    auto vstep = [&](const RotC<float>* pr, const int r) {
+    // V step: the rotations `pr` on row s of V (x), then the tournament permutation into y
+    auto vstep = [&](const RotC<float>* pr, float (&xr)[D], float (&xi)[D], float (&yr)[D], float (&yi)[D]) {
 #pragma unroll
         for (int q = 0; q < n; ++q) {
             const RotC<float> Q = pr[q];
-            const int a = rr_sigma(r, 2 * q, D), b = rr_sigma(r, 2 * q + 1, D);
-            mix_cols(vr[a], vi[a], vr[b], vi[b], Q.c, Q.wr, Q.wi);
+            mix_cols(xr[2 * q], xi[2 * q], xr[2 * q + 1], xi[2 * q + 1], Q.c, Q.wr, Q.wi);
         }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { yr[c] = xr[rr_src(c, D)]; yi[c] = xi[rr_src(c, D)]; }
     };
 
-    // round r of a sweep, with parity par: rotations from the diagonal blocks of `cur` into
-    // prm2[par], the delayed V step with prm2[par ^ 1] (round r - 1's rotations), then every
-    // off-diagonal block into `nxt` at its next position
-    auto round = [&](const float2* cur, float2* nxt, int par, const int r) {
+    // one round with parity par: rotations from the diagonal blocks of `cur` into prm2[par], the
+    // delayed V step with prm2[par ^ 1] (x into y), then every off-diagonal block into `nxt` at
+    // its next position
+    auto round = [&](const float2* cur, float2* nxt, int par, float (&xr)[D], float (&xi)[D], float (&yr)[D],
+                     float (&yi)[D]) {
         const float4* c4 = reinterpret_cast<const float4*>(cur);
         const unsigned char* cb = reinterpret_cast<const unsigned char*>(cur);
         RotC<float>* pc = prm2 + n * par;
@@ -308,7 +309,7 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
                 nxt[d1] = b1;
             }
         }
-        vstep(prm2 + n * (par ^ 1), r == 0 ? D - 2 : r - 1);
+        vstep(prm2 + n * (par ^ 1), xr, xi, yr, yi);
         __syncwarp();
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
@@ -340,6 +341,7 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     sums(cur, off2, norm2);
     const float thresh = 1e-12f * norm2;
     int sweeps = 0, par = 0;
+    float ur[D], ui[D];
     for (bool first = true;; first = false) {
         if (!first) {
             float o2, a2;
@@ -349,17 +351,22 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         if (active) active = !((off2 <= thresh) || (sweeps >= max_sweeps));
         if (!__any_sync(kFull, active)) break;
         if (active) ++sweeps;
-#pragma unroll
-        for (int rd = 0; rd < D - 1; ++rd) {   // D - 1 rounds per sweep (odd: cur and nxt swap)
-            round(cur, nxt, par, rd);
-            float2* t = cur; cur = nxt; nxt = t;
-            par ^= 1;
+#pragma unroll 1
+        for (int rd = 0; rd + 1 < D - 1; rd += 2) {
+            round(cur, nxt, par, vr, vi, ur, ui);
+            round(nxt, cur, par ^ 1, ur, ui, vr, vi);
         }
+        round(cur, nxt, par, vr, vi, ur, ui);   // D - 1 rounds per sweep is odd
+        { float2* t = cur; cur = nxt; nxt = t; }
+        par ^= 1;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
     }
-    // the last round's rotations (with no sweep: identities) complete V
-    vstep(prm2 + n * (par ^ 1), D - 2);
+    // the last round's rotations (or, with no sweep, the initial permutation) complete V
+    vstep(prm2 + n * (par ^ 1), vr, vi, ur, ui);
+#pragma unroll
+    for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
     // the slots are back in natural order: lambda_s on the diagonal, row s of V in (vr, vi)
-    float ur[D], ui[D];
     const float lam = cur[eidx<D>(s, s)].x;
     const float lmin = group_min<D>(lam);
     float wgt, F;

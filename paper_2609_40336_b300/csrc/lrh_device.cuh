@@ -18,13 +18,6 @@ __host__ __device__ constexpr int rr_src(int s, int D) {
     return D == 2 ? s : s == 0 ? 0 : (s == 2 ? 1 : ((s & 1) == 0 ? s - 2 : (s == D - 1 ? D - 2 : s + 2)));
 }
 
-// Index held by slot o after r rounds of a sweep that starts in natural order: rr_src applied r
-// times.
-__host__ __device__ constexpr int rr_sigma(int r, int o, int D) {
-    for (int i = 0; i < r; ++i) o = rr_src(o, D);
-    return o;
-}
-
 __device__ __forceinline__ int pext_bits(int x, int m) {
     int r = 0, k = 0;
 #pragma unroll
