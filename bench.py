@@ -697,6 +697,15 @@ def fp32_peak(dev):
         f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (sm_max_mhz, MEASURED_PEAKS.json)"
 
 
+def warm_started(inf, ci):
+    """Whether class ci's pass starts its eigensolves from stored bases (the 2x2-block layout of
+    regions of 3 and 4 sites, lrh_options.cold_start off): each such eigensolve first forms
+    V^H V, V (3 I - V^H V) / 2, theta V and V^H (theta V), four complex D x D products (32 D^3
+    flop)."""
+    shape = inf["class_block"][ci]
+    return inf.get("warm_bytes", 0) > 0 and inf["class_sites"][ci] in (3, 4) and 4096 < shape < 8192
+
+
 def roofline(s, dev, stream, k):
     """Dominant kernel: the region pass of class k, timed with CUDA events around a CUDA graph
     of back-to-back launches on the library's stream (no host launch gaps)."""
@@ -726,7 +735,8 @@ def roofline(s, dev, stream, k):
     dur = e0.elapsed_time(e1) / reps * 1e-3
     inf1 = s.info()
     sweeps = (inf1["sweeps"][ci] - inf0["sweeps"][ci]) / (reps * n_reg)
-    fpr = 20 * sweeps * D * D * (D - 1) + 8 * D ** 3
+    warm = warm_started(inf1, ci)
+    fpr = 20 * sweeps * D * D * (D - 1) + 8 * D ** 3 + (32 * D ** 3 if warm else 0)
     achieved = n_reg * fpr / dur / 1e12
     tr = recorded_traffic(shape)
     return {"bound": "alu", "kernel": f"region pass, {n_reg} regions of {D}x{D}, launch shape {shape}",
@@ -734,7 +744,8 @@ def roofline(s, dev, stream, k):
             "traffic": tr["dram_bytes_per_launch"] if tr else None,
             "traffic_note": tr.get("note") if tr else "no ncu capture of the current kernel sources and shape",
             "peak_basis": basis, "launch_us": dur * 1e6, "sweeps_per_region": sweeps, "flops_per_region": fpr,
-            "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger"}
+            "flop_model": "20*S*D^2*(D-1) Jacobi (Hermitian rows + V columns) + 8*D^3 for W W^dagger" +
+                          (" + 32*D^3 for the warm start from the stored basis" if warm else "")}
 
 
 def roofline_persistent(s, dev, stream, n_iter):
@@ -764,14 +775,14 @@ def roofline_persistent(s, dev, stream, n_iter):
             parts.append(f"{regions} regions of 2x2 (closed form, not counted)")
             continue
         sweeps = inf1["sweeps"][ci] - inf0["sweeps"][ci]
-        flops += 20.0 * sweeps * D * D * (D - 1) + 8.0 * D ** 3 * regions * n_iter
+        flops += 20.0 * sweeps * D * D * (D - 1) + (8.0 + (32.0 if warm_started(inf1, ci) else 0.0)) * D ** 3 * regions * n_iter
         parts.append(f"{regions} regions of {D}x{D} ({sweeps / (regions * n_iter):.2f} sweeps)")
     achieved = flops / dur / 1e12
     return {"bound": "alu", "kernel": f"persist_kernel: {n_iter} iterations of " + ", ".join(parts),
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "traffic_note": "cooperative launch not captured with ncu (multi-pass replay of a grid barrier)",
             "peak_basis": basis, "launch_us": dur * 1e6, "us_per_iteration": dur * 1e6 / n_iter,
-            "flop_model": "sum over classes of 20*S*D^2*(D-1) + 8*D^3 per region and iteration"}
+            "flop_model": "sum over classes of 20*S*D^2*(D-1) + 8*D^3 per region and iteration, + 32*D^3 where warm-started"}
 
 
 SCREEN_PER_SITE = 1e-4

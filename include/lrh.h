@@ -184,6 +184,15 @@ typedef struct {
                                     and certify (FP64) only if the estimate is >= target[i] -
                                     screen_tol on every targeted instance; the run's last
                                     checkpoint is always certified.  0: certify every checkpoint */
+    int32_t cold_start;          /* 0 (default): the FP32 eigensolve of a region of 3 or 4 sites
+                                    starts from the eigenvectors its previous pass stored (one
+                                    D x D basis per region and instance on the device, the
+                                    identity at creation): theta_e is first rotated into that
+                                    basis, after one Newton-Schulz step makes it unitary to
+                                    rounding, and Jacobi sweeps only what theta_e moved since.
+                                    Nonzero: every eigensolve starts from the identity and the
+                                    stored bases are neither read nor written.  Either way the
+                                    eigensolve stops at the same threshold.                   */
 } lrh_options;
 
 typedef struct lrh_problem lrh_problem;
@@ -215,6 +224,7 @@ typedef struct {
                                      ||offdiag||_F^2 <= 1e-12 ||theta||_F^2                      */
     int32_t n_sites;
     int32_t kappa_G;              /* max over sites i of |{e->f : i in f}| (Thm 6; Delta_G at level 1) */
+    int64_t warm_bytes;           /* device bytes of the stored eigenbases (lrh_options.cold_start) */
 } lrh_info;
 
 /* Parameter rules of the convergence theorems for a target error density eps (per site):
@@ -355,7 +365,8 @@ int lrh_set_class_mode(lrh_problem* p, int32_t mode);
 int lrh_selftest_barrier_timeout(lrh_problem* p);
 
 /* Checkpoint / resume.  The state is the iteration scalars (theta_k, step counter, beta,
- * L_hat, alpha, iteration parity), nu, zeta, nu_best and q_best, packed into one host buffer
+ * L_hat, alpha, iteration parity), nu, zeta, nu_best, q_best and the stored eigenbases of the
+ * regions of 3 and 4 sites (lrh_options.cold_start; lrh_info.warm_bytes), packed into one host buffer
  * of lrh_state_bytes() bytes; lrh_set_state accepts only a buffer from a problem with the same
  * instance count, message layout and variant.  Resuming from a saved state and iterating gives
  * bit-identical messages to an uninterrupted run.  Both synchronise. */
@@ -398,8 +409,9 @@ int lrh_level1_eval_noalloc(int32_t n_sites, int32_t n_edges, const int32_t* edg
 /* Theorem parameter rules (see lrh_params) for target error density eps > 0; host only. */
 int lrh_theorem_parameters(const lrh_problem* p, double eps, double R, double c_frac, lrh_params* out);
 
-/* Zero nu, zeta, nu_best (Alg. 1 / Alg. 2 initialisation), set theta = 1, t = 0 and
- * q_best = -inf.  Stream-ordered. */
+/* Zero nu, zeta, nu_best (Alg. 1 / Alg. 2 initialisation), set theta = 1, t = 0,
+ * q_best = -inf and every stored eigenbasis to the identity: the state at creation.
+ * Stream-ordered. */
 int lrh_reset(lrh_problem* p);
 
 /* Run the schedule of lrh_options from the current multipliers: Alg. 2 runs one stage per

@@ -70,6 +70,7 @@ class Options(C.Structure):
         ("tune_cache", C.c_char_p),
         ("target", C.POINTER(C.c_double)),
         ("screen_tol", C.c_double),
+        ("cold_start", C.c_int32),
     ]
 
 
@@ -95,6 +96,7 @@ class Info(C.Structure):
         ("sweep_capped", C.c_uint64 * 8),
         ("n_sites", C.c_int32),
         ("kappa_G", C.c_int32),
+        ("warm_bytes", C.c_int64),
     ]
 
 

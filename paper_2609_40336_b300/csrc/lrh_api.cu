@@ -127,6 +127,7 @@ struct lrh_problem {
     int64_t halo_send_chunks = 0, halo_recv_chunks = 0;
     bool halo_ready = false;
     bool halo_passed = false;   // lrh_halo_pass ran and lrh_halo_update has not yet
+    int64_t warm_elems = 0;     // complex entries of the stored eigenbases (P.warm)
 
     template <typename T>
     int dalloc(T** ptr, int64_t count) {
@@ -195,7 +196,19 @@ int push_state(lrh_problem* p, bool set_theta_t, double theta, double t) {
     const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
     const int cert = o.cert_sweeps > 0 ? o.cert_sweeps : 40;
     LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), theta, t, set_theta_t ? 1 : 0, o.beta,
-                            1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, cert, p->stream));
+                            1.0 / p->lhat_eff, o.alpha, degen, o.variant, o.step_rule, sweeps, cert,
+                            o.cold_start ? 1 : 0, p->stream));
+    return LRH_OK;
+}
+
+// every stored eigenbasis back to the identity (the state at creation)
+int reset_warm(lrh_problem* p) {
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
+        const int k = p->class_k[c];
+        if (p->P.warm && p->P.warm_off[k] >= 0)
+            LRH_CK(launch_warm_identity(p->P.warm + p->P.warm_off[k], (int64_t)p->n_inst * p->class_count[c], 1 << k,
+                                        p->stream));
+    }
     return LRH_OK;
 }
 
@@ -922,6 +935,19 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         if (p->class_k[c] == 3 || p->class_k[c] == 4) p->class_block[c] = LRH_SHAPE_BLOCKS + 128;   // 2x2-block layout
     }
     p->P.tc_backtransform = 0;
+    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites), the identity at first
+    for (int k = 0; k < kClassSlots; ++k) P.warm_off[k] = -1;
+    for (size_t c = 0; c < p->class_k.size(); ++c) {
+        const int k = p->class_k[c];
+        if (k != 3 && k != 4) continue;
+        P.warm_off[k] = p->warm_elems;
+        p->warm_elems += NI * p->class_count[c] * ((int64_t)1 << (2 * k));
+    }
+    if (p->warm_elems > 0) {
+        if ((rc = p->dalloc(&P.warm, p->warm_elems))) return rc;
+        if ((rc = reset_warm(p))) return rc;
+        LRH_CK(cudaStreamSynchronize(p->stream));
+    }
     if (maxk == 8) {   // scratch slots of the D = 256 pass (theta overflow, V, rho, rotation log)
         int slots = 0;
         LRH_CK(big_launch_slots(&slots));
@@ -982,6 +1008,7 @@ int lrh_get_info(const lrh_problem* p, lrh_info* info) {
     }
     info->n_sites = p->n_sites;
     info->kappa_G = p->kappa;
+    info->warm_bytes = (int64_t)sizeof(float2) * p->warm_elems;
     info->concurrent_classes = (p->fused && p->persist_grid > 0) ? 2 : (p->concurrent ? 1 : 0);
     info->loop = effective_loop(p);
     info->persistent_grid = p->persist_grid;
@@ -1227,6 +1254,7 @@ struct StateHeader {
     int32_t variant;
     int64_t msg_elems;
     int64_t iteration;
+    int64_t warm_elems;
     lrh::IterState st;
 };
 constexpr uint64_t kStateMagic = 0x3154415453485231ull;
@@ -1235,7 +1263,7 @@ constexpr uint64_t kStateMagic = 0x3154415453485231ull;
 int64_t lrh_state_bytes(const lrh_problem* p) {
     if (!p) return 0;
     return (int64_t)sizeof(StateHeader) + 3 * (int64_t)sizeof(float2) * p->n_inst * p->msg_elems +
-           (int64_t)sizeof(double) * p->n_inst;
+           (int64_t)sizeof(double) * p->n_inst + (int64_t)sizeof(float2) * p->warm_elems;
 }
 
 int lrh_get_state(lrh_problem* p, void* buf, int64_t bytes) {
@@ -1248,6 +1276,7 @@ int lrh_get_state(lrh_problem* p, void* buf, int64_t bytes) {
     h.variant = p->opt.variant;
     h.msg_elems = p->msg_elems;
     h.iteration = p->iteration;
+    h.warm_elems = p->warm_elems;
     char* out = static_cast<char*>(buf);
     const size_t m = sizeof(float2) * p->n_inst * p->msg_elems;
     LRH_CK(cudaMemcpyAsync(&h.st, p->P.st, sizeof(IterState), cudaMemcpyDeviceToHost, p->stream));
@@ -1258,6 +1287,9 @@ int lrh_get_state(lrh_problem* p, void* buf, int64_t bytes) {
         LRH_CK(cudaMemcpyAsync(q + 2 * m, p->P.nu_best, m, cudaMemcpyDeviceToHost, p->stream));
     }
     LRH_CK(cudaMemcpyAsync(q + 3 * m, p->P.q_best, sizeof(double) * p->n_inst, cudaMemcpyDeviceToHost, p->stream));
+    if (p->warm_elems)
+        LRH_CK(cudaMemcpyAsync(q + 3 * m + sizeof(double) * p->n_inst, p->P.warm, sizeof(float2) * p->warm_elems,
+                               cudaMemcpyDeviceToHost, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
     std::memcpy(out, &h, sizeof(h));
     return LRH_OK;
@@ -1268,7 +1300,8 @@ int lrh_set_state(lrh_problem* p, const void* buf, int64_t bytes) {
     if (bytes != lrh_state_bytes(p)) return fail(LRH_EINVAL, "bytes must equal lrh_state_bytes()");
     StateHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (h.magic != kStateMagic || h.n_inst != p->n_inst || h.msg_elems != p->msg_elems || h.variant != p->opt.variant)
+    if (h.magic != kStateMagic || h.n_inst != p->n_inst || h.msg_elems != p->msg_elems || h.variant != p->opt.variant ||
+        h.warm_elems != p->warm_elems)
         return fail(LRH_EINVAL, "state does not belong to a problem of this shape and variant");
     DeviceGuard dg(p->device);
     const char* q = static_cast<const char*>(buf) + sizeof(StateHeader);
@@ -1280,6 +1313,9 @@ int lrh_set_state(lrh_problem* p, const void* buf, int64_t bytes) {
         LRH_CK(cudaMemcpyAsync(p->P.nu_best, q + 2 * m, m, cudaMemcpyHostToDevice, p->stream));
     }
     LRH_CK(cudaMemcpyAsync(p->P.q_best, q + 3 * m, sizeof(double) * p->n_inst, cudaMemcpyHostToDevice, p->stream));
+    if (p->warm_elems)
+        LRH_CK(cudaMemcpyAsync(p->P.warm, q + 3 * m + sizeof(double) * p->n_inst, sizeof(float2) * p->warm_elems,
+                               cudaMemcpyHostToDevice, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
     p->iteration = h.iteration;
     return LRH_OK;
@@ -1354,10 +1390,37 @@ int time_adaptive(lrh_problem* p, float min_ms, F fn, float* ms) {
 
 extern "C" {
 
+namespace {
+int autotune_impl(lrh_problem* p, const char* cache_path, int32_t flags);
+}
+
 int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
     if (p->has_ghost) return fail(LRH_EUNSUPPORTED, "problems with ghost regions iterate with lrh_halo_pass / lrh_halo_update");
     DeviceGuard dg(p->device);
+    // the timing passes rewrite the stored eigenbases: keep a copy and put it back, so that a
+    // run gives the same results whether or not it was tuned
+    float2* keep = nullptr;
+    const size_t wb = sizeof(float2) * (size_t)p->warm_elems;
+    if (wb) {
+        if (cudaMalloc(&keep, wb) != cudaSuccess) return fail(LRH_ENOMEM, "cudaMalloc (copy of the stored eigenbases)");
+        if (cudaMemcpyAsync(keep, p->P.warm, wb, cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+            cudaFree(keep);
+            return fail(LRH_ECUDA, "copy of the stored eigenbases");
+        }
+    }
+    int rc = autotune_impl(p, cache_path, flags);
+    if (keep) {
+        const cudaError_t e1 = cudaMemcpyAsync(p->P.warm, keep, wb, cudaMemcpyDeviceToDevice, p->stream);
+        const cudaError_t e2 = cudaStreamSynchronize(p->stream);
+        cudaFree(keep);
+        if (!rc && (e1 != cudaSuccess || e2 != cudaSuccess)) rc = fail(LRH_ECUDA, "restoring the stored eigenbases");
+    }
+    return rc;
+}
+
+namespace {
+int autotune_impl(lrh_problem* p, const char* cache_path, int32_t flags) {
     int sms = 0;
     LRH_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
     const bool force = (flags & 1) != 0;
@@ -1500,6 +1563,7 @@ int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags) {
     drop_graphs(p);   // captured launch shapes are stale
     return read_err(p);
 }
+}  // namespace
 
 int lrh_set_launch_shape(lrh_problem* p, int32_t k_sites, int32_t block) {
     if (!p) return fail(LRH_EINVAL, "NULL problem");
@@ -1600,6 +1664,7 @@ int lrh_reset(lrh_problem* p) {
     LRH_CK(cudaMemsetAsync(p->P.best_flag, 0, sizeof(int32_t) * p->n_inst, p->stream));
     int rc = push_state(p, true, 1.0, 0.0);
     if (rc) return rc;
+    if ((rc = reset_warm(p))) return rc;
     LRH_CK(cudaStreamSynchronize(p->stream));   // the host vector above must outlive the copy
     return LRH_OK;
 }
@@ -1614,7 +1679,7 @@ int estimate_q32(lrh_problem* p, double* out) {
     const int sweeps = o.max_sweeps > 0 ? o.max_sweeps : 15;
     const int cert = o.cert_sweeps > 0 ? o.cert_sweeps : 40;
     LRH_CK(launch_set_state(p->P, (int)(p->iteration & 1), 0.0, 0.0, 0, o.beta, 1.0 / p->lhat_eff, o.alpha, degen,
-                            LRH_SUBGRADIENT, o.step_rule, sweeps, cert, p->stream));
+                            LRH_SUBGRADIENT, o.step_rule, sweeps, cert, 1, p->stream));   // cold: stored bases untouched
     PassIO io{};
     io.nu_in = p->P.nu;
     io.rho_out = p->P.rho;

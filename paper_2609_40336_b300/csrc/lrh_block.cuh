@@ -144,6 +144,80 @@ __device__ __forceinline__ void rot_fast(float app, float aqq, float br, float b
     dnew.y = aqq + tb;
 }
 
+// Warm start of a region's eigensolve from a stored basis V (row s of V in (vr, vi), every lane
+// of the group; the stored V is the previous pass's eigenvectors, unitary to FP32 rounding).
+// One Newton-Schulz step restores unitarity to rounding, V <- V (3 I - V^H V) / 2, so that the
+// defect does not build up over the passes; then theta <- V^H theta V, which has theta's
+// eigenvalues and is nearly diagonal when theta moved little since V was formed.  Row s of theta
+// comes in (ar, ai) and leaves as row s of V^H theta V; (vr, vi) leave as row s of the corrected
+// V.  Staging: Va and Ga, two D x LD complex arrays of the group (the W / rho staging area).
+// Every lane of the warp calls it (warp barriers inside).
+template <int D, int LD>
+__device__ __forceinline__ void warm_basis(float2* Va, float2* Ga, const int s, float (&ar)[D], float (&ai)[D],
+                                           float (&vr)[D], float (&vi)[D]) {
+    float xr[D], xi[D];
+    auto put_row = [&](float2* A, const float (&yr)[D], const float (&yi)[D]) {
+        float4* row = reinterpret_cast<float4*>(A + s * LD);
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) row[c] = make_float4(yr[2 * c], yi[2 * c], yr[2 * c + 1], yi[2 * c + 1]);
+    };
+    // x += (a_r + i a_i) * row c of A
+    auto axpy_row = [&](const float2* A, const int c, const float a_r, const float a_i) {
+        const float4* row = reinterpret_cast<const float4*>(A + c * LD);
+#pragma unroll
+        for (int t = 0; t < D / 2; ++t) {
+            const float4 y = row[t];
+            xr[2 * t] = fmaf(a_r, y.x, fmaf(-a_i, y.y, xr[2 * t]));
+            xi[2 * t] = fmaf(a_r, y.y, fmaf(a_i, y.x, xi[2 * t]));
+            xr[2 * t + 1] = fmaf(a_r, y.z, fmaf(-a_i, y.w, xr[2 * t + 1]));
+            xi[2 * t + 1] = fmaf(a_r, y.w, fmaf(a_i, y.z, xi[2 * t + 1]));
+        }
+    };
+    auto zero_x = [&]() {
+#pragma unroll
+        for (int t = 0; t < D; ++t) { xr[t] = 0.f; xi[t] = 0.f; }
+    };
+    // G = V^H V, row s: sum_c conj(V[c][s]) V[c][:]
+    put_row(Va, vr, vi);
+    __syncwarp();
+    zero_x();
+#pragma unroll 4
+    for (int c = 0; c < D; ++c) {
+        const float2 a = Va[c * LD + s];
+        axpy_row(Va, c, a.x, -a.y);
+    }
+    put_row(Ga, xr, xi);
+    __syncwarp();
+    // V <- (3 V - V G) / 2, row s: sum_c V[s][c] G[c][:]
+    zero_x();
+#pragma unroll
+    for (int c = 0; c < D; ++c) axpy_row(Ga, c, vr[c], vi[c]);
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        vr[t] = fmaf(1.5f, vr[t], -0.5f * xr[t]);
+        vi[t] = fmaf(1.5f, vi[t], -0.5f * xi[t]);
+    }
+    __syncwarp();   // every lane has read Va (G) and Ga (V G)
+    put_row(Va, vr, vi);
+    __syncwarp();
+    // T = theta V, row s: sum_c theta[s][c] V[c][:]
+    zero_x();
+#pragma unroll
+    for (int c = 0; c < D; ++c) axpy_row(Va, c, ar[c], ai[c]);
+    put_row(Ga, xr, xi);
+    __syncwarp();
+    // V^H T, row s: sum_c conj(V[c][s]) T[c][:]
+    zero_x();
+#pragma unroll 4
+    for (int c = 0; c < D; ++c) {
+        const float2 a = Va[c * LD + s];
+        axpy_row(Ga, c, a.x, -a.y);
+    }
+#pragma unroll
+    for (int t = 0; t < D; ++t) { ar[t] = xr[t]; ai[t] = xi[t]; }
+    __syncwarp();   // the staging is free again
+}
+
 template <int D, int BLOCK>
 __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const PassIO& io,
                                                      const int32_t* __restrict__ cls, const int32_t count, const int k,
@@ -170,8 +244,14 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     const int max_sweeps = P.st->max_sweeps;
     const Thetas T = pass_thetas(P, io);
 
-    // ---- assemble row s and store its upper part (the matrix is exactly Hermitian)
+    // ---- assemble row s (with a stored basis: of V^H theta V) and store its upper part (the
+    //      matrix is exactly Hermitian)
     RegionInfo R;
+    float vr[D], vi[D];   // row s of the starting basis (the identity, or the stored V)
+    const bool warm = P.warm != nullptr && P.warm_off[k] >= 0 && !P.st->cold;   // uniform over the launch
+    float4* wrow = (warm && valid)
+        ? reinterpret_cast<float4*>(P.warm + P.warm_off[k] + unit * (int64_t)(D * D) + (int64_t)s * D)
+        : nullptr;
     {
         float ar[D], ai[D];
         if (valid) {
@@ -181,6 +261,20 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
             R = RegionInfo{-1, -1, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
+        }
+        if (wrow) {
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c) {
+                const float4 v = wrow[c];
+                vr[2 * c] = v.x; vi[2 * c] = v.y; vr[2 * c + 1] = v.z; vi[2 * c + 1] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) { vr[c] = c == s ? 1.f : 0.f; vi[c] = 0.f; }
+        }
+        if (warm) {
+            float2* Va = reinterpret_cast<float2*>(base);
+            warm_basis<D, LD>(Va, Va + D * LD, s, ar, ai, vr, vi);
         }
 #pragma unroll
         for (int c = 0; c < D; ++c)
@@ -243,11 +337,15 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     bool active = true;
 
     // V takes each round's rotations one round late (so that their dependent chain overlaps V's
-    // independent FMAs); it starts as the identity with its columns in inverse tournament order,
-    // so that the first, rotation-free step (y[c] = x[rr_src(c)]) restores the identity
-    float vr[D], vi[D];
+    // independent FMAs); it starts as the starting basis with its columns in inverse tournament
+    // order, so that the first, rotation-free step (y[c] = x[rr_src(c)]) restores it
+    {
+        float tr_[D], ti_[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { vr[c] = (c == rr_src(s, D)) ? 1.f : 0.f; vi[c] = 0.f; }
+        for (int c = 0; c < D; ++c) { tr_[c] = vr[c]; ti_[c] = vi[c]; }
+#pragma unroll
+        for (int c = 0; c < D; ++c) { vr[rr_src(c, D)] = tr_[c]; vi[rr_src(c, D)] = ti_[c]; }
+    }
     if (s < 2 * n) prm2[s] = RotC<float>{1.f, 0.f, 0.f, 0.f};
     __syncwarp();
 
@@ -366,7 +464,21 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
     vstep(prm2 + n * (par ^ 1), vr, vi, ur, ui);
 #pragma unroll
     for (int c = 0; c < D; ++c) { vr[c] = ur[c]; vi[c] = ui[c]; }
-    // the slots are back in natural order: lambda_s on the diagonal, row s of V in (vr, vi)
+    // the slots are back in natural order: lambda_s on the diagonal, row s of V in (vr, vi),
+    // stored as the next pass's starting basis (the identity when the region's V is not finite,
+    // so that a non-finite input does not outlive the pass that saw it)
+    if (warm) {
+        bool fin = true;
+#pragma unroll
+        for (int c = 0; c < D; ++c) fin = fin && isfinite(vr[c]) && isfinite(vi[c]);
+        const bool bad = group_sum<D>(fin ? 0.f : 1.f) > 0.f;   // every lane of the warp
+        if (wrow) {
+#pragma unroll
+            for (int c = 0; c < D / 2; ++c)
+                wrow[c] = bad ? make_float4(2 * c == s ? 1.f : 0.f, 0.f, 2 * c + 1 == s ? 1.f : 0.f, 0.f)
+                              : make_float4(vr[2 * c], vi[2 * c], vr[2 * c + 1], vi[2 * c + 1]);
+        }
+    }
     const float lam = cur[eidx<D>(s, s)].x;
     const float lmin = group_min<D>(lam);
     float wgt, F;

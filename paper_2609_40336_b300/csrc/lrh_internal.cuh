@@ -51,6 +51,8 @@ struct IterState {
     int32_t step_rule;
     int32_t max_sweeps;
     int32_t cert_sweeps;   // sweep cap of the FP64 certification Jacobi
+    int32_t cold;          // nonzero: eigensolves start from the identity (stored bases unused)
+    int32_t pad_;
 };
 
 // Inputs and outputs of one region pass.  A "pending" pass first applies the previous
@@ -153,6 +155,11 @@ struct DevProblem {
     int64_t big_slot;        // complex entries per slot
     int32_t big_slots;       // slots (= CTAs of a D = 256 launch)
     int32_t big_log_sweeps;  // sweeps the rotation log of a slot holds (the D = 256 sweep cap)
+    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites): class k's unit u
+    // (= instance * count + position in the class list) owns the D x D row-major complex matrix
+    // at warm + warm_off[k] + u D^2 (warm_off[k] < 0: no stored basis for the class)
+    float2* warm;
+    int64_t warm_off[kClassSlots];
 };
 
 // Record `msg` as the thread-local detail returned by lrh_last_error; returns `code`.
@@ -203,7 +210,9 @@ cudaError_t launch_update(const DevProblem& P, int par, int mode, cudaStream_t s
 cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_best, cudaStream_t s);
 cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double t, int set_theta_t,
                              double beta, double inv_lhat, double alpha, double degen_tol,
-                             int variant, int step_rule, int max_sweeps, int cert_sweeps, cudaStream_t s);
+                             int variant, int step_rule, int max_sweeps, int cert_sweeps, int cold, cudaStream_t s);
+// every stored eigenbasis (n_mats matrices of D x D) set to the identity
+cudaError_t launch_warm_identity(float2* warm, int64_t n_mats, int D, cudaStream_t s);
 cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t s);
 
 // Adjoint (lrh_vjp.cu): theta_bar per region for the classes, then nu_bar and term cotangents.

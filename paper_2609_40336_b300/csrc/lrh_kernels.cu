@@ -24,6 +24,7 @@
 #include "lrh_device.cuh"
 #include "lrh_block.cuh"
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
@@ -664,7 +665,7 @@ __global__ void __launch_bounds__(kReduce) reduce_kernel(const DevProblem P, con
 
 __global__ void set_state_kernel(IterState* st, int par, double theta, double t, int set_theta_t, double beta,
                                  double inv_lhat, double alpha, double degen_tol, int variant, int step_rule,
-                                 int max_sweeps, int cert_sweeps) {
+                                 int max_sweeps, int cert_sweeps, int cold) {
     if (set_theta_t) {
         st->theta[par] = theta;
         st->t[par] = t;
@@ -679,6 +680,18 @@ __global__ void set_state_kernel(IterState* st, int par, double theta, double t,
     st->step_rule = step_rule;
     st->max_sweeps = max_sweeps;
     st->cert_sweeps = cert_sweeps;
+    st->cold = cold;
+}
+
+__global__ void warm_identity_kernel(float4* w, int64_t n_pairs_total, int D) {
+    // entries 2j, 2j+1 of the flattened matrices (D even): (i, c) and (i, c + 1)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t per = (int64_t)D * D / 2;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_pairs_total; j += stride) {
+        const int64_t e = 2 * (j % per);
+        const int64_t i = e / D, c = e % D;
+        w[j] = make_float4(i == c ? 1.f : 0.f, 0.f, i == c + 1 ? 1.f : 0.f, 0.f);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1058,9 +1071,17 @@ cudaError_t launch_reduce(const DevProblem& P, const double* vals, int track_bes
 
 cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double t, int set_theta_t, double beta,
                              double inv_lhat, double alpha, double degen_tol, int variant, int step_rule,
-                             int max_sweeps, int cert_sweeps, cudaStream_t s) {
+                             int max_sweeps, int cert_sweeps, int cold, cudaStream_t s) {
     set_state_kernel<<<1, 1, 0, s>>>(P.st, par, theta, t, set_theta_t, beta, inv_lhat, alpha, degen_tol, variant,
-                                     step_rule, max_sweeps, cert_sweeps);
+                                     step_rule, max_sweeps, cert_sweeps, cold);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_identity(float2* warm, int64_t n_mats, int D, cudaStream_t s) {
+    const int64_t pairs = n_mats * D * D / 2;
+    if (pairs <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((pairs + 255) / 256, 148 * 16);
+    warm_identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(reinterpret_cast<float4*>(warm), pairs, D);
     return cudaGetLastError();
 }
 

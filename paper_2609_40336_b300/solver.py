@@ -117,7 +117,9 @@ class Solver:
     graph), "persistent" (one cooperative launch per call, classes of <= 4 sites) or "auto" (the
     autotuner's choice); ``use_graph`` True / False is shorthand for "graph" / "eager".
     ``betas``, ``iters_per_stage``, ``certify_every`` and ``deadline_s`` describe the schedule
-    that ``solve`` runs inside the library.
+    that ``solve`` runs inside the library.  ``cold_start`` True makes every eigensolve of the
+    regions of 3 and 4 sites start from the identity instead of the basis their previous pass
+    stored (lrh_options.cold_start).
     """
 
     def __init__(self, problem, variant: str = "nesterov", beta: float = 1.0, lhat: Optional[float] = None,
@@ -125,7 +127,7 @@ class Solver:
                  max_sweeps: int = 15, use_graph: Optional[bool] = None, loop: str = "auto", stream=None,
                  cert_sweeps: int = 0, betas: Optional[Sequence[float]] = None, iters_per_stage: int = 0,
                  certify_every: int = 0, deadline_s: float = 0.0, tune_cache: Optional[str] = None,
-                 targets: Optional[Sequence[float]] = None, screen_tol: float = 0.0):
+                 targets: Optional[Sequence[float]] = None, screen_tol: float = 0.0, cold_start: bool = False):
         self._lib = L.load()
         self._h = C.c_void_p(0)
         desc, self._keep = marshal(problem.n_sites, problem.regions, problem.term_sites, problem.term_mats,
@@ -135,7 +137,8 @@ class Solver:
                               beta=float(beta), lhat=float(lhat) if lhat else 0.0, degen_tol=float(degen_tol),
                               max_sweeps=int(max_sweeps), loop=_loop_code(loop, use_graph),
                               cert_sweeps=int(cert_sweeps), iters_per_stage=int(iters_per_stage),
-                              certify_every=int(certify_every), deadline_s=float(deadline_s))
+                              certify_every=int(certify_every), deadline_s=float(deadline_s),
+                              cold_start=1 if cold_start else 0)
         self._set_betas(betas)
         self.n_instances = int(desc.n_instances)
         self._set_targets(targets)
@@ -183,7 +186,7 @@ class Solver:
                     concurrent_classes=int(inf.concurrent_classes), loop=_LOOP_NAMES[inf.loop],
                     persistent_grid=inf.persistent_grid, persistent_tiles=inf.persistent_tiles,
                     sweep_capped=[int(x) for x in inf.sweep_capped[:nc]], n_sites=inf.n_sites,
-                    kappa_G=inf.kappa_G)
+                    kappa_G=inf.kappa_G, warm_bytes=int(inf.warm_bytes))
 
     def pairs(self):
         par = np.zeros(self.n_pairs, np.int32)
@@ -225,6 +228,7 @@ class Solver:
         for k in ("alpha", "beta", "degen_tol"):
             if k in kw: setattr(o, k, float(kw.pop(k)))
         if "max_sweeps" in kw: o.max_sweeps = int(kw.pop("max_sweeps"))
+        if "cold_start" in kw: o.cold_start = 1 if kw.pop("cold_start") else 0
         if "use_graph" in kw: o.loop = _loop_code("auto", kw.pop("use_graph"))
         if "loop" in kw: o.loop = _loop_code(kw.pop("loop"), None)
         if kw:
@@ -288,7 +292,8 @@ class Solver:
         return out
 
     def reset(self) -> None:
-        """nu = zeta = nu_best = 0, theta = 1, t = 0, q_best = -inf (lrh_reset)."""
+        """nu = zeta = nu_best = 0, theta = 1, t = 0, q_best = -inf, stored eigenbases = identity
+        (lrh_reset)."""
         L.check(self._lib.lrh_reset(self._h), "lrh_reset")
 
     def solve(self, max_records: int = 0) -> dict:

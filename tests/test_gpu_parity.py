@@ -235,7 +235,13 @@ def test_autotune_chooses_valid_shapes_and_uses_cache(tmp_path):
     s = Solver(p, beta=4.0)
     s.step(5)
     s.evaluate()
-    g0, v0 = s.messages("grad"), s.region_values("last")
+    # the same passes without tuning: the second evaluation starts its 16 x 16 eigensolves from
+    # the bases the first stored, and tuning must leave those bases as it found them
+    r = Solver(p, beta=4.0)
+    r.step(5)
+    r.evaluate()
+    r.evaluate()
+    g0, v0 = r.messages("grad"), r.region_values("last")
     cache = tmp_path / "tune.jsonl"
     before = s.info()["class_block"]
     shapes = s.autotune(str(cache), force=True)
