@@ -667,10 +667,19 @@ def kernel_source_hash(sources=None):
     return h.hexdigest()[:16]
 
 
+def shape_family(shape):
+    """Layout of a launch shape: the lane, 2x2-block and warp-per-region layouts (the CTA size,
+    64 / 128 / 256 threads, only changes which CTA runs a region, not what a region reads or
+    writes)."""
+    if shape is None:
+        return None
+    return "t4" if shape < 0 else ("lane" if shape < 4096 else ("blocks" if shape < 8192 else "warp16"))
+
+
 def recorded_traffic(shape):
     """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/traffic.json),
     only while the sources that kernel is built from are the ones that capture measured and the
-    capture was of the same launch shape."""
+    capture was of the same layout (any CTA size of it)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -678,7 +687,7 @@ def recorded_traffic(shape):
         rec = json.load(f).get(WL_KEY)
     if not rec or rec.get("kernel_sources_sha256_16") != kernel_source_hash(rec.get("sources")):
         return None
-    if rec.get("launch_shape") is not None and rec["launch_shape"] != shape:
+    if rec.get("launch_shape") is not None and shape_family(rec["launch_shape"]) != shape_family(shape):
         return None
     return rec
 

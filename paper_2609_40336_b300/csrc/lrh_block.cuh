@@ -144,6 +144,84 @@ __device__ __forceinline__ void rot_fast(float app, float aqq, float br, float b
     dnew.y = aqq + tb;
 }
 
+// Row s of theta_e = h_e - sum_children 1 (x) m + sum_parents m, with the message entries of
+// pass_entry (the same subtractions and additions in the same order as assemble_row_io, so the
+// same values).  A child f of k_f sites touches D_f of the row's D entries: its message row
+// a = pext(s, M_f) is gathered once (D_f entries, float4 loads) and subtracted at the columns
+// rest | (the b-th submask of M_f) through the lane's row of `rowbuf` in shared memory, instead of
+// an unrolled loop over all D columns that issues its loads for every column.
+template <int D, int LD>
+__device__ __forceinline__ void assemble_row_blk(const DevProblem& P, const RegionInfo& R, int inst, int s,
+                                                 const PassIO& io, const Thetas& T, float2* rowbuf,
+                                                 float (&ar)[D], float (&ai)[D]) {
+    if (R.h_off >= 0) {
+        const float4* hrow = reinterpret_cast<const float4*>(P.h32 + (int64_t)inst * P.h_elems + R.h_off + (int64_t)s * D);
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) {
+            const float4 v = hrow[c];
+            ar[2 * c] = v.x; ai[2 * c] = v.y; ar[2 * c + 1] = v.z; ai[2 * c + 1] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
+    }
+    const int64_t mbase = (int64_t)inst * P.msg_elems;
+    const int64_t rbase = (int64_t)inst * P.rho_elems;
+    if (R.child_end > R.child_begin) {
+        float4* row4 = reinterpret_cast<float4*>(rowbuf + s * LD);
+        float2* row = rowbuf + s * LD;
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) row4[c] = make_float4(ar[2 * c], ai[2 * c], ar[2 * c + 1], ai[2 * c + 1]);
+        for (int q = R.child_begin; q < R.child_end; ++q) {
+            const PairInfo pi = P.child_info[q];
+            const int M = pi.mask;
+            const int Df = 1 << pi.kf;
+            const int rest = s & ~M;
+            const int64_t x0 = (int64_t)pext_bits(s, M) * Df;
+            int sub = 0;   // submasks of M in increasing order: column rest | sub holds entry b
+            for (int b = 0; b < Df; b += 2) {
+                const float4 m = pass_entry2(io, T, mbase + pi.off + x0 + b, rbase + pi.child_rho + x0 + b, false);
+                const int c0 = rest | sub;
+                sub = ((sub | ~M) + 1) & M;
+                const int c1 = rest | sub;
+                sub = ((sub | ~M) + 1) & M;
+                float2 v0 = row[c0], v1 = row[c1];
+                v0.x -= m.x; v0.y -= m.y;
+                v1.x -= m.z; v1.y -= m.w;
+                row[c0] = v0;
+                row[c1] = v1;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < D / 2; ++c) {
+            const float4 v = row4[c];
+            ar[2 * c] = v.x; ai[2 * c] = v.y; ar[2 * c + 1] = v.z; ai[2 * c + 1] = v.w;
+        }
+    }
+    for (int q = R.parent_begin; q < R.parent_end; ++q) {
+        const PairInfo pi = P.parent_info[q];
+        if constexpr (D <= 8) {   // float4 gathers; at D = 16 the unrolled loads would crowd the registers
+#pragma unroll
+            for (int c = 0; c < D; c += 2) {
+                const int64_t x = (int64_t)s * D + c;
+                const float4 m = pass_entry2(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                ar[c] += m.x;
+                ai[c] += m.y;
+                ar[c + 1] += m.z;
+                ai[c + 1] += m.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const int64_t x = (int64_t)s * D + c;
+                const float2 m = pass_entry(io, T, mbase + pi.off + x, rbase + R.rho_off + x, true);
+                ar[c] += m.x;
+                ai[c] += m.y;
+            }
+        }
+    }
+}
+
 // Warm start of a region's eigensolve from a stored basis V (row s of V in (vr, vi), every lane
 // of the group; the stored V is the previous pass's eigenvectors, unitary to FP32 rounding).
 // One Newton-Schulz step restores unitarity to rounding, V <- V (3 I - V^H V) / 2, so that the
@@ -181,26 +259,35 @@ __device__ __forceinline__ void warm_basis(float2* Va, float2* Ga, const int s, 
     put_row(Va, vr, vi);
     __syncwarp();
     zero_x();
-#pragma unroll 4
+#pragma unroll 2
     for (int c = 0; c < D; ++c) {
         const float2 a = Va[c * LD + s];
         axpy_row(Va, c, a.x, -a.y);
     }
     put_row(Ga, xr, xi);
     __syncwarp();
-    // V <- (3 V - V G) / 2, row s: sum_c V[s][c] G[c][:]
+    // V <- (3 V - V G) / 2, row s: 1.5 V[s][:] - 0.5 sum_c V[s][c] G[c][:]
     zero_x();
-#pragma unroll
-    for (int c = 0; c < D; ++c) axpy_row(Ga, c, vr[c], vi[c]);
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-        vr[t] = fmaf(1.5f, vr[t], -0.5f * xr[t]);
-        vi[t] = fmaf(1.5f, vi[t], -0.5f * xi[t]);
+#pragma unroll 2
+    for (int c = 0; c < D; ++c) {
+        const float2 a = Va[s * LD + c];
+        axpy_row(Ga, c, a.x, a.y);
     }
-    __syncwarp();   // every lane has read Va (G) and Ga (V G)
-    put_row(Va, vr, vi);
+    {
+        const float4* row = reinterpret_cast<const float4*>(Va + s * LD);
+#pragma unroll
+        for (int t = 0; t < D / 2; ++t) {
+            const float4 y = row[t];
+            xr[2 * t] = fmaf(1.5f, y.x, -0.5f * xr[2 * t]);
+            xi[2 * t] = fmaf(1.5f, y.y, -0.5f * xi[2 * t]);
+            xr[2 * t + 1] = fmaf(1.5f, y.z, -0.5f * xr[2 * t + 1]);
+            xi[2 * t + 1] = fmaf(1.5f, y.w, -0.5f * xi[2 * t + 1]);
+        }
+    }
+    __syncwarp();   // every lane has read Va (G, V G) and Ga (V G)
+    put_row(Va, xr, xi);
     __syncwarp();
-    // T = theta V, row s: sum_c theta[s][c] V[c][:]
+    // T = theta V, row s: sum_c theta[s][c] V[c][:] (theta's row in registers: unrolled)
     zero_x();
 #pragma unroll
     for (int c = 0; c < D; ++c) axpy_row(Va, c, ar[c], ai[c]);
@@ -208,13 +295,21 @@ __device__ __forceinline__ void warm_basis(float2* Va, float2* Ga, const int s, 
     __syncwarp();
     // V^H T, row s: sum_c conj(V[c][s]) T[c][:]
     zero_x();
-#pragma unroll 4
+#pragma unroll 2
     for (int c = 0; c < D; ++c) {
         const float2 a = Va[c * LD + s];
         axpy_row(Ga, c, a.x, -a.y);
     }
 #pragma unroll
     for (int t = 0; t < D; ++t) { ar[t] = xr[t]; ai[t] = xi[t]; }
+    {
+        const float4* row = reinterpret_cast<const float4*>(Va + s * LD);
+#pragma unroll
+        for (int t = 0; t < D / 2; ++t) {
+            const float4 y = row[t];
+            vr[2 * t] = y.x; vi[2 * t] = y.y; vr[2 * t + 1] = y.z; vi[2 * t + 1] = y.w;
+        }
+    }
     __syncwarp();   // the staging is free again
 }
 
@@ -256,12 +351,13 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         float ar[D], ai[D];
         if (valid) {
             R = P.reg[r];
-            assemble_row_io<D>(P, R, inst, s, io, T, ar, ai);
+            assemble_row_blk<D, LD>(P, R, inst, s, io, T, reinterpret_cast<float2*>(base), ar, ai);
         } else {
             R = RegionInfo{-1, -1, 0, 0, 0, 0, 0};
 #pragma unroll
             for (int c = 0; c < D; ++c) { ar[c] = 0.f; ai[c] = 0.f; }
         }
+        __syncwarp();   // every lane is done with its staging row before the buffers are written
         if (wrow) {
 #pragma unroll
             for (int c = 0; c < D / 2; ++c) {
@@ -509,7 +605,11 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
         for (int c = 0; c < D / 2; ++c) wrow[c] = make_float4(ur[2 * c], ui[2 * c], ur[2 * c + 1], ui[2 * c + 1]);
     }
     __syncwarp();
-    for (int j = s; j < D; ++j) {   // upper triangle of row s
+    // entry (s, j) for j = s + d mod D, d = 0..D/2: every unordered pair once (d = D/2 from the
+    // lower of its two rows), D/2 + 1 entries per lane instead of a triangle's D - s
+    for (int d = 0; d <= D / 2; ++d) {
+        if (d == D / 2 && s >= D / 2) break;
+        const int j = (s + d) & (D - 1);
         const float4* wj = reinterpret_cast<const float4*>(Wb + j * LD);
         float accr = 0.f, acci = 0.f;
 #pragma unroll
@@ -520,8 +620,8 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
             accr += ur[2 * c + 1] * x.z + ui[2 * c + 1] * x.w;
             acci += ui[2 * c + 1] * x.z - ur[2 * c + 1] * x.w;
         }
-        Rb[s * LD + j] = make_float2(accr, j == s ? 0.f : acci);
-        if (j > s) Rb[j * LD + s] = make_float2(accr, -acci);   // exactly Hermitian
+        Rb[s * LD + j] = make_float2(accr, d == 0 ? 0.f : acci);
+        if (d > 0) Rb[j * LD + s] = make_float2(accr, -acci);   // exactly Hermitian
     }
     __syncwarp();
     if (valid) {
