@@ -565,7 +565,8 @@ def solve(s):
 
 
 def launches_per_step(info):
-    """Kernels of the library per step: lrh_reset 1; per Alg. 2 stage 1 (restart) + the
+    """Kernels of the library per step: lrh_reset 1 + one per class with stored eigenbases
+    (regions of 3 and 4 sites: reset to the identity); per Alg. 2 stage 1 (restart) + the
     iterations (graph: one pass per iteration, nc kernels or 1 with the one-launch class mode,
     + final update + advance; persistent: 1 + 2); Alg. 1: 1 (restart) + per iteration a pass,
     a reduction and an update, or 1 cooperative kernel; then nc certification kernels + 1
@@ -573,11 +574,12 @@ def launches_per_step(info):
     nc = len(info["class_sites"])
     per_pass = 1 if info["concurrent_classes"] == 2 else nc
     persistent = info["loop"] == "persistent"
+    reset = 1 + (sum(1 for k in info["class_sites"] if k in (3, 4)) if info.get("warm_bytes", 0) > 0 else 0)
     if WL.variant == "nesterov":
         body = 3 if persistent else WL.iters_per_stage * per_pass + 2
-        return 1 + len(WL.betas) * (1 + body) + nc + 1
+        return reset + len(WL.betas) * (1 + body) + nc + 1
     body = 1 if persistent else WL.iters * (per_pass + 2)
-    return 1 + 1 + body + nc + 1
+    return reset + 1 + body + nc + 1
 
 
 def run_lrh(args, ws, rank, dev, stream):
