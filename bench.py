@@ -566,7 +566,7 @@ def solve(s):
 
 def launches_per_step(info):
     """Kernels of the library per step: lrh_reset 1 + one per class with stored eigenbases
-    (regions of 3 and 4 sites: reset to the identity); per Alg. 2 stage 1 (restart) + the
+    (regions of 3, 4, 6 and 7 sites: reset to the identity); per Alg. 2 stage 1 (restart) + the
     iterations (graph: one pass per iteration, nc kernels or 1 with the one-launch class mode,
     + final update + advance; persistent: 1 + 2); Alg. 1: 1 (restart) + per iteration a pass,
     a reduction and an update, or 1 cooperative kernel; then nc certification kernels + 1
@@ -574,7 +574,7 @@ def launches_per_step(info):
     nc = len(info["class_sites"])
     per_pass = 1 if info["concurrent_classes"] == 2 else nc
     persistent = info["loop"] == "persistent"
-    reset = 1 + (sum(1 for k in info["class_sites"] if k in (3, 4)) if info.get("warm_bytes", 0) > 0 else 0)
+    reset = 1 + (sum(1 for k in info["class_sites"] if k in (3, 4, 6, 7)) if info.get("warm_bytes", 0) > 0 else 0)
     if WL.variant == "nesterov":
         body = 3 if persistent else WL.iters_per_stage * per_pass + 2
         return reset + len(WL.betas) * (1 + body) + nc + 1
@@ -709,12 +709,13 @@ def fp32_peak(dev):
 
 
 def warm_started(inf, ci):
-    """Whether class ci's pass starts its eigensolves from stored bases (the 2x2-block layout of
-    regions of 3 and 4 sites, lrh_options.cold_start off): each such eigensolve first forms
-    V^H V, V (3 I - V^H V) / 2, theta V and V^H (theta V), four complex D x D products (32 D^3
-    flop)."""
+    """Whether class ci's pass starts its eigensolves from stored bases (regions of 3 and 4 sites
+    in the 2x2-block layout, and the CTA classes of 6 and 7 sites; lrh_options.cold_start off):
+    each such eigensolve first forms V^H V, V (3 I - V^H V) / 2, theta V and V^H (theta V), four
+    complex D x D products (32 D^3 flop)."""
     shape = inf["class_block"][ci]
-    return inf.get("warm_bytes", 0) > 0 and inf["class_sites"][ci] in (3, 4) and 4096 < shape < 8192
+    k = inf["class_sites"][ci]
+    return inf.get("warm_bytes", 0) > 0 and ((k in (3, 4) and 4096 < shape < 8192) or k in (6, 7))
 
 
 def roofline(s, dev, stream, k):

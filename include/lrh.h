@@ -184,7 +184,7 @@ typedef struct {
                                     and certify (FP64) only if the estimate is >= target[i] -
                                     screen_tol on every targeted instance; the run's last
                                     checkpoint is always certified.  0: certify every checkpoint */
-    int32_t cold_start;          /* 0 (default): the FP32 eigensolve of a region of 3 or 4 sites
+    int32_t cold_start;          /* 0 (default): the FP32 eigensolve of a region of 3, 4, 6 or 7 sites
                                     starts from the eigenvectors its previous pass stored (one
                                     D x D basis per region and instance on the device, the
                                     identity at creation): theta_e is first rotated into that
@@ -366,7 +366,7 @@ int lrh_selftest_barrier_timeout(lrh_problem* p);
 
 /* Checkpoint / resume.  The state is the iteration scalars (theta_k, step counter, beta,
  * L_hat, alpha, iteration parity), nu, zeta, nu_best, q_best and the stored eigenbases of the
- * regions of 3 and 4 sites (lrh_options.cold_start; lrh_info.warm_bytes), packed into one host buffer
+ * regions of 3, 4, 6 and 7 sites (lrh_options.cold_start; lrh_info.warm_bytes), packed into one host buffer
  * of lrh_state_bytes() bytes; lrh_set_state accepts only a buffer from a problem with the same
  * instance count, message layout and variant.  Resuming from a saved state and iterating gives
  * bit-identical messages to an uninterrupted run.  Both synchronise. */

@@ -935,11 +935,12 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
         if (p->class_k[c] == 3 || p->class_k[c] == 4) p->class_block[c] = LRH_SHAPE_BLOCKS + 128;   // 2x2-block layout
     }
     p->P.tc_backtransform = 0;
-    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites), the identity at first
+    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites) and of the CTA classes
+    // of 6 and 7 sites, the identity at first
     for (int k = 0; k < kClassSlots; ++k) P.warm_off[k] = -1;
     for (size_t c = 0; c < p->class_k.size(); ++c) {
         const int k = p->class_k[c];
-        if (k != 3 && k != 4) continue;
+        if (k != 3 && k != 4 && k != 6 && k != 7) continue;
         P.warm_off[k] = p->warm_elems;
         p->warm_elems += NI * p->class_count[c] * ((int64_t)1 << (2 * k));
     }

@@ -685,6 +685,150 @@ __device__ bool backtransform_tc(const DevProblem& P, unsigned char* sm, float* 
     return ok;
 }
 
+// Warm start of a CTA region's eigensolve (D = 64, 128) from the basis V its previous pass stored
+// at Vg (D x D row-major complex: natural rows, eigenvector labels as columns), in two parts
+// around the assembly of theta (which needs the shared buffer `buf`, D x (D + 1) complex):
+//   warm_cta_basis: one Newton-Schulz step, V <- V (3 I - V^H V) / 2 (V^H V formed from V staged
+//     in buf, then held in buf while each thread forms its rows' chunk of the new V from V's row
+//     in global memory), written back to Vg;
+//   warm_cta_rotate (after the assembly): T = theta V (theta from buf, V from Vg) into buf, then
+//     V^H T (V from Vg, T from buf) into buf at the Jacobi's positions (sig), upper triangle.
+// Both products run over the TR x TC register tiles of the rho formation.  CTA barriers inside.
+template <int D>
+struct WarmTile {
+    static constexpr int NT = CtaCfg<D>::NT, TR = CtaCfg<D>::TR, TC = CtaCfg<D>::TC, CS = D / TC;
+    float r[TR][TC], i[TR][TC];
+    int i0, cb;
+    __device__ __forceinline__ WarmTile() {
+        const int t = threadIdx.x;
+        i0 = (t / CS) * TR;
+        cb = t % CS;
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) { r[a][b] = 0.f; i[a][b] = 0.f; }
+    }
+    // += conj(x[a]) * y[b]  (cx) or x[a] * y[b]
+    template <bool CX>
+    __device__ __forceinline__ void mac(const float2 (&x)[TR], const float2 (&y)[TC]) {
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) {
+                if (CX) {
+                    r[a][b] = fmaf(x[a].x, y[b].x, fmaf(x[a].y, y[b].y, r[a][b]));
+                    i[a][b] = fmaf(x[a].x, y[b].y, fmaf(-x[a].y, y[b].x, i[a][b]));
+                } else {
+                    r[a][b] = fmaf(x[a].x, y[b].x, fmaf(-x[a].y, y[b].y, r[a][b]));
+                    i[a][b] = fmaf(x[a].x, y[b].y, fmaf(x[a].y, y[b].x, i[a][b]));
+                }
+            }
+    }
+    // the tile into a plain D x D row-major array
+    __device__ __forceinline__ void store(float2* out) const {
+#pragma unroll
+        for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) out[(i0 + a) * D + cb + CS * b] = make_float2(r[a][b], i[a][b]);
+    }
+};
+
+template <int D>
+__device__ void warm_cta_basis(float2* buf, float2* Vg) {
+    using WT = WarmTile<D>;
+    constexpr int NT = WT::NT, TR = WT::TR, TC = WT::TC, CS = WT::CS, W = D / 4;
+    const int t = threadIdx.x;
+    {   // V into buf (float4 copies: D x D complex)
+        const float4* src = reinterpret_cast<const float4*>(Vg);
+        float4* dst = reinterpret_cast<float4*>(buf);
+        for (int e = t; e < D * D / 2; e += NT) dst[e] = src[e];
+    }
+    __syncthreads();
+    WT G;   // G = V^H V: G[i][c] = sum_k conj(V[k][i]) V[k][c]
+    for (int k = 0; k < D; ++k) {
+        const float2* vk = buf + k * D;
+        float2 x[TR], y[TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a) x[a] = vk[G.i0 + a];
+#pragma unroll
+        for (int b = 0; b < TC; ++b) y[b] = vk[G.cb + CS * b];
+        G.template mac<true>(x, y);
+    }
+    __syncthreads();
+    G.store(buf);
+    __syncthreads();
+    // rows' chunk of V (3 I - G) / 2: thread (row, chunk) forms V'[row][chunk W + m]
+    const int row = vrow_of(t), chunk = vchunk_of(t);
+    float ur[W], ui[W];
+#pragma unroll
+    for (int m = 0; m < W; ++m) { ur[m] = 0.f; ui[m] = 0.f; }
+    const float2* vrow = Vg + (int64_t)row * D;
+    for (int c = 0; c < D; ++c) {
+        const float2 a = vrow[c];
+        const float2* gc = buf + c * D + chunk * W;
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+            const float2 g = gc[m];
+            ur[m] = fmaf(a.x, g.x, fmaf(-a.y, g.y, ur[m]));
+            ui[m] = fmaf(a.x, g.y, fmaf(a.y, g.x, ui[m]));
+        }
+    }
+    __syncthreads();   // every thread has read V's rows from Vg (its own chunk is written by it alone)
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+        float2* e = Vg + (int64_t)row * D + chunk * W + m;
+        const float2 o = *e;
+        *e = make_float2(fmaf(1.5f, o.x, -0.5f * ur[m]), fmaf(1.5f, o.y, -0.5f * ui[m]));
+    }
+    __syncthreads();
+}
+
+template <int D>
+__device__ void warm_cta_rotate(float2* buf, const float2* Vg) {
+    using WT = WarmTile<D>;
+    constexpr int TR = WT::TR, TC = WT::TC, CS = WT::CS;
+    Full<float> A{buf, D};
+    WT T;   // T = theta V: T[i][c] = sum_k theta[i][k] V[k][c]
+    int si[TR];
+#pragma unroll
+    for (int a = 0; a < TR; ++a) si[a] = A.sig(T.i0 + a);
+    for (int k = 0; k < D; ++k) {
+        const int sk = A.sig(k);
+        const float2* vk = Vg + (int64_t)k * D;
+        float2 x[TR], y[TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a) x[a] = A.get(si[a], sk);
+#pragma unroll
+        for (int b = 0; b < TC; ++b) y[b] = vk[T.cb + CS * b];
+        T.template mac<false>(x, y);
+    }
+    __syncthreads();
+    T.store(buf);
+    __syncthreads();
+    WT M;   // V^H T: M[i][c] = sum_k conj(V[k][i]) T[k][c]
+    for (int k = 0; k < D; ++k) {
+        const float2* vk = Vg + (int64_t)k * D;
+        const float2* tk = buf + k * D;
+        float2 x[TR], y[TC];
+#pragma unroll
+        for (int a = 0; a < TR; ++a) x[a] = vk[M.i0 + a];
+#pragma unroll
+        for (int b = 0; b < TC; ++b) y[b] = tk[M.cb + CS * b];
+        M.template mac<true>(x, y);
+    }
+    __syncthreads();
+    // upper triangle at the Jacobi's positions (exactly Hermitian, real diagonal)
+#pragma unroll
+    for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+            const int ii = M.i0 + a, jj = M.cb + CS * b;
+            if (ii < jj) A.set(A.sig(ii), A.sig(jj), make_float2(M.r[a][b], M.i[a][b]));
+            else if (ii == jj) A.set(A.sig(ii), A.sig(ii), make_float2(M.r[a][b], 0.f));
+        }
+    __syncthreads();
+}
+
 template <int D>
 __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const DevProblem P, const PassIO io,
                                                                         const int32_t* __restrict__ cls,
@@ -712,15 +856,38 @@ __global__ void __launch_bounds__(CtaCfg<D>::NT) region_pass_cta_kernel(const De
     build_table<D, float>(tab);
     Full<float> A{buf, D};
     if (t < D) idx0[t] = A.sig(t);
+    // warm start from the stored basis (uniform over the CTA)
+    const bool warm = P.warm != nullptr && P.warm_off[k] >= 0 && !P.st->cold;
+    float2* Vg = warm ? P.warm + P.warm_off[k] + (int64_t)blockIdx.x * (D * D) : nullptr;
+    if (warm) warm_cta_basis<D>(buf, Vg);
     assemble_packed_io<D>(P, R, inst, A, io, Th);
     __syncthreads();
+    if (warm) warm_cta_rotate<D>(buf, Vg);
     const int row = vrow_of(t), chunk = vchunk_of(t);
     float vr[W], vi[W];
+    if (warm) {
 #pragma unroll
-    for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
+        for (int m = 0; m < W; ++m) {
+            const float2 v = Vg[(int64_t)row * D + chunk * W + m];
+            vr[m] = v.x; vi[m] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < W; ++m) { vr[m] = (chunk * W + m == row) ? 1.f : 0.f; vi[m] = 0.f; }
+    }
     float norm2, off2;
     const int sweeps =
         jacobi_cta<D, float, true>(A, prm, idx0, idx1, tab, red, vr, vi, P.st->max_sweeps, 1e-12f, norm2, off2);
+    if (warm) {   // the eigenvectors as the next pass's starting basis (the identity if not finite)
+        bool fin = true;
+#pragma unroll
+        for (int m = 0; m < W; ++m) fin = fin && isfinite(vr[m]) && isfinite(vi[m]);
+        const bool bad = __syncthreads_or(fin ? 0 : 1) != 0;
+#pragma unroll
+        for (int m = 0; m < W; ++m)
+            Vg[(int64_t)row * D + chunk * W + m] = bad ? make_float2(chunk * W + m == row ? 1.f : 0.f, 0.f)
+                                                       : make_float2(vr[m], vi[m]);
+    }
     // the slot maps are back to the identity after whole sweeps: diag = eigenvalues
     if (t < D) lam[t] = A.dget(A.sig(t)).x;
     __syncthreads();

@@ -155,7 +155,8 @@ struct DevProblem {
     int64_t big_slot;        // complex entries per slot
     int32_t big_slots;       // slots (= CTAs of a D = 256 launch)
     int32_t big_log_sweeps;  // sweeps the rotation log of a slot holds (the D = 256 sweep cap)
-    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites): class k's unit u
+    // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites) and of the CTA classes
+    // of 6 and 7 sites: class k's unit u
     // (= instance * count + position in the class list) owns the D x D row-major complex matrix
     // at warm + warm_off[k] + u D^2 (warm_off[k] < 0: no stored basis for the class)
     float2* warm;

@@ -118,7 +118,7 @@ class Solver:
     autotuner's choice); ``use_graph`` True / False is shorthand for "graph" / "eager".
     ``betas``, ``iters_per_stage``, ``certify_every`` and ``deadline_s`` describe the schedule
     that ``solve`` runs inside the library.  ``cold_start`` True makes every eigensolve of the
-    regions of 3 and 4 sites start from the identity instead of the basis their previous pass
+    regions of 3, 4, 6 and 7 sites start from the identity instead of the basis their previous pass
     stored (lrh_options.cold_start).
     """
 

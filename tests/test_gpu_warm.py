@@ -1,6 +1,6 @@
-"""Warm-started eigensolves of the regions of 3 and 4 sites (2x2-block layout): each pass starts
-from the basis the region's previous pass stored, made unitary by one Newton-Schulz step, with
-theta rotated into it.  Against the FP64 oracle element by element after a small move of the
+"""Warm-started eigensolves of the regions of 3 and 4 sites (2x2-block layout) and of 6 and 7 sites
+(CTA layout): each pass starts from the basis the region's previous pass stored, made unitary by
+one Newton-Schulz step, with theta rotated into it.  Against the FP64 oracle element by element after a small move of the
 multipliers, after a jump to unrelated multipliers and after many passes at one point (the
 stored basis must not drift from unitary); warm and cold runs agree to rounding, the warm one
 with fewer sweeps; the stored bytes, reset and recovery from a non-finite pass."""
@@ -26,7 +26,10 @@ CASES = {
     "xxz_tri4_plaq": lambda: L.xxz_triangular(4, 3),
     "j1j2_4_plaq": lambda: L.j1j2_square(4),
     "chain_L4_dense": lambda: L.random_chain(11, 21, L=4, scale=0.6),
+    "chain_L6_D64": lambda: L.perturbed_chain(9, L=6, delta=0.3, seed=6),
+    "chain_L7_D128": lambda: L.perturbed_chain(9, L=7, delta=0.3, seed=7),
 }
+WARM_K = (3, 4, 6, 7)
 
 
 def _evaluate_at(s, nu):
@@ -44,7 +47,7 @@ def _check_against_oracle(s, p, P, h, nu, beta):
 
 def _block_sweeps(s):
     inf = s.info()
-    return {k: inf["sweeps"][i] for i, k in enumerate(inf["class_sites"]) if k in (3, 4)}
+    return {k: inf["sweeps"][i] for i, k in enumerate(inf["class_sites"]) if k in WARM_K}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
@@ -74,7 +77,7 @@ def test_warm_pass_after_a_small_move_matches_oracle(name, beta):
         1.0, float(np.max(np.abs(c.region_values("last")))))
 
 
-@pytest.mark.parametrize("name", ["xxz_tri4_plaq", "chain_L3_D8"])
+@pytest.mark.parametrize("name", ["xxz_tri4_plaq", "chain_L3_D8", "chain_L7_D128"])
 def test_warm_pass_after_a_jump_matches_oracle(name):
     """The stored bases belong to unrelated multipliers: Jacobi still converges from them."""
     p = CASES[name]()
@@ -104,15 +107,16 @@ def test_many_passes_at_one_point_keep_the_basis_unitary():
     _check_against_oracle(s, p, P, h, nu, 64.0)
 
 
-def test_alg2_run_warm_equals_cold_to_rounding_and_resets():
-    p = CASES["xxz_tri4_plaq"]()
+@pytest.mark.parametrize("name,k", [("xxz_tri4_plaq", 4), ("chain_L7_D128", 7)])
+def test_alg2_run_warm_equals_cold_to_rounding_and_resets(name, k):
+    p = CASES[name]()
     P = Poset(p.regions)
     h = dual.local_terms(p, P)
     runs = {}
     for cold in (False, True):
         s = Solver(p, variant="nesterov", beta=4.0, cold_start=cold)
         s.step(30)
-        runs[cold] = (s, s.messages("nu").astype(np.complex128), _block_sweeps(s)[4])
+        runs[cold] = (s, s.messages("nu").astype(np.complex128), _block_sweeps(s)[k])
     (sw, nw, kw), (sc, nc, kc) = runs[False], runs[True]
     assert kw < kc
     st = dual.NesterovState(nu=dual.zeros_messages(P, p.n_instances), zeta=dual.zeros_messages(P, p.n_instances))
@@ -140,8 +144,26 @@ def test_stored_bytes_and_no_store_without_block_classes():
     inf = s.info()
     n16 = inf["class_regions"][inf["class_sites"].index(4)]
     assert inf["warm_bytes"] == 8 * p.n_instances * n16 * 256
+    c = Solver(CASES["chain_L7_D128"]())          # classes 1..7: bases for 3, 4, 6 and 7 sites
+    inf = c.info()
+    want = sum(8 * n * 4 ** k for k, n in zip(inf["class_sites"], inf["class_regions"]) if k in WARM_K)
+    assert inf["warm_bytes"] == want
     q = L.heisenberg_square(6)                   # edges and sites only: no 3- or 4-site class
     assert Solver(q).info()["warm_bytes"] == 0
+
+
+def test_tensor_core_back_transform_from_a_warm_start_matches_oracle():
+    """The 128 x 128 pass with rho = W W^dagger on the tensor cores, after a small move."""
+    p = CASES["chain_L7_D128"]()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    nu1 = random_traceless_messages(P, p.n_instances, seed=97, scale=0.4)
+    nu2 = (nu1 + random_traceless_messages(P, p.n_instances, seed=98, scale=1e-3)).astype(np.complex64)
+    s = Solver(p, variant="nesterov", beta=16.0)
+    s.set_launch_shape(7, 2)                      # LRH_SHAPE_CTA_TENSOR
+    _evaluate_at(s, nu1)
+    _evaluate_at(s, nu2)
+    _check_against_oracle(s, p, P, h, nu2, 16.0)
 
 
 def test_non_finite_pass_leaves_identity_bases_and_the_run_recovers():
