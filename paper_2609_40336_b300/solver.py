@@ -45,11 +45,12 @@ def marshal(n_sites: int, regions: Sequence[Sequence[int]], term_sites: Sequence
     if len(mats):
         off[1:] = np.cumsum(sizes)[:-1]
     total = int(sizes.sum())
-    flat = np.zeros((n_inst, max(total, 1)), np.complex128)
-    for o, m in zip(off, mats):
-        if m.shape[0] != n_inst:
-            raise ValueError("all term matrices need the same number of instances")
-        flat[:, o:o + m.shape[1] * m.shape[2]] = m.reshape(n_inst, -1)
+    if any(m.shape[0] != n_inst for m in mats):
+        raise ValueError("all term matrices need the same number of instances")
+    if total:
+        flat = np.concatenate([m.reshape(n_inst, -1).astype(np.complex128, copy=False) for m in mats], axis=1)
+    else:
+        flat = np.zeros((n_inst, 1), np.complex128)
     pp = np.ascontiguousarray([q[0] for q in pairs] if pairs else [0], np.int32)
     pc = np.ascontiguousarray([q[1] for q in pairs] if pairs else [0], np.int32)
     tr = np.ascontiguousarray(term_region if term_region is not None else [0], np.int32)
