@@ -15,6 +15,7 @@
 #include <new>
 #include <set>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -214,57 +215,84 @@ int reset_warm(lrh_problem* p) {
 
 // Hermitian part of every term matrix (exactly: (m + m^dagger)/2) embedded into the dense
 // region terms h_e in FP64, instance-major, at the offsets of region_h_off.
+// fn(lo, hi) over [0, n) split into contiguous ranges on the host's cores (disjoint outputs)
+void parallel_ranges(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
+    const int64_t hw = std::max<int64_t>(1, std::min<int64_t>((int64_t)std::thread::hardware_concurrency(), 32));
+    const int64_t nt = std::min<int64_t>(hw, n);
+    if (nt <= 1) { fn(0, n); return; }
+    std::vector<std::thread> th;
+    for (int64_t w = 0; w < nt; ++w) th.emplace_back(fn, n * w / nt, n * (w + 1) / nt);
+    for (auto& x : th) x.join();
+}
+
+// Every term's Hermitian part embedded into its region: for each instance, the terms in order
+// (each entry of h_e sums its terms in ascending t, whatever the split over instances).
 void embed_terms(const lrh_problem* p, const double* term_mats, std::vector<double>& h64) {
     auto pext = [](int x, int m) { int r = 0, q = 0; for (int bb = 0; bb < 8; ++bb) if (m >> bb & 1) { r |= (x >> bb & 1) << q; ++q; } return r; };
     h64.assign((size_t)(2 * p->n_inst * std::max<int64_t>(p->h_elems, 1)), 0.0);
+    // per term, its entries (i, j) of h_e with the term entries (a, c) and (c, a) they take
+    struct Ent { int32_t hij, ac, ca; bool diag; };
+    std::vector<std::vector<Ent>> ents((size_t)p->n_terms);
     for (int t = 0; t < p->n_terms; ++t) {
-        const int e = p->term_region[t];
-        const int k = p->region_k[e];
-        const int64_t D = (int64_t)1 << k;
-        const int M = p->term_mask[t];
-        const int64_t Dt = (int64_t)1 << p->term_kt[t];
-        for (int inst = 0; inst < p->n_inst; ++inst) {
-            const double* m = term_mats + 2 * ((int64_t)inst * p->term_total + p->term_off[t]);
-            double* h = h64.data() + 2 * ((int64_t)inst * p->h_elems + p->region_h_off[e]);
-            for (int i = 0; i < D; ++i)
-                for (int j = 0; j < D; ++j) {
-                    if (((i ^ j) & ~M) != 0) continue;
-                    const int64_t a = pext(i, M), c = pext(j, M);
-                    const double re = 0.5 * (m[2 * (a * Dt + c)] + m[2 * (c * Dt + a)]);
-                    const double im = (a == c) ? 0.0 : 0.5 * (m[2 * (a * Dt + c) + 1] - m[2 * (c * Dt + a) + 1]);
-                    h[2 * (i * D + j)] += re;
-                    h[2 * (i * D + j) + 1] += im;
-                }
-        }
+        const int k = p->region_k[p->term_region[t]];
+        const int D = 1 << k, M = p->term_mask[t], Dt = 1 << p->term_kt[t];
+        for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) {
+                if (((i ^ j) & ~M) != 0) continue;
+                const int a = pext(i, M), c = pext(j, M);
+                ents[t].push_back(Ent{i * D + j, a * Dt + c, c * Dt + a, a == c});
+            }
     }
+    parallel_ranges(p->n_inst, [&](int64_t lo, int64_t hi) {
+        for (int64_t inst = lo; inst < hi; ++inst)
+            for (int t = 0; t < p->n_terms; ++t) {
+                const double* m = term_mats + 2 * (inst * p->term_total + p->term_off[t]);
+                double* h = h64.data() + 2 * (inst * p->h_elems + p->region_h_off[p->term_region[t]]);
+                for (const Ent& x : ents[t]) {
+                    h[2 * x.hij] += 0.5 * (m[2 * x.ac] + m[2 * x.ca]);
+                    h[2 * x.hij + 1] += x.diag ? 0.0 : 0.5 * (m[2 * x.ac + 1] - m[2 * x.ca + 1]);
+                }
+            }
+    });
 }
 
+// FP64 terms to the device, and their FP32 copy rounded there (round to nearest, as a host cast)
 int upload_terms(lrh_problem* p, const std::vector<double>& h64) {
     if (!p->h_elems) return LRH_OK;
-    std::vector<float> h32h(h64.size());
-    for (size_t i = 0; i < h64.size(); ++i) h32h[i] = (float)h64[i];
-    LRH_CK(cudaMemcpyAsync(const_cast<float2*>(p->P.h32), h32h.data(), sizeof(float) * h32h.size(), cudaMemcpyHostToDevice, p->stream));
-    LRH_CK(cudaMemcpyAsync(const_cast<double2*>(p->P.h64), h64.data(), sizeof(double) * h64.size(), cudaMemcpyHostToDevice, p->stream));
+    const int64_t n = (int64_t)p->n_inst * p->h_elems;
+    LRH_CK(cudaMemcpyAsync(const_cast<double2*>(p->P.h64), h64.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, p->stream));
+    LRH_CK(launch_round_terms(const_cast<float2*>(p->P.h32), p->P.h64, n, p->stream));
     LRH_CK(cudaStreamSynchronize(p->stream));
     return LRH_OK;
 }
 
 int check_terms(const lrh_problem* p, const int64_t* term_ptr, const double* term_mats) {
-    for (int t = 0; t < p->n_terms; ++t) {
-        const int64_t Dt = (int64_t)1 << (term_ptr[t + 1] - term_ptr[t]);
-        for (int i = 0; i < p->n_inst; ++i) {
-            const double* m = term_mats + 2 * ((int64_t)i * p->term_total + p->term_off[t]);
-            double mx = 0;
-            for (int64_t a = 0; a < Dt * Dt; ++a) mx = std::max(mx, std::fabs(m[2 * a]) + std::fabs(m[2 * a + 1]));
-            for (int64_t a = 0; a < Dt; ++a)
-                for (int64_t c = 0; c < Dt; ++c) {
-                    const double dr = m[2 * (a * Dt + c)] - m[2 * (c * Dt + a)];
-                    const double di = m[2 * (a * Dt + c) + 1] + m[2 * (c * Dt + a) + 1];
-                    if (!std::isfinite(dr) || !std::isfinite(di)) return fail(LRH_EINVAL, "non-finite term entry");
-                    if (std::fabs(dr) + std::fabs(di) > 1e-10 * std::max(1.0, mx))
-                        return fail(LRH_ENOTHERM, "term " + std::to_string(t) + " is not Hermitian");
-                }
-        }
+    // per instance range: the first offending term (lowest t, then lowest instance) and its kind
+    std::vector<int64_t> bad((size_t)p->n_inst, -1);
+    std::vector<int> kind((size_t)p->n_inst, 0);
+    parallel_ranges(p->n_inst, [&](int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            for (int t = 0; t < p->n_terms && bad[(size_t)i] < 0; ++t) {
+                const int64_t Dt = (int64_t)1 << (term_ptr[t + 1] - term_ptr[t]);
+                const double* m = term_mats + 2 * (i * p->term_total + p->term_off[t]);
+                double mx = 0;
+                for (int64_t a = 0; a < Dt * Dt; ++a) mx = std::max(mx, std::fabs(m[2 * a]) + std::fabs(m[2 * a + 1]));
+                for (int64_t a = 0; a < Dt && bad[(size_t)i] < 0; ++a)
+                    for (int64_t c = 0; c < Dt; ++c) {
+                        const double dr = m[2 * (a * Dt + c)] - m[2 * (c * Dt + a)];
+                        const double di = m[2 * (a * Dt + c) + 1] + m[2 * (c * Dt + a) + 1];
+                        if (!std::isfinite(dr) || !std::isfinite(di)) { bad[(size_t)i] = t; kind[(size_t)i] = 1; break; }
+                        if (std::fabs(dr) + std::fabs(di) > 1e-10 * std::max(1.0, mx)) { bad[(size_t)i] = t; kind[(size_t)i] = 2; break; }
+                    }
+            }
+    });
+    int64_t t0 = -1;
+    int k0 = 0;
+    for (int64_t i = 0; i < p->n_inst; ++i)
+        if (bad[(size_t)i] >= 0 && (t0 < 0 || bad[(size_t)i] < t0)) { t0 = bad[(size_t)i]; k0 = kind[(size_t)i]; }
+    if (t0 >= 0) {
+        if (k0 == 1) return fail(LRH_EINVAL, "non-finite term entry");
+        return fail(LRH_ENOTHERM, "term " + std::to_string(t0) + " is not Hermitian");
     }
     return LRH_OK;
 }

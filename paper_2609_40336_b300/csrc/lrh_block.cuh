@@ -643,11 +643,12 @@ __device__ __forceinline__ void region_pass_blk_impl(const DevProblem& P, const 
                 const int ra = pdep_bits(idx >> kf, M);
                 const int rb = pdep_bits(idx & (Df - 1), M);
                 float accr = 0.f, acci = 0.f;
+                int x = 0;   // pdep(c, Mc) for c = 0, 1, ...: the submasks of Mc in increasing order
                 for (int c = 0; c < nrest; ++c) {
-                    const int x = pdep_bits(c, Mc);
                     const float2 v = Rb[(ra | x) * LD + (rb | x)];
                     accr += v.x;
                     acci += v.y;
+                    x = ((x | ~Mc) + 1) & Mc;
                 }
                 trb[pi.off + idx] = make_float2(accr, acci);
             }
@@ -946,11 +947,12 @@ __device__ __forceinline__ void region_pass_w16_impl(const DevProblem& P, const 
                 const int ra = pdep_bits(idx >> kf, M);
                 const int rb = pdep_bits(idx & (Df - 1), M);
                 float accr = 0.f, acci = 0.f;
+                int x = 0;   // pdep(c, Mc) for c = 0, 1, ...: the submasks of Mc in increasing order
                 for (int c = 0; c < nrest; ++c) {
-                    const int x = pdep_bits(c, Mc);
                     const float2 v = Rb[(ra | x) * LD + (rb | x)];
                     accr += v.x;
                     acci += v.y;
+                    x = ((x | ~Mc) + 1) & Mc;
                 }
                 trb[pi.off + idx] = make_float2(accr, acci);
             }

@@ -214,6 +214,8 @@ cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double 
                              int variant, int step_rule, int max_sweeps, int cert_sweeps, int cold, cudaStream_t s);
 // every stored eigenbasis (n_mats matrices of D x D) set to the identity
 cudaError_t launch_warm_identity(float2* warm, int64_t n_mats, int D, cudaStream_t s);
+// h32[i] = h64[i] rounded to FP32 (n complex entries)
+cudaError_t launch_round_terms(float2* h32, const double2* h64, int64_t n, cudaStream_t s);
 cudaError_t launch_copy(float2* dst, const float2* src, int64_t n, cudaStream_t s);
 
 // Adjoint (lrh_vjp.cu): theta_bar per region for the classes, then nu_bar and term cotangents.

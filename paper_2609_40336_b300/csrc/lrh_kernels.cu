@@ -183,11 +183,12 @@ __device__ __forceinline__ void region_pass_impl(const DevProblem& P, const Pass
                 const int ra = pdep_bits(idx >> kf, M);
                 const int rb = pdep_bits(idx & (Df - 1), M);
                 float accr = 0.f, acci = 0.f;
+                int x = 0;   // pdep(c, Mc) for c = 0, 1, ...: the submasks of Mc in increasing order
                 for (int c = 0; c < nrest; ++c) {
-                    const int x = pdep_bits(c, Mc);
                     const float2 v = Rb[(ra | x) * LD + (rb | x)];
                     accr += v.x;
                     acci += v.y;
+                    x = ((x | ~Mc) + 1) & Mc;
                 }
                 trb[pi.off + idx] = make_float2(accr, acci);
             }
@@ -1074,6 +1075,21 @@ cudaError_t launch_set_state(const DevProblem& P, int par, double theta, double 
                              int max_sweeps, int cert_sweeps, int cold, cudaStream_t s) {
     set_state_kernel<<<1, 1, 0, s>>>(P.st, par, theta, t, set_theta_t, beta, inv_lhat, alpha, degen_tol, variant,
                                      step_rule, max_sweeps, cert_sweeps, cold);
+    return cudaGetLastError();
+}
+
+__global__ void round_terms_kernel(float2* __restrict__ h32, const double2* __restrict__ h64, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double2 v = h64[i];
+        h32[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    }
+}
+
+cudaError_t launch_round_terms(float2* h32, const double2* h64, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 16);
+    round_terms_kernel<<<(unsigned)blocks, 256, 0, s>>>(h32, h64, n);
     return cudaGetLastError();
 }
 

@@ -53,6 +53,25 @@ def test_non_finite_term_is_rejected_on_the_host():
     assert e.value.code == -1
 
 
+def test_first_bad_term_is_reported_whatever_instance_holds_it():
+    """Terms are checked on the host's cores, instances split between threads: the error names
+    the lowest bad term, and a non-finite entry and a non-Hermitian term give their own codes."""
+    p = L.add_instances(L.random_chain(9, 3, L=2), [5, 6, 7], scale=0.3)
+    s = Solver(p)
+    mats = [m.copy() for m in p.term_mats]
+    mats[4][3, 0, 1] += 0.5            # term 4 broken in the last instance only
+    mats[6][1, 1, 0] += 0.5            # term 6 in the second
+    with pytest.raises(_lib.LrhError) as e:
+        s.set_terms(mats)
+    assert e.value.code == _lib.ENOTHERM and "term 4 " in str(e.value)
+    mats = [m.copy() for m in p.term_mats]
+    mats[1][2, 0, 0] = np.nan
+    with pytest.raises(_lib.LrhError) as e:
+        s.set_terms(mats)
+    assert e.value.code == _lib.EINVAL
+    s.set_terms(p.term_mats)           # the good terms still load
+
+
 def test_unconverged_certification_is_flagged_and_still_a_lower_bound():
     """With one FP64 sweep the certification cannot converge on 16 x 16 regions: lrh_bound
     returns LRH_ENOCONV and min_i a_ii - ||offdiag||_F, which is below the exact Q(nu)."""
