@@ -10,7 +10,8 @@ import pytest
 import lrh_gen as g
 from oracle import dual
 from oracle.poset import Poset
-from tests.gpu_helpers import check_grad, grad_entry_tol, random_traceless_messages, region_norms
+from tests.gpu_helpers import (check_grad, grad_entry_tol, ground_sensitivity, random_traceless_messages,
+                               region_norms)
 
 pytestmark = pytest.mark.gpu
 L = g.lattices
@@ -75,6 +76,26 @@ def test_warm_pass_after_a_small_move_matches_oracle(name, beta):
     # warm and cold agree to rounding
     assert np.max(np.abs(s.region_values("last") - c.region_values("last"))) <= 2e-5 * max(
         1.0, float(np.max(np.abs(c.region_values("last")))))
+
+
+@pytest.mark.parametrize("name", ["xxz_tri4_plaq", "chain_L6_D64", "chain_L7_D128"])
+def test_warm_ground_state_pass_matches_oracle(name):
+    """Alg. 1's pass (ground projector of the eigenvalues within the degeneracy tolerance) from
+    the bases of a pass at nearby multipliers: the projector does not depend on the basis."""
+    p = CASES[name]()
+    P = Poset(p.regions)
+    h = dual.local_terms(p, P)
+    nu1 = random_traceless_messages(P, p.n_instances, seed=99, scale=0.6)
+    nu2 = (nu1 + random_traceless_messages(P, p.n_instances, seed=100, scale=1e-3)).astype(np.complex64)
+    s = Solver(p, variant="subgradient", alpha=0.1, step_rule="const")
+    s.set_messages("nu", nu1)
+    s.evaluate()
+    s.set_messages("nu", nu2)
+    s.evaluate()
+    ref = dual.region_pass(P, h, nu2.astype(np.complex128), "ground", tol=1e-5)
+    norms = region_norms(P, h, nu2)
+    assert np.all(np.abs(s.region_values("last") - ref.value) <= 1e-5 * np.maximum(1.0, norms))
+    check_grad(s.messages("grad"), ref.grad, grad_entry_tol(P, norms, ground_sensitivity(P, h, nu2, 1e-5)))
 
 
 @pytest.mark.parametrize("name", ["xxz_tri4_plaq", "chain_L3_D8", "chain_L7_D128"])
