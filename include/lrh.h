@@ -191,8 +191,11 @@ typedef struct {
                                     basis, after one Newton-Schulz step makes it unitary to
                                     rounding, and Jacobi sweeps only what theta_e moved since.
                                     Nonzero: every eigensolve starts from the identity and the
-                                    stored bases are neither read nor written.  Either way the
-                                    eigensolve stops at the same threshold.                   */
+                                    stored bases are neither read nor written; nonzero at
+                                    lrh_create allocates no bases at all (lrh_info.warm_bytes
+                                    = 0), and the problem then stays cold whatever later
+                                    options say.  Either way the eigensolve stops at the same
+                                    threshold.                                                */
 } lrh_options;
 
 typedef struct lrh_problem lrh_problem;

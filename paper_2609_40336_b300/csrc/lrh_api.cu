@@ -964,9 +964,9 @@ int lrh_create(const lrh_problem_desc* d, const lrh_options* opts, void* stream,
     }
     p->P.tc_backtransform = 0;
     // stored eigenbases of the 2x2-block classes (regions of 3 and 4 sites) and of the CTA classes
-    // of 6 and 7 sites, the identity at first
+    // of 6 and 7 sites, the identity at first (none for a problem created with cold starts)
     for (int k = 0; k < kClassSlots; ++k) P.warm_off[k] = -1;
-    for (size_t c = 0; c < p->class_k.size(); ++c) {
+    for (size_t c = 0; c < p->class_k.size() && !p->opt.cold_start; ++c) {
         const int k = p->class_k[c];
         if (k != 3 && k != 4 && k != 6 && k != 7) continue;
         P.warm_off[k] = p->warm_elems;
