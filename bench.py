@@ -617,6 +617,7 @@ def run_lrh(args, ws, rank, dev, stream):
         dist.barrier()
     step_ms = []
     bounds = None
+    sweeps0 = s.info()["sweeps"]
     wall0 = time.perf_counter()
     for _ in range(args.steps):
         if flush is not None:
@@ -650,7 +651,14 @@ def run_lrh(args, ws, rank, dev, stream):
                 "certified_bound_per_site": [float(b) / p.n_sites for b in bounds][:8],
                 "us_per_iteration": 1e3 * total_ms / args.steps / iters,
                 "wall_s_timed_region": wall, "clocks": clocks.summary(),
-                "gpu_launches": launches_per_step(info) * args.steps}
+                "gpu_launches": launches_per_step(info) * args.steps,
+                # the same wall time split by size class: regions of the class x iterations / time
+                "per_class_eigensolves_per_s": {
+                    f"{2 ** k}x{2 ** k}": ws * n_k * s.n_instances * iters * args.steps / (total_ms / 1e3)
+                    for k, n_k in zip(info["class_sites"], info["class_regions"])},
+                "sweeps_per_eigensolve_timed": {
+                    f"{2 ** k}x{2 ** k}": (sw1 - sw0) / max(1, n_k * s.n_instances * iters * args.steps)
+                    for k, n_k, sw0, sw1 in zip(info["class_sites"], info["class_regions"], sweeps0, info["sweeps"])}}
         line.update(extras)
         print(json.dumps(line), flush=True)
     s.close()

@@ -342,7 +342,10 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
  * from / appended to `cache_path` (JSON lines keyed by class size, region count and SM count;
  * NULL = no cache); flags bit 0 forces re-measuring.  Runs region passes at the current point
  * (their outputs are recomputed by the next iteration) and iterations on a saved copy of the
- * multipliers, which it restores; must not be called during stream capture; synchronises. */
+ * multipliers, which it restores; the stored eigenbases (lrh_options.cold_start) are copied to
+ * a temporary device buffer of lrh_info.warm_bytes and put back (LRH_ENOMEM if that buffer
+ * cannot be had), so tuning does not change later results; must not be called during stream
+ * capture; synchronises. */
 int lrh_autotune(lrh_problem* p, const char* cache_path, int32_t flags);
 
 /* Set the launch shape of one region class by hand (what lrh_autotune chooses): 64, 128 or
