@@ -869,6 +869,23 @@ def measure_extras(s, p, dev, stream, args, fstar, value, tune):
                     f"another for the time-to-1e-4 estimate (same iteration count)"}
     except Exception as ex:   # the comparator is context, not the product
         out["fp64_torch_comparator"] = {"error": str(ex)[:200]}
+    # ---- the adjoint of the smoothed bound at the solve's final point (lrh_vjp, device outputs)
+    if WL.variant == "nesterov" and s.info()["max_region_sites"] <= 7:
+        s.vjp_device(1.0)   # allocates the adjoint buffers
+        reps = 5
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            s.vjp_device(1.0)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        pass_ms = (out.get("roofline") or {}).get("launch_us", 0.0) / 1e3
+        out["adjoint"] = {"ms_per_vjp": ms, "vjp_over_dominant_pass": ms / pass_ms if pass_ms > 0 else None,
+                          "note": "d Q_beta / d(nu, terms) for every instance at the final point: eigenvectors recomputed, "
+                                  "divided-difference kernel, adjoint of the partial traces and embeddings"}
     # ---- end to end through the public API with host buffers (create from host arrays, solve, read)
     steps = max(1, min(2, args.steps))
     h2d = 0
