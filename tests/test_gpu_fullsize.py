@@ -103,3 +103,30 @@ def test_fullsize_sampled_parity(name):
         assert np.abs(block(P, nu2, q, i) - nw).max() <= tol
     print(f"FULLSIZE {name}: {N_SAMPLES} samples, worst gradient error / bound = {worst:.3f}, "
           f"loop={s.info()['loop']}, shapes={s.info()['class_block']}")
+
+
+@pytest.mark.parametrize("name", sorted(WORKLOADS))
+def test_fullsize_parity_after_many_warm_started_passes(name):
+    """40 Alg. 2 iterations from nu = 0 (every eigensolve of the 16 x 16, 64 x 64 and 128 x 128
+    classes starting from the previous pass's basis), then one more pass at the reached
+    multipliers: sampled gradients and values against the oracle at those multipliers."""
+    p = WORKLOADS[name]()
+    P = Poset(p.regions)
+    I = p.n_instances
+    s = Solver(p, variant="nesterov", beta=BETA)
+    assert s.info()["warm_bytes"] > 0
+    s.step(40)
+    s.restart()                      # theta = 1: the next pass evaluates at eta = nu
+    s.evaluate()
+    nu = s.messages("nu").astype(np.complex128)
+    g = s.messages("grad")
+    vals = s.region_values("last")
+    qs, ins = samples(P, I, 11)
+    grads, ovals, norms = dual.sampled_pass(p, P, nu, qs, ins, "smooth", beta=BETA)
+    worst = 0.0
+    for q, i, gq in zip(qs, ins, grads):
+        worst = max(worst, np.abs(block(P, g, q, i) - gq).max() / bound_of(P, q, i, norms))
+    assert worst <= 1.0, worst
+    for (i, e), v in ovals.items():
+        assert abs(vals[i, e] - v) <= 1e-5 * max(1.0, norms[(i, e)]), (i, e)
+    print(f"FULLSIZE-WARM {name}: worst gradient error / bound = {worst:.3f}")
