@@ -340,7 +340,8 @@ int lrh_vjp(lrh_problem* p, const double* q_bar, const void* g_bar, int32_t g_ba
  * the problem allows a persistent launch, the graph against the persistent iteration driver
  * (used when lrh_options.loop is LRH_LOOP_AUTO); then keeps the fastest.  Choices are read
  * from / appended to `cache_path` (JSON lines keyed by class size, region count and SM count;
- * NULL = no cache); flags bit 0 forces re-measuring.  Runs region passes at the current point
+ * NULL = no cache); flags bit 0 forces re-measuring.  Classes of 3 and 4 sites with stored
+ * eigenbases are tuned among the 2x2-block shapes only (the layout that warm-starts).  Runs region passes at the current point
  * (their outputs are recomputed by the next iteration) and iterations on a saved copy of the
  * multipliers, which it restores; the stored eigenbases (lrh_options.cold_start) are copied to
  * a temporary device buffer of lrh_info.warm_bytes and put back (LRH_ENOMEM if that buffer

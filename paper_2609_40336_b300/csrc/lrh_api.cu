@@ -1481,8 +1481,13 @@ int autotune_impl(lrh_problem* p, const char* cache_path, int32_t flags) {
             if (rc) return rc;
             continue;
         }
+        // with stored eigenbases the 3- and 4-site classes are tuned among the 2x2-block shapes
+        // only, the layout that warm-starts: passes timed at one point cannot see the sweeps the
+        // warm starts save from one iteration to the next (at nu = 0 every layout is trivial)
+        const bool warm_k = (k == 3 || k == 4) && p->P.warm != nullptr && p->P.warm_off[k] >= 0 && !p->opt.cold_start;
         const std::string key = "region_pass k=" + std::to_string(k) + " units=" +
-                                std::to_string((int64_t)p->class_count[c] * p->n_inst) + " sms=" + std::to_string(sms);
+                                std::to_string((int64_t)p->class_count[c] * p->n_inst) + " sms=" + std::to_string(sms) +
+                                (warm_k ? " warm" : "");
         int blk = 0;
         if (!cache_lookup(cache, key, &blk)) {
             float best = 1e30f;
@@ -1492,6 +1497,7 @@ int autotune_impl(lrh_problem* p, const char* cache_path, int32_t flags) {
                 if (cand < 0 && k != 2) continue;   // thread-per-region layout: 4 x 4 regions
                 if (cand > LRH_SHAPE_BLOCKS && cand < LRH_SHAPE_WARP16 && k != 3 && k != 4) continue;   // 8 x 8, 16 x 16
                 if (cand > LRH_SHAPE_WARP16 && k != 4) continue;   // one warp per 16 x 16 region
+                if (warm_k && !(cand > LRH_SHAPE_BLOCKS && cand < LRH_SHAPE_WARP16)) continue;
                 float ms = 0;
                 int rc = time_adaptive(p, 2.0f, [&]() -> int {
                     LRH_CK(launch_region_pass(p->P, plain_io(p), k, p->class_list[c], p->class_count[c], p->stream, cand));
