@@ -250,27 +250,32 @@ class HaloDriver:
 
 class DistExchange:
     """Exchange between shards in separate processes (torch.distributed: NCCL for device
-    buffers, gloo for host buffers); shard i runs on rank i of ``group``."""
+    buffers, gloo for host buffers); shard i runs on rank i of ``group``.  ``host_staging``
+    sends device buffers through host copies (for a backend without device point-to-point,
+    e.g. gloo)."""
 
-    def __init__(self, group=None):
+    def __init__(self, group=None, host_staging: bool = False):
         import torch.distributed as dist
         self.dist = dist
         self.group = group
+        self.host_staging = host_staging
 
     def exchange(self, drv: HaloDriver) -> None:
         dist = self.dist
         ops, landing = [], []
         for peer, (a, b) in drv.send_seg.items():
-            ops.append(dist.P2POp(dist.isend, drv.send[:, 2 * a:2 * b].contiguous(), peer, self.group))
+            t = drv.send[:, 2 * a:2 * b].contiguous()
+            ops.append(dist.P2POp(dist.isend, t.cpu() if self.host_staging else t, peer, self.group))
         for peer, (a, b) in drv.recv_seg.items():
-            t = drv.recv.new_empty((drv.recv.shape[0], 2 * (b - a)))
+            shape = (drv.recv.shape[0], 2 * (b - a))
+            t = drv.recv.new_empty(shape, device="cpu") if self.host_staging else drv.recv.new_empty(shape)
             ops.append(dist.P2POp(dist.irecv, t, peer, self.group))
             landing.append((a, b, t))
         if ops:
             for req in dist.batch_isend_irecv(ops):
                 req.wait()
         for a, b, t in landing:
-            drv.recv[:, 2 * a:2 * b] = t
+            drv.recv[:, 2 * a:2 * b] = t.to(drv.recv.device) if self.host_staging else t
 
     def allsum(self, x: np.ndarray) -> np.ndarray:
         """Sum of every shard's per-instance partial values, added in shard order."""
